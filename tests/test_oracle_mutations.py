@@ -1,0 +1,52 @@
+"""Planted mistakes in a scratch copy of the oracle (CPU only): each must make
+at least one oracle pin fail.  Shows that the pins constrain the dropped-term,
+wrong-sign, wrong-index and transposed-operand errors they are meant to."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PINS = ["tests/test_oracle_coeffs.py", "tests/test_oracle_scheme.py", "tests/test_oracle_bruteforce.py"]
+
+MUTATIONS = {
+    "cross_term_sign": ("- EXT(u, a + 1, b - 1, mx)\n                - EXT(u, a - 1, b + 1, mx)",
+                        "+ EXT(u, a + 1, b - 1, mx)\n                - EXT(u, a - 1, b + 1, mx)"),
+    "source_time_index": ("double tk = T + k * dt;\n            double sk",
+                          "double tk = T + (k + 1) * dt;\n            double sk"),
+    "upwind_direction": ("ux = nu > 0.0 ? (uc - uW) / g->dx : (uE - uc) / g->dx;",
+                         "ux = nu < 0.0 ? (uc - uW) / g->dx : (uE - uc) / g->dx;"),
+    "edge_weight_sign": ("e->gL[b + 1] = ((-0.5 - rx) * A[0]", "e->gL[b + 1] = ((-0.5 + rx) * A[0]"),
+    "C0_dropped_term": ("- g->hy * g->hy * Uyy / 24.0", ""),
+    "ghost_corner_order": ("for (int b = -1; b <= ny + 1; ++b) {\n        double gl",
+                           "for (int b = 0; b <= ny; ++b) {\n        double gl"),
+    "trapezoid_weight": ("double wb = (b == 0 || b == ny) ? 0.5 : 1.0;", "double wb = (b == 0) ? 0.5 : 1.0;"),
+    "nu_sign": ("out[3] = Vxi - c_xi;", "out[3] = Vxi + c_xi;"),
+    "jacobian_derivative": ("double Jeta = xab * yb + xa * ybb - xbb * ya - xb * yab;",
+                            "double Jeta = xab * yb + xa * ybb + xbb * ya - xb * yab;"),
+    "transposed_metric": ("double a[2] = { yb, -xb }, b[2] = { -ya, xa };",
+                          "double a[2] = { yb, -xb }, b[2] = { -xa, ya };"),
+    "periodic_wrap": ("return ((i % n) + n) % n;", "return i < 0 ? 0 : (i >= n ? n - 1 : i);"),
+    "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
+                       "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    src = open(os.path.join(ROOT, "oracle", "pd_oracle.c")).read()
+    old, new = MUTATIONS[name]
+    assert old in src, "mutation anchor missing: " + name
+    d = tmp_path / name
+    d.mkdir()
+    (d / "pd_oracle.c").write_text(src.replace(old, new, 1))
+    shutil.copy(os.path.join(ROOT, "oracle", "pd_oracle.h"), d)
+    so = str(d / "lib.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fopenmp",
+                    "-fPIC", "-shared", "-o", so, str(d / "pd_oracle.c"), "-lm"], check=True)
+    env = dict(os.environ, ORC_SO_OVERRIDE=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider"] + PINS,
+                       cwd=ROOT, env=env, capture_output=True, text=True)
+    assert r.returncode != 0, "planted mistake %s passed every pin:\n%s" % (name, r.stdout[-2000:])
