@@ -1,0 +1,336 @@
+"""Benchmark of the patch-dynamics hot path on GB300.
+
+Workload: the 65 x 65 tanh-stretched heterogeneous tensor-diffusion CDR problem
+(11 x 11 micro points per patch, 20 forward-Euler micro steps per burst,
+200 macro steps, FP32 bursts with FP64 restriction and projection).  One bench
+step = one pd_step call over all 200 macro steps (lift -> burst -> restrict ->
+project per macro step, captured in a CUDA graph), with the macro field already
+resident in HBM.  The L2 is flushed (512 MB write) between timed steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run: every rank runs an independent
+replica of the workload on its own GPU (no data-path collective; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "patch point-updates/s (roofline frac), macro steps/s at fixed L2 err vs FP64"
+UNIT = "point-updates/s"
+FLOP_PER_UPDATE = 25.0        # algorithmic FP32 flops per point-update (9-point stencil + source)
+WORKLOAD = "tanh-stretched heterogeneous CDR, 65x65 macro grid, 11x11 micro, K=20, 200 macro steps"
+
+# DRAM traffic of one fused macro-step launch from an ncu capture of this
+# kernel source (sha256 of the kernel sources); null once the kernel changes.
+NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("pd_kernels.cu", "pd_internal.h"):
+        with open(os.path.join(ROOT, "paper_2405_08764_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def peaks() -> dict:
+    p = {"hbm_gbs": None, "sm_max_mhz": 2070.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        p.update(hbm_gbs=d.get("hbm_gbs"), sm_max_mhz=d.get("sm_max_mhz", 2070.0), source="measured")
+    else:
+        p["hbm_gbs"] = 6800.0
+    # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop per clock at the maximum SM clock
+    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(prob: dict, target_s: float = 12.0) -> dict:
+    """The CPU oracle as it stands on the host cores, on a bounded sample of the
+    workload: the first few macro steps of the same problem."""
+    import numpy as np
+    import oracle
+    o = oracle.Oracle(prob)
+    U = o.init_field()
+    dtm = 0.5 * o.dt_macro()
+    dt = o.dt_micro()
+    per_step = o.n_patch * o.mx * o.my * o.s.k_micro
+    t = time.perf_counter()
+    o.step(U, 0.0, dtm, 1, dt)
+    one = max(time.perf_counter() - t, 1e-3)
+    n = max(1, min(200, int(target_s / one)))
+    t = time.perf_counter()
+    o.step(U, 0.0, dtm, n, dt)
+    el = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    del np
+    return {"value": n * per_step / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of 200 macro steps of the benchmark workload (%.1f s)" % (n, el)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2405_08764_gb300 import workloads as W
+    prob = W.bench_workload()
+    o = oracle.Oracle(prob)
+    U = o.init_field()
+    dtm, dt = 0.5 * o.dt_macro(), o.dt_micro()
+    per_macro = o.n_patch * o.mx * o.my * o.s.k_micro
+    n_sample = 20  # macro steps per reference step (bounded sample)
+    for _ in range(args.warmup):
+        o.step(U, 0.0, dtm, 1, dt)
+    times = []
+    for s in range(args.steps):
+        t = time.perf_counter()
+        U = o.step(U, s * n_sample * dtm, dtm, n_sample, dt)
+        times.append(time.perf_counter() - t)
+    el = sum(times)
+    value = args.steps * n_sample * per_macro / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "%d of 200 macro steps per step" % n_sample,
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d macro steps per step, %d steps" % (n_sample, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2405_08764_gb300 import workloads as W
+    from paper_2405_08764_gb300.api import Grid
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prob = W.bench_workload()
+    if ws > 1:
+        # independent replica per rank: its own seeded source amplitudes
+        prob = W.c2_heterogeneous(seed=2 + rank)
+    g = Grid(prob, prec="fp32")
+    info = g.info()
+    n_macro = prob["n_macro"]
+    dtm = info["dt_macro_suggested"]
+    updates = info["n_patch"] * info["m_xi"] * info["m_eta"] * info["k_micro"] * n_macro
+    U0 = g.init_field()
+    U = U0.clone()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # warm-up: graph capture and first replays
+    for _ in range(args.warmup):
+        U.copy_(U0)
+        g.step(U, 0.0, dtm, n_macro)
+    g.sync()
+
+    # timed region: K steps, per-step CUDA events, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    g.set_timing(True)
+    l0 = g.launches()
+    for s in range(args.steps):
+        U.copy_(U0)
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        g.step(U, 0.0, dtm, n_macro)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    launches = g.launches() - l0
+    kern_ms, kern_n = g.timing()
+    g.set_timing(False)
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    g.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = ws * updates * args.steps / (ms / 1e3)
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # initial field, pd_step, D2H of the result, all inside the timed region
+    Uh = U0.cpu().pin_memory()
+    Uout = torch.empty_like(Uh).pin_memory()
+    Ud = torch.empty_like(U0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(args.steps):
+        Ud.copy_(Uh, non_blocking=True)
+        g.step(Ud, 0.0, dtm, n_macro)
+        Uout.copy_(Ud, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = ws * updates * args.steps / (e2e_ms / 1e3)
+    nbytes = U0.numel() * 8
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # accuracy at this configuration: FP32 result against the FP64 path
+    g64 = Grid(prob, prec="fp64")
+    V = g64.init_field()
+    g64.step(V, 0.0, dtm, n_macro)
+    g64.sync()
+    a, b = U.cpu().numpy(), V.cpu().numpy()
+    l2 = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    pk = peaks()
+    per_launch_updates = updates / n_macro
+    achieved = (FLOP_PER_UPDATE * per_launch_updates * kern_n / (kern_ms / 1e3)) / 1e12 if kern_ms > 0 else None
+    sha = kernel_sources_sha()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sources_sha256"] == sha else None
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+        "frac": (achieved / pk["fp32_tflops"]) if achieved else None, "traffic": traffic,
+        "kernel": "patch_warp_kernel<11,cross,tsrc,float,fused> (one macro step per launch)",
+        "flop_per_point_update": FLOP_PER_UPDATE,
+        "kernel_ms_per_launch": kern_ms / kern_n if kern_n else None,
+        "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (
+            pk["sm_max_mhz"], pk["source"]),
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "macro_steps_per_step": n_macro, "n_patch": info["n_patch"],
+                   "point_updates_per_step": updates, "dt_macro": dtm,
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "macro_steps_per_s": n_macro * args.steps / (ms / 1e3),
+        "l2_rel_err_vs_fp64": l2,
+        "roofline": roofline,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import __graft_entry__
+    __graft_entry__.build()
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

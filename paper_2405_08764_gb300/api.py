@@ -1,0 +1,207 @@
+"""Thin Python binding of libpd: torch tensors for device memory, torch's
+current CUDA stream for ordering, and argument marshalling to the C ABI.  Every
+step of the patch-dynamics path runs in the library's kernels; there is no CPU
+or PyTorch fallback."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("libpd needs a CUDA device (GB300, sm_103a)")
+
+
+def grid_desc(p: dict, prec: str) -> N.GridDesc:
+    d = N.GridDesc()
+    d.n_xi, d.n_eta, d.periodic_xi = int(p["n_xi"]), int(p["n_eta"]), int(p["periodic_xi"])
+    d.xi0, d.xi1, d.eta0, d.eta1 = [float(v) for v in p["box"]]
+    d.map = N.MAPS[p["map"]]
+    for k in range(4):
+        d.map_p[k] = float(p["map_p"][k])
+    d.m_xi, d.m_eta = int(p["m_xi"]), int(p["m_eta"])
+    d.h_ratio_xi, d.h_ratio_eta = float(p["h_ratio_xi"]), float(p["h_ratio_eta"])
+    d.k_micro, d.cfl_micro = int(p["k_micro"]), float(p["cfl_micro"])
+    d.prec = N.PD_FP32 if prec == "fp32" else N.PD_FP64
+    d.conv_scheme = N.CONV[p["conv"]]
+    d.restrict_mode = N.RESTRICT[p["restrict"]]
+    return d
+
+
+def coeff_desc(p: dict):
+    c = N.CoeffDesc()
+    c.M11, c.M12, c.M22 = [float(v) for v in p["M"]]
+    c.d0, c.dx, c.dy = [float(v) for v in p["d_aff"]]
+    c.ds, c.dk = [float(v) for v in p["d_sin"]]
+    four = p["four"]
+    c.n_four = len(four["c"])
+    for k in range(c.n_four):
+        c.four_c[k] = float(four["c"][k])
+        c.four_phi[k] = float(four["phi"][k])
+    c.four_ra, c.four_rb = float(four["ra"]), float(four["rb"])
+    for k in range(3):
+        c.va[k] = float(p["va"][k])
+        c.vb[k] = float(p["vb"][k])
+        c.src_p[k] = float(p["src_p"][k])
+    c.f0 = float(p["f0"])
+    c.src = N.SRC[p["src"]]
+    amp = None
+    if p.get("src_amp") is not None:
+        amp = np.ascontiguousarray(p["src_amp"], dtype=np.float64)
+        c.src_amp = amp.ctypes.data_as(C.POINTER(C.c_double))
+    c.tkind, c.tc = N.TIME[p["time"]], float(p["tc"])
+    c.sol = N.SOL[p["sol"]]
+    return c, amp
+
+
+def _ptr(t: torch.Tensor) -> int:
+    assert t.is_cuda and t.is_contiguous()
+    return t.data_ptr()
+
+
+class Grid:
+    """A set of patch-dynamics instances on the current CUDA device.
+
+    probs: one workloads-style problem dictionary or a list of them (all with
+    the same micro size and precision).  prec: "fp32" (FP32 bursts, FP64
+    restriction and projection) or "fp64"."""
+
+    def __init__(self, probs, prec: str = "fp32", graphs: bool = True):
+        _require_cuda()
+        self.L = N.load()
+        if isinstance(probs, dict):
+            probs = [probs]
+        self.probs = [dict(p) for p in probs]
+        self.prec = prec
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        n = len(self.probs)
+        descs = (N.GridDesc * n)(*[grid_desc(p, prec) for p in self.probs])
+        h = C.c_void_p()
+        st = torch.cuda.current_stream().cuda_stream
+        rc = self.L.pd_create_grid(descs, n, C.c_void_p(st), C.byref(h))
+        if rc != N.PD_OK:
+            raise N.PDError(rc, "pd_create_grid rejected the descriptors")
+        self.h = h
+        self.L.pd_set_graph_mode(self.h, 1 if graphs else 0)
+        for k, p in enumerate(self.probs):
+            c, amp = coeff_desc(p)
+            N.check(self.L.pd_set_coeffs(self.h, k, C.byref(c)), self.h)
+            del amp
+        nm, npch, sb = C.c_longlong(), C.c_longlong(), C.c_size_t()
+        N.check(self.L.pd_sizes(self.h, C.byref(nm), C.byref(npch), C.byref(sb)), self.h)
+        self.n_macro_total, self.n_patch_total, self.state_bytes = nm.value, npch.value, sb.value
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.L.pd_destroy_grid(h)
+            except Exception:
+                pass
+            self.h = C.c_void_p()
+
+    # -- plumbing -------------------------------------------------------------
+    def _stream(self):
+        self.L.pd_set_stream(self.h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def info(self, inst: int = 0) -> dict:
+        o = N.Info()
+        N.check(self.L.pd_query(self.h, inst, C.byref(o)), self.h)
+        return {f: getattr(o, f) for f, _ in N.Info._fields_}
+
+    def new_field(self) -> torch.Tensor:
+        return torch.zeros(self.n_macro_total, dtype=torch.float64, device=self.device)
+
+    def new_state(self) -> torch.Tensor:
+        return torch.zeros(self.state_bytes, dtype=torch.uint8, device=self.device)
+
+    def state_views(self, state: torch.Tensor, inst: int = 0) -> dict:
+        """typed views of the micro-state sections (all instances)."""
+        i = self.info(inst)
+        P, mx, my, es = self.n_patch_total, i["m_xi"], i["m_eta"], i["edge_stride"]
+        rdt = torch.float32 if self.prec == "fp32" else torch.float64
+        rb = 4 if self.prec == "fp32" else 8
+
+        def sec(off, n, dt, b):
+            return state[off:off + n * b].view(dt)
+        return {
+            "u0": sec(i["off_u0"], P * mx * my, torch.float64, 8).view(P, my, mx),
+            "r": sec(i["off_r"], P * mx * my, rdt, rb).view(P, my, mx),
+            "w": sec(i["off_w"], P * mx * my, rdt, rb).view(P, my, mx),
+            "edge": sec(i["off_edge"], P * 4 * es, torch.float64, 8).view(P, 4, es),
+            "bias": sec(i["off_bias"], P, torch.float64, 8),
+        }
+
+    # -- C-ABI entry points ----------------------------------------------------
+    def init_field(self, U: torch.Tensor | None = None, t: float = 0.0, kinds=None) -> torch.Tensor:
+        U = self.new_field() if U is None else U
+        self._stream()
+        for k, p in enumerate(self.probs):
+            kind = p["init"] if kinds is None else kinds[k]
+            prm = list(p.get("init_p", [])) or [0.0]
+            arr = (C.c_double * len(prm))(*prm)
+            N.check(self.L.pd_init_field(self.h, k, N.INIT[kind], arr, len(prm), float(t),
+                                         C.c_void_p(_ptr(U))), self.h)
+        return U
+
+    def coeffs(self, inst: int = 0) -> torch.Tensor:
+        i = self.info(inst)
+        out = torch.empty(i["n_patch"] * i["m_xi"] * i["m_eta"] * 8, dtype=torch.float64, device=self.device)
+        self._stream()
+        N.check(self.L.pd_get_coeffs(self.h, inst, C.c_void_p(_ptr(out))), self.h)
+        return out.view(i["n_patch"], i["m_eta"], i["m_xi"], 8)
+
+    def lift(self, U: torch.Tensor, t: float, state: torch.Tensor):
+        self._stream()
+        N.check(self.L.pd_lift(self.h, C.c_void_p(_ptr(U)), float(t), C.c_void_p(_ptr(state))), self.h)
+
+    def micro_burst(self, state: torch.Tensor, t: float, k_steps: int):
+        self._stream()
+        N.check(self.L.pd_micro_burst(self.h, C.c_void_p(_ptr(state)), float(t), int(k_steps)), self.h)
+
+    def restrict(self, state: torch.Tensor, dU: torch.Tensor | None = None) -> torch.Tensor:
+        dU = torch.empty(self.n_patch_total, dtype=torch.float64, device=self.device) if dU is None else dU
+        self._stream()
+        N.check(self.L.pd_restrict(self.h, C.c_void_p(_ptr(state)), C.c_void_p(_ptr(dU))), self.h)
+        return dU
+
+    def project(self, U: torch.Tensor, dU: torch.Tensor, t: float, dt_macro: float):
+        self._stream()
+        N.check(self.L.pd_project(self.h, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(dU)), float(t),
+                                  float(dt_macro)), self.h)
+
+    def step(self, U: torch.Tensor, t0: float, dt_macro: float, n_macro: int):
+        self._stream()
+        N.check(self.L.pd_step(self.h, C.c_void_p(_ptr(U)), float(t0), float(dt_macro), int(n_macro)), self.h)
+
+    def sync(self):
+        N.check(self.L.pd_sync(self.h), self.h)
+
+    def launches(self) -> int:
+        return int(self.L.pd_launch_count(self.h))
+
+    def set_timing(self, enabled: bool):
+        N.check(self.L.pd_set_timing(self.h, 1 if enabled else 0), self.h)
+
+    def timing(self):
+        """(summed fused-kernel event time in ms, fused launches covered)"""
+        ms, n = C.c_double(), C.c_longlong()
+        N.check(self.L.pd_get_timing(self.h, C.byref(ms), C.byref(n)), self.h)
+        return ms.value, n.value
+
+    def save_checkpoint(self, U: torch.Tensor, t: float, step: int, path: str):
+        self._stream()
+        N.check(self.L.pd_save_checkpoint(self.h, C.c_void_p(_ptr(U)), float(t), int(step),
+                                          path.encode()), self.h)
+
+    def load_checkpoint(self, U: torch.Tensor, path: str):
+        t, s = C.c_double(), C.c_longlong()
+        self._stream()
+        N.check(self.L.pd_load_checkpoint(self.h, C.c_void_p(_ptr(U)), C.byref(t), C.byref(s),
+                                          path.encode()), self.h)
+        return t.value, s.value

@@ -1,0 +1,747 @@
+// Host side of libpd: descriptors, device buffers, setup, launch sequencing,
+// CUDA-graph capture of the macro loop, checkpoints and error reporting.
+#include "pd_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+using namespace pd;
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// header block of the micro-state buffer: lift time, s(t), burst time table
+constexpr size_t kStateHeader = 256 + 8 * (size_t)kMaxK + 256;
+
+struct Inst {
+    pd_grid_desc d;
+    InstDev I;                       // host copy (pointers are device pointers)
+    void* rec = nullptr;             // coefficient records
+    int2* bnd_ij = nullptr;
+    double2* bnd_xy = nullptr;
+    double* amp = nullptr;
+    pd_coeff_desc coef;
+    bool coef_set = false;
+    double dt = 0, tau = 0, dtm_sugg = 0;
+    std::vector<int2> bnd_host;
+};
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n_nodes = 0;
+};
+
+struct GraphKey {
+    uintptr_t U;
+    int n;
+    std::vector<double> dtm;
+    bool operator<(const GraphKey& o) const
+    {
+        if (U != o.U) return U < o.U;
+        if (n != o.n) return n < o.n;
+        return dtm < o.dtm;
+    }
+};
+
+}  // namespace
+
+struct pd_grid {
+    std::vector<Inst> inst;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    int* err = nullptr;              // device error flags
+    unsigned long long* acc = nullptr; // device accumulators (3)
+    double* U_scratch = nullptr;     // second macro buffer for pd_step
+    size_t U_scratch_n = 0;
+    double* tab = nullptr;           // time tables (pd_step)
+    size_t tab_n = 0;
+    char* state = nullptr;           // internal micro state (fallback step path)
+    double* dU = nullptr;
+    long long n_macro_total = 0, n_patch_total = 0;
+    size_t state_bytes = 0;
+    bool graphs = true;
+    std::map<GraphKey, GraphEntry> gcache;
+    long long launches = 0;
+    std::string last;
+    int device = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;   // pending event pairs
+    std::vector<cudaEvent_t> tfree;
+    double t_ms = 0.0;
+    long long t_launches = 0;
+};
+
+namespace {
+
+pd_status fail(pd_grid* g, pd_status s, const std::string& msg)
+{
+    if (g) g->last = msg;
+    return s;
+}
+
+pd_status cuda_fail(pd_grid* g, cudaError_t e, const char* where)
+{
+    return fail(g, PD_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PD_CUDA(g, call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(g, e_, #call); \
+    } while (0)
+
+bool valid_desc(const pd_grid_desc& d, std::string& why)
+{
+    if (d.n_xi < 2 || d.n_eta < 2) { why = "n_xi, n_eta must be >= 2"; return false; }
+    if (d.periodic_xi && d.n_xi < 3) { why = "periodic xi needs n_xi >= 3"; return false; }
+    if (d.m_xi < 3 || d.m_eta < 3 || d.m_xi > kMaxM || d.m_eta > kMaxM) { why = "m must be in [3, 32]"; return false; }
+    if (!(d.h_ratio_xi > 0 && d.h_ratio_xi < 1 && d.h_ratio_eta > 0 && d.h_ratio_eta < 1)) {
+        why = "patch ratio h / Delta must lie in (0, 1)"; return false;
+    }
+    if (d.k_micro < 1 || d.k_micro > kMaxK) { why = "k_micro must be in [1, 4096]"; return false; }
+    if (!(d.cfl_micro > 0 && d.cfl_micro <= 1)) { why = "cfl_micro must be in (0, 1]"; return false; }
+    if (!(d.xi1 > d.xi0) || !(d.eta1 > d.eta0)) { why = "empty computational box"; return false; }
+    if (d.map < 0 || d.map > 3) { why = "unknown map"; return false; }
+    if (d.prec != PD_FP32 && d.prec != PD_FP64) { why = "unknown precision"; return false; }
+    if (d.conv_scheme != PD_CONV_UPWIND && d.conv_scheme != PD_CONV_CENTRAL) { why = "unknown convection scheme"; return false; }
+    if (d.restrict_mode != PD_RESTRICT_LIFTED && d.restrict_mode != PD_RESTRICT_MACRO) { why = "unknown restriction"; return false; }
+    if (d.map == PD_MAP_POLAR && !(d.map_p[0] > 0 && d.map_p[1] > d.map_p[0])) { why = "polar map needs 0 < r_in < r_out"; return false; }
+    if (d.map == PD_MAP_SINE && !(std::fabs(d.map_p[0]) < 1)) { why = "sine stretching needs |lambda| < 1"; return false; }
+    long long np = (long long)(d.periodic_xi ? d.n_xi : d.n_xi - 1) * (d.n_eta - 1);
+    if (np * d.m_xi * d.m_eta > (1LL << 40)) { why = "problem too large"; return false; }
+    return true;
+}
+
+// monomial coefficients of the Lagrange basis on {-D, 0, D}: ell_p(s) = sum_k L[p][k] s^k
+void lagrange_monomials(double D, double L[3][3])
+{
+    L[0][0] = 0;   L[0][1] = -0.5 / D; L[0][2] = 0.5 / (D * D);
+    L[1][0] = 1;   L[1][1] = 0;        L[1][2] = -1.0 / (D * D);
+    L[2][0] = 0;   L[2][1] = 0.5 / D;  L[2][2] = 0.5 / (D * D);
+}
+
+void poly_weights(InstDev& I)
+{
+    double Lx[3][3], Ly[3][3];
+    lagrange_monomials(I.Dx, Lx);
+    lagrange_monomials(I.Dy, Ly);
+    const int kl[9][2] = { {0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}, {2, 1}, {1, 2}, {2, 2} };
+    for (int r = 0; r < 9; ++r)
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) I.lw[r][p * 3 + q] = Lx[p][kl[r][0]] * Ly[q][kl[r][1]];
+    // row 0: C0 = c00 - h_xi^2 c20 / 12 - h_eta^2 c02 / 12 (eq. C_0)
+    for (int jj = 0; jj < 9; ++jj)
+        I.lw[0][jj] -= I.hx * I.hx / 12.0 * I.lw[3][jj] + I.hy * I.hy / 12.0 * I.lw[5][jj];
+}
+
+void fill_inst(Inst& s, long long u_off, long long p_off)
+{
+    const pd_grid_desc& d = s.d;
+    InstDev& I = s.I;
+    std::memset(&I, 0, sizeof(I));
+    I.n_xi = d.n_xi; I.n_eta = d.n_eta; I.periodic = d.periodic_xi ? 1 : 0;
+    I.nxp = I.periodic ? d.n_xi : d.n_xi + 1;
+    I.nyp = d.n_eta + 1;
+    I.ncols = I.periodic ? d.n_xi : d.n_xi - 1;
+    I.nrows = d.n_eta - 1;
+    I.i0 = I.periodic ? 0 : 1;
+    I.mx = d.m_xi; I.my = d.m_eta; I.K = d.k_micro;
+    I.conv = d.conv_scheme; I.restrict_mode = d.restrict_mode; I.map = d.map;
+    I.n_patch = I.ncols * I.nrows;
+    I.xi0 = d.xi0; I.xi1 = d.xi1; I.eta0 = d.eta0; I.eta1 = d.eta1;
+    I.Dx = (d.xi1 - d.xi0) / d.n_xi;
+    I.Dy = (d.eta1 - d.eta0) / d.n_eta;
+    I.hx = d.h_ratio_xi * I.Dx;
+    I.hy = d.h_ratio_eta * I.Dy;
+    I.dx = I.hx / (d.m_xi - 1);
+    I.dy = I.hy / (d.m_eta - 1);
+    for (int k = 0; k < 4; ++k) I.map_p[k] = d.map_p[k];
+    I.u_off = u_off; I.p_off = p_off;
+    poly_weights(I);
+    s.bnd_host.clear();
+    for (int j = 0; j < I.nyp; ++j)
+        for (int i = 0; i < I.nxp; ++i) {
+            bool b = (j == 0 || j == I.nyp - 1) || (!I.periodic && (i == 0 || i == I.nxp - 1));
+            if (b) s.bnd_host.push_back(make_int2(i, j));
+        }
+    I.n_bnd = (int)s.bnd_host.size();
+}
+
+// Z_k(mu r) = J_k(mu ra) Y_k(mu r) - Y_k(mu ra) J_k(mu r); first root of Z_k(mu rb)
+double bessel_cross(int k, double mu, double ra, double r)
+{
+    return std::cyl_bessel_j((double)k, mu * ra) * std::cyl_neumann((double)k, mu * r)
+         - std::cyl_neumann((double)k, mu * ra) * std::cyl_bessel_j((double)k, mu * r);
+}
+
+double first_root(int k, double ra, double rb)
+{
+    double h = 0.02 * M_PI / (rb - ra);
+    double lo = h, flo = bessel_cross(k, lo, ra, rb);
+    for (int it = 0; it < 200000; ++it) {
+        double hi = lo + h, fhi = bessel_cross(k, hi, ra, rb);
+        if ((flo < 0) != (fhi < 0)) {
+            for (int b = 0; b < 200 && hi - lo > 1e-15 * hi; ++b) {
+                double mid = 0.5 * (lo + hi), fm = bessel_cross(k, mid, ra, rb);
+                if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else hi = mid;
+            }
+            return 0.5 * (lo + hi);
+        }
+        lo = hi; flo = fhi;
+    }
+    return NAN;
+}
+
+pd_status check_inst(pd_grid* g, int inst)
+{
+    if (!g) return PD_EINVAL;
+    if (inst < 0 || inst >= (int)g->inst.size()) return fail(g, PD_EINVAL, "instance index out of range");
+    return PD_OK;
+}
+
+pd_status all_coeffs_set(pd_grid* g)
+{
+    for (size_t k = 0; k < g->inst.size(); ++k)
+        if (!g->inst[k].coef_set) return fail(g, PD_ESTATE, "pd_set_coeffs not called for instance " + std::to_string(k));
+    return PD_OK;
+}
+
+void layout(const pd_grid* g, const Inst& s, pd_info& o)
+{
+    long long P = g->n_patch_total;
+    int mm = s.d.m_xi * s.d.m_eta;
+    size_t es = s.d.prec == PD_FP32 ? 4 : 8;
+    // all instances of a grid share m and precision in the state buffer layout
+    o.edge_stride = (s.d.m_xi > s.d.m_eta ? s.d.m_xi : s.d.m_eta) + 2;
+    o.off_u0 = align256(kStateHeader);
+    o.off_r = align256(o.off_u0 + (size_t)P * mm * 8);
+    o.off_w = align256(o.off_r + (size_t)P * mm * es);
+    o.off_edge = align256(o.off_w + (size_t)P * mm * es);
+    o.off_bias = align256(o.off_edge + (size_t)P * 4 * o.edge_stride * 8);
+    o.state_bytes = align256(o.off_bias + (size_t)P * 8);
+}
+
+pd_status ensure_step_buffers(pd_grid* g, int n_macro)
+{
+    if (!g->U_scratch) {
+        PD_CUDA(g, cudaMalloc(&g->U_scratch, sizeof(double) * g->n_macro_total));
+        g->U_scratch_n = (size_t)g->n_macro_total;
+    }
+    size_t need = 0;
+    for (auto& s : g->inst) need += (size_t)n_macro * (s.d.k_micro + kTabExtra);
+    if (need > g->tab_n) {
+        if (g->tab) {
+            cudaStreamSynchronize(g->stream);
+            cudaFree(g->tab);
+            for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+            g->gcache.clear();
+        }
+        PD_CUDA(g, cudaMalloc(&g->tab, sizeof(double) * need));
+        g->tab_n = need;
+    }
+    return PD_OK;
+}
+
+// sequence of kernels for n_macro steps on stream st (captured or direct)
+pd_status enqueue_steps(pd_grid* g, double* U, int n_macro, const std::vector<double>& dtm, cudaStream_t st, int& n_launch)
+{
+    size_t tab_off = 0;
+    for (size_t k = 0; k < g->inst.size(); ++k) {
+        Inst& s = g->inst[k];
+        const InstDev& I = s.I;
+        double* bufs[2] = { U + I.u_off, g->U_scratch + I.u_off };
+        int stride = I.K + kTabExtra;
+        if (fused_supported(I)) {
+            for (int t = 0; t < n_macro; ++t) {
+                cudaError_t e = launch_fused_step(I, nullptr, s.d.prec, bufs[t & 1], bufs[(t + 1) & 1],
+                                                  g->tab + tab_off + (size_t)t * stride, dtm[k], st, &n_launch);
+                if (e != cudaSuccess) return cuda_fail(g, e, "fused step");
+            }
+            if (n_macro & 1) {
+                cudaError_t e = cudaMemcpyAsync(bufs[0], bufs[1], sizeof(double) * (size_t)I.nxp * I.nyp,
+                                                cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return cuda_fail(g, e, "copy back");
+            }
+        } else {
+            return fail(g, PD_EINVAL, "fused step needs m_xi == m_eta in {3,5,7,9,11}");
+        }
+        tab_off += (size_t)n_macro * stride;
+    }
+    return PD_OK;
+}
+
+pd_status step_fallback(pd_grid* g, double* U, double t0, const std::vector<double>& dtm, int n_macro)
+{
+    // separate passes through an internal state buffer (m not covered by the fused kernel)
+    if (!g->state) {
+        PD_CUDA(g, cudaMalloc(&g->state, g->state_bytes));
+        PD_CUDA(g, cudaMalloc(&g->dU, sizeof(double) * g->n_patch_total));
+    }
+    for (int t = 0; t < n_macro; ++t) {
+        for (size_t k = 0; k < g->inst.size(); ++k) {
+            Inst& s = g->inst[k];
+            pd_info lay;
+            layout(g, s, lay);
+            double T = t0 + t * dtm[k];
+            cudaError_t e = launch_lift(s.I, nullptr, s.d.prec, U + s.I.u_off, T, g->state, lay, g->stream);
+            if (e == cudaSuccess) e = launch_burst(s.I, nullptr, s.d.prec, g->state, lay, T, s.I.K, g->stream);
+            if (e == cudaSuccess) e = launch_restrict(s.I, s.d.prec, g->state, lay, g->dU, g->stream);
+            if (e == cudaSuccess) e = launch_project(s.I, U + s.I.u_off, g->dU, T, dtm[k], g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "step (separate passes)");
+            g->launches += 6;
+        }
+    }
+    return PD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pd_abi_version(void) { return PD_ABI_VERSION; }
+
+const char* pd_status_str(pd_status s)
+{
+    switch (s) {
+    case PD_OK: return "ok";
+    case PD_EINVAL: return "invalid argument";
+    case PD_ENOMEM: return "out of device memory";
+    case PD_ECUDA: return "CUDA error";
+    case PD_ESTATE: return "call out of order";
+    case PD_EUNSTABLE: return "step above the stability bound";
+    case PD_ETIMEOUT: return "device wait timed out";
+    case PD_ENUMERIC: return "non-finite values on the device";
+    }
+    return "unknown status";
+}
+
+const char* pd_last_error(const pd_grid* g) { return g ? g->last.c_str() : "null grid"; }
+
+long long pd_launch_count(const pd_grid* g) { return g ? g->launches : 0; }
+
+pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_stream, pd_grid** out)
+{
+    if (!descs || n_inst < 1 || !out) return PD_EINVAL;
+    *out = nullptr;
+    pd_grid* g = new pd_grid();
+    g->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&g->device);
+    long long u_off = 0, p_off = 0;
+    g->inst.resize(n_inst);
+    for (int k = 0; k < n_inst; ++k) {
+        std::string why;
+        if (!valid_desc(descs[k], why)) {
+            delete g;
+            return PD_EINVAL;
+        }
+        if (k > 0 && (descs[k].m_xi != descs[0].m_xi || descs[k].m_eta != descs[0].m_eta || descs[k].prec != descs[0].prec)) {
+            delete g;
+            return PD_EINVAL;
+        }
+        g->inst[k].d = descs[k];
+        fill_inst(g->inst[k], u_off, p_off);
+        u_off += (long long)g->inst[k].I.nxp * g->inst[k].I.nyp;
+        p_off += g->inst[k].I.n_patch;
+    }
+    g->n_macro_total = u_off;
+    g->n_patch_total = p_off;
+    cudaError_t e = cudaMalloc(&g->err, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->acc, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+    for (int k = 0; k < n_inst && e == cudaSuccess; ++k) {
+        Inst& s = g->inst[k];
+        size_t es = s.d.prec == PD_FP32 ? 4 : 8;
+        size_t npts = (size_t)s.I.n_patch * s.I.mx * s.I.my;
+        e = cudaMalloc(&s.rec, npts * 8 * es);
+        if (e == cudaSuccess) e = cudaMalloc(&s.bnd_ij, sizeof(int2) * (s.I.n_bnd + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&s.bnd_xy, sizeof(double2) * (s.I.n_bnd + 1));
+        if (e == cudaSuccess && s.I.n_bnd)
+            e = cudaMemcpy(s.bnd_ij, s.bnd_host.data(), sizeof(int2) * s.I.n_bnd, cudaMemcpyHostToDevice);
+        s.I.rec = s.rec; s.I.bnd_ij = s.bnd_ij; s.I.bnd_xy = s.bnd_xy; s.I.err = g->err;
+    }
+    if (e != cudaSuccess) {
+        pd_destroy_grid(g);
+        return e == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA;
+    }
+    pd_info lay;
+    layout(g, g->inst[0], lay);
+    g->state_bytes = lay.state_bytes;
+    *out = g;
+    return PD_OK;
+}
+
+pd_status pd_destroy_grid(pd_grid* g)
+{
+    if (!g) return PD_EINVAL;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+    for (auto& pr : g->tev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (auto e : g->tfree) cudaEventDestroy(e);
+    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
+    cudaFree(g->err); cudaFree(g->acc); cudaFree(g->U_scratch); cudaFree(g->tab);
+    cudaFree(g->state); cudaFree(g->dU);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    delete g;
+    return PD_OK;
+}
+
+pd_status pd_set_stream(pd_grid* g, void* st)
+{
+    if (!g) return PD_EINVAL;
+    g->stream = (cudaStream_t)st;
+    return PD_OK;
+}
+
+pd_status pd_set_graph_mode(pd_grid* g, int enabled)
+{
+    if (!g) return PD_EINVAL;
+    g->graphs = enabled != 0;
+    return PD_OK;
+}
+
+pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
+{
+    pd_status rc = check_inst(g, inst);
+    if (rc) return rc;
+    if (!c) return fail(g, PD_EINVAL, "null coefficient descriptor");
+    if (c->src < 0 || c->src > 3 || c->tkind < 0 || c->tkind > 2 || c->sol < 0 || c->sol > 2)
+        return fail(g, PD_EINVAL, "unknown source, time or solution kind");
+    if (c->n_four < 0 || c->n_four > 3) return fail(g, PD_EINVAL, "n_four must be in [0, 3]");
+    if (c->n_four > 0 && !(c->four_rb > c->four_ra)) return fail(g, PD_EINVAL, "four_rb must exceed four_ra");
+    if (c->src == PD_SRC_GAUSS_PATCH && !c->src_amp) return fail(g, PD_EINVAL, "GAUSS_PATCH needs src_amp");
+    Inst& s = g->inst[inst];
+    cudaSetDevice(g->device);
+    if (c->src == PD_SRC_GAUSS_PATCH) {
+        if (!s.amp) PD_CUDA(g, cudaMalloc(&s.amp, sizeof(double) * s.I.n_patch));
+        PD_CUDA(g, cudaMemcpyAsync(s.amp, c->src_amp, sizeof(double) * s.I.n_patch, cudaMemcpyHostToDevice, g->stream));
+    }
+    s.coef = *c;
+    s.coef.src_amp = nullptr;
+    s.I.sol = c->sol; s.I.tkind = c->tkind; s.I.tc = c->tc;
+    s.I.has_tsrc = (c->src != PD_SRC_NONE && c->tkind != PD_TIME_CONST) ? 1 : 0;
+    PD_CUDA(g, cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long) * 4, g->stream));
+    PD_CUDA(g, cudaMemsetAsync(g->err, 0, sizeof(int) * 4, g->stream));
+    PD_CUDA(g, launch_precompute(s.I, *c, s.amp, s.rec, s.d.prec, g->acc, g->acc + 1, g->stream));
+    g->launches += 3;
+    unsigned long long h[2];
+    int herr = 0;
+    PD_CUDA(g, cudaMemcpyAsync(h, g->acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    PD_CUDA(g, cudaMemcpyAsync(&herr, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    PD_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (herr & ERR_JACOBIAN) return fail(g, PD_EINVAL, "singular mapping or non-finite coefficients");
+    double rate, mrate;
+    std::memcpy(&rate, &h[0], sizeof(double));
+    std::memcpy(&mrate, &h[1], sizeof(double));
+    if (!(rate > 0)) return fail(g, PD_EINVAL, "zero operator: no micro step bound");
+    s.dt = s.d.cfl_micro / rate;
+    s.tau = s.d.k_micro * s.dt;
+    s.dtm_sugg = mrate > 0 ? 0.5 / mrate : s.tau;
+    s.I.dt = s.dt; s.I.tau = s.tau;
+    // cross term present unless K^{xi eta} vanishes identically (orthogonal map, K = d m I,
+    // or a separable map with M12 = 0)
+    bool separable = s.d.map != PD_MAP_POLAR;
+    s.I.has_cross = (c->M12 != 0.0 || (!separable && c->M11 != c->M22)) ? 1 : 0;
+    s.coef_set = true;
+    for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+    g->gcache.clear();
+    return PD_OK;
+}
+
+pd_status pd_query(const pd_grid* gc, int inst, pd_info* o)
+{
+    pd_grid* g = const_cast<pd_grid*>(gc);
+    pd_status rc = check_inst(g, inst);
+    if (rc) return rc;
+    if (!o) return fail(g, PD_EINVAL, "null output");
+    const Inst& s = g->inst[inst];
+    std::memset(o, 0, sizeof(*o));
+    o->n_patch = s.I.n_patch;
+    o->n_macro = s.I.nxp * s.I.nyp;
+    o->nxp = s.I.nxp; o->nyp = s.I.nyp;
+    o->m_xi = s.d.m_xi; o->m_eta = s.d.m_eta; o->k_micro = s.d.k_micro; o->prec = s.d.prec;
+    o->u_offset = s.I.u_off;
+    o->patch_offset = s.I.p_off;
+    o->dt_micro = s.dt; o->tau = s.tau; o->dt_macro_suggested = s.dtm_sugg;
+    layout(g, s, *o);
+    return PD_OK;
+}
+
+pd_status pd_sizes(const pd_grid* g, long long* nm, long long* np, size_t* sb)
+{
+    if (!g) return PD_EINVAL;
+    if (nm) *nm = g->n_macro_total;
+    if (np) *np = g->n_patch_total;
+    if (sb) *sb = g->state_bytes;
+    return PD_OK;
+}
+
+pd_status pd_get_coeffs(pd_grid* g, int inst, double* out)
+{
+    pd_status rc = check_inst(g, inst);
+    if (rc) return rc;
+    Inst& s = g->inst[inst];
+    if (!s.coef_set) return fail(g, PD_ESTATE, "coefficients not set");
+    if (!out) return fail(g, PD_EINVAL, "null output");
+    PD_CUDA(g, launch_get_coeffs(s.I, s.d.prec, out, g->stream));
+    g->launches += 1;
+    return PD_OK;
+}
+
+pd_status pd_init_field(pd_grid* g, int inst, int kind, const double* prm, int n_prm, double t, double* U)
+{
+    pd_status rc = check_inst(g, inst);
+    if (rc) return rc;
+    Inst& s = g->inst[inst];
+    if (!U) return fail(g, PD_EINVAL, "null field");
+    if (kind < 0 || kind > 4) return fail(g, PD_EINVAL, "unknown init kind");
+    if ((kind == PD_INIT_EXACT) && !s.coef_set) return fail(g, PD_ESTATE, "EXACT needs pd_set_coeffs");
+    double mu[8] = { 0 };
+    if (kind == PD_INIT_BESSEL) {
+        if (!prm || n_prm < 3 || prm[0] < 1 || prm[0] > 8 || n_prm < 3 + (int)prm[0])
+            return fail(g, PD_EINVAL, "BESSEL needs {n_modes<=8, r_in, r_out, a_1..a_n}");
+        for (int k = 1; k <= (int)prm[0]; ++k) mu[k - 1] = first_root(k, prm[1], prm[2]);
+    }
+    if (kind == PD_INIT_ANNULUS_POLY && (!prm || n_prm < 2)) return fail(g, PD_EINVAL, "ANNULUS_POLY needs {r_in, r_out}");
+    pd_coeff_desc c = s.coef_set ? s.coef : pd_coeff_desc{};
+    if (!s.coef_set) c.d0 = 1.0;
+    PD_CUDA(g, launch_init_field(s.I, c, kind, prm, n_prm, mu, t, U + s.I.u_off, g->stream));
+    g->launches += 1;
+    return PD_OK;
+}
+
+pd_status pd_lift(pd_grid* g, const double* U, double t, void* state)
+{
+    if (!g) return PD_EINVAL;
+    if (!U || !state) return fail(g, PD_EINVAL, "null pointer");
+    if (((uintptr_t)state) & 255) return fail(g, PD_EINVAL, "state buffer must be 256-byte aligned");
+    pd_status rc = all_coeffs_set(g);
+    if (rc) return rc;
+    for (auto& s : g->inst) {
+        pd_info lay;
+        layout(g, s, lay);
+        PD_CUDA(g, launch_lift(s.I, nullptr, s.d.prec, U + s.I.u_off, t, (char*)state, lay, g->stream));
+        g->launches += 2;
+    }
+    return PD_OK;
+}
+
+pd_status pd_micro_burst(pd_grid* g, void* state, double t, int k_steps)
+{
+    if (!g) return PD_EINVAL;
+    if (!state) return fail(g, PD_EINVAL, "null state");
+    if (k_steps < 0 || k_steps > kMaxK) return fail(g, PD_EINVAL, "k_steps must be in [0, 4096]");
+    pd_status rc = all_coeffs_set(g);
+    if (rc) return rc;
+    if (k_steps == 0) return PD_OK;
+    for (auto& s : g->inst) {
+        pd_info lay;
+        layout(g, s, lay);
+        PD_CUDA(g, launch_burst(s.I, nullptr, s.d.prec, (char*)state, lay, t, k_steps, g->stream));
+        g->launches += 2;
+    }
+    return PD_OK;
+}
+
+pd_status pd_restrict(pd_grid* g, const void* state, double* dU)
+{
+    if (!g) return PD_EINVAL;
+    if (!state || !dU) return fail(g, PD_EINVAL, "null pointer");
+    pd_status rc = all_coeffs_set(g);
+    if (rc) return rc;
+    for (auto& s : g->inst) {
+        pd_info lay;
+        layout(g, s, lay);
+        PD_CUDA(g, launch_restrict(s.I, s.d.prec, (const char*)state, lay, dU, g->stream));
+        g->launches += 1;
+    }
+    return PD_OK;
+}
+
+pd_status pd_project(pd_grid* g, double* U, const double* dU, double t, double dtm)
+{
+    if (!g) return PD_EINVAL;
+    if (!U || !dU) return fail(g, PD_EINVAL, "null pointer");
+    if (!(dtm > 0)) return fail(g, PD_EINVAL, "dt_macro must be positive");
+    pd_status rc = all_coeffs_set(g);
+    if (rc) return rc;
+    for (auto& s : g->inst) {
+        PD_CUDA(g, launch_project(s.I, U + s.I.u_off, dU, t, dtm, g->stream));
+        g->launches += 1;
+    }
+    return PD_OK;
+}
+
+pd_status pd_step(pd_grid* g, double* U, double t0, double dt_macro, int n_macro)
+{
+    if (!g) return PD_EINVAL;
+    if (!U) return fail(g, PD_EINVAL, "null field");
+    if (n_macro < 0) return fail(g, PD_EINVAL, "n_macro must be >= 0");
+    pd_status rc = all_coeffs_set(g);
+    if (rc) return rc;
+    if (n_macro == 0) return PD_OK;
+    cudaSetDevice(g->device);
+    std::vector<double> dtm(g->inst.size());
+    for (size_t k = 0; k < g->inst.size(); ++k) dtm[k] = dt_macro > 0 ? dt_macro : g->inst[k].dtm_sugg;
+    bool all_fused = true;
+    for (auto& s : g->inst) all_fused &= fused_supported(s.I);
+    if (!all_fused) return step_fallback(g, U, t0, dtm, n_macro);
+    rc = ensure_step_buffers(g, n_macro);
+    if (rc) return rc;
+    // per-step time tables (s(t) differences, T, T_next) for every instance
+    size_t tab_off = 0;
+    for (size_t k = 0; k < g->inst.size(); ++k) {
+        Inst& s = g->inst[k];
+        PD_CUDA(g, launch_time_table(s.I, t0, dtm[k], n_macro, g->tab + tab_off, g->stream));
+        g->launches += 1;
+        tab_off += (size_t)n_macro * (s.I.K + kTabExtra);
+    }
+    if (!g->graphs) {
+        int nl = 0;
+        rc = enqueue_steps(g, U, n_macro, dtm, g->stream, nl);
+        g->launches += nl;
+        return rc;
+    }
+    // graphs bake kernel arguments: key on the field pointer, the step count and the macro steps
+    GraphKey key{ (uintptr_t)U, n_macro, dtm };
+    auto it = g->gcache.find(key);
+    if (it == g->gcache.end()) {
+        GraphEntry ge;
+        PD_CUDA(g, cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+        int nl = 0;
+        rc = enqueue_steps(g, U, n_macro, dtm, g->cap, nl);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(g, e, "graph instantiate"); }
+        ge.graph = graph;
+        ge.n_nodes = nl;
+        it = g->gcache.emplace(key, ge).first;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (g->timing) {
+        for (cudaEvent_t* e : { &e0, &e1 }) {
+            if (!g->tfree.empty()) { *e = g->tfree.back(); g->tfree.pop_back(); }
+            else PD_CUDA(g, cudaEventCreate(e));
+        }
+        PD_CUDA(g, cudaEventRecord(e0, g->stream));
+    }
+    PD_CUDA(g, cudaGraphLaunch(it->second.exec, g->stream));
+    g->launches += it->second.n_nodes;
+    if (g->timing) {
+        PD_CUDA(g, cudaEventRecord(e1, g->stream));
+        g->tev.emplace_back(e0, e1);
+        int nf = 0;
+        for (auto& s2 : g->inst) if (fused_supported(s2.I)) nf += n_macro;
+        g->t_launches += nf;
+    }
+    return PD_OK;
+}
+
+pd_status pd_set_timing(pd_grid* g, int enabled)
+{
+    if (!g) return PD_EINVAL;
+    double ms;
+    long long n;
+    pd_get_timing(g, &ms, &n);
+    g->timing = enabled != 0;
+    g->t_ms = 0.0;
+    g->t_launches = 0;
+    return PD_OK;
+}
+
+pd_status pd_get_timing(pd_grid* g, double* ms, long long* n)
+{
+    if (!g) return PD_EINVAL;
+    for (auto& pr : g->tev) {
+        PD_CUDA(g, cudaEventSynchronize(pr.second));
+        float f = 0.f;
+        PD_CUDA(g, cudaEventElapsedTime(&f, pr.first, pr.second));
+        g->t_ms += f;
+        g->tfree.push_back(pr.first);
+        g->tfree.push_back(pr.second);
+    }
+    g->tev.clear();
+    if (ms) *ms = g->t_ms;
+    if (n) *n = g->t_launches;
+    return PD_OK;
+}
+
+pd_status pd_sync(pd_grid* g)
+{
+    if (!g) return PD_EINVAL;
+    PD_CUDA(g, cudaStreamSynchronize(g->stream));
+    int h = 0;
+    PD_CUDA(g, cudaMemcpy(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & ERR_NONFINITE) {
+        cudaMemset(g->err, 0, sizeof(int));
+        return fail(g, PD_ENUMERIC, "non-finite restricted change (unstable macro or micro step?)");
+    }
+    return PD_OK;
+}
+
+namespace {
+uint64_t desc_hash(const pd_grid* g)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (auto& s : g->inst) {
+        const unsigned char* p = reinterpret_cast<const unsigned char*>(&s.d);
+        for (size_t k = 0; k < sizeof(s.d); ++k) { h ^= p[k]; h *= 1099511628211ull; }
+    }
+    return h;
+}
+const char kMagic[8] = { 'P', 'D', 'C', 'K', 'P', 'T', '0', '1' };
+}  // namespace
+
+pd_status pd_save_checkpoint(pd_grid* g, const double* U, double t, long long step, const char* path)
+{
+    if (!g || !U || !path) return fail(g, PD_EINVAL, "null argument");
+    std::vector<double> h((size_t)g->n_macro_total);
+    PD_CUDA(g, cudaMemcpyAsync(h.data(), U, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
+    PD_CUDA(g, cudaStreamSynchronize(g->stream));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(g, PD_EINVAL, std::string("cannot open ") + path);
+    uint64_t hash = desc_hash(g);
+    long long n = g->n_macro_total;
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&hash, 8, 1, f) == 1 && std::fwrite(&n, 8, 1, f) == 1
+           && std::fwrite(&t, 8, 1, f) == 1 && std::fwrite(&step, 8, 1, f) == 1
+           && std::fwrite(h.data(), sizeof(double), h.size(), f) == h.size();
+    ok &= std::fclose(f) == 0;
+    return ok ? PD_OK : fail(g, PD_EINVAL, "short write");
+}
+
+pd_status pd_load_checkpoint(pd_grid* g, double* U, double* t, long long* step, const char* path)
+{
+    if (!g || !U || !path) return fail(g, PD_EINVAL, "null argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(g, PD_EINVAL, std::string("cannot open ") + path);
+    char mg[8];
+    uint64_t hash = 0;
+    long long n = 0, st = 0;
+    double tt = 0;
+    bool ok = std::fread(mg, 1, 8, f) == 8 && std::fread(&hash, 8, 1, f) == 1 && std::fread(&n, 8, 1, f) == 1
+           && std::fread(&tt, 8, 1, f) == 1 && std::fread(&st, 8, 1, f) == 1;
+    if (!ok || std::memcmp(mg, kMagic, 8) != 0) { std::fclose(f); return fail(g, PD_EINVAL, "not a checkpoint"); }
+    if (hash != desc_hash(g) || n != g->n_macro_total) { std::fclose(f); return fail(g, PD_EINVAL, "checkpoint of another grid"); }
+    std::vector<double> h((size_t)n);
+    ok = std::fread(h.data(), sizeof(double), h.size(), f) == h.size();
+    std::fclose(f);
+    if (!ok) return fail(g, PD_EINVAL, "truncated checkpoint");
+    PD_CUDA(g, cudaMemcpyAsync(U, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, g->stream));
+    PD_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (t) *t = tt;
+    if (step) *step = st;
+    return PD_OK;
+}
+
+}  // extern "C"

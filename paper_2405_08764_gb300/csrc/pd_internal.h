@@ -1,0 +1,200 @@
+// Internal definitions of the GB300 patch-dynamics library.
+//
+// Device-side layout
+//   * coefficient records: one 8-value record per micro point (alpha, beta,
+//     gamma, nu, omega, phi, G * patch amplitude, 0), stored in "strip image"
+//     order: for patch row jr and micro row b, the micro columns of all
+//     patches of that row are contiguous:
+//        rec[((jr * my + b) * ncols + ic) * mx + a]
+//     so a warp whose lanes hold consecutive micro columns of consecutive
+//     patches reads one contiguous run per micro row.
+//   * macro field U: FP64, U[j * nxp + i] per instance.
+//   * micro state (separate C-ABI passes): see include/pd.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pd.h"
+
+namespace pd {
+
+constexpr int kMaxK = 4096;      // micro steps per burst
+constexpr int kMaxM = 32;        // micro points per side (one warp spans a patch row)
+constexpr int kTabExtra = 3;     // time table row: ds_0..ds_{K-1}, s(T), T, T_next
+
+// Per-instance constants used by the kernels (FP64; kernels convert).
+struct InstDev {
+    int n_xi, n_eta, periodic, nxp, nyp, ncols, nrows, i0;
+    int mx, my, K, conv, restrict_mode, tkind, sol, map;
+    int n_patch, n_bnd;
+    int has_cross, has_tsrc;
+    double xi0, eta0, Dx, Dy, hx, hy, dx, dy;
+    double dt, tau, tc;
+    double map_p[4];
+    double xi1, eta1;
+    double lw[9][9];             // monomial coefficients of the 3x3 interpolant, see poly_weights
+    long long u_off;             // offset of this instance in U (doubles)
+    long long p_off;             // offset in patches (dU, micro state)
+    const void* rec;             // coefficient records (float or double, 8 per point)
+    const int2* bnd_ij;          // boundary nodes (i, j)
+    const double2* bnd_xy;       // their physical coordinates
+    int* err;                    // device error flags
+};
+
+// Monomial coefficients of the biquadratic interpolant P(s, t) of eq.
+// (Lagrange_2D) around the patch centre, c_kl of s^k t^l, plus the lift
+// constant C0 of eq. (C_0):
+//   index 0: C0, 1: c10, 2: c01, 3: c20, 4: c11, 5: c02, 6: c21, 7: c12, 8: c22.
+// The lift of eq. (Lifting) with central macro differences is
+//   u0 = C0 + c10 s + c01 t + c20 s^2 + c11 s t + c02 t^2.
+template <typename real>
+struct Poly {
+    real C0, c10, c01, c20, c11, c02, c21, c12, c22;
+};
+
+template <typename real>
+struct PatchGeo {
+    real hx, hy, dx, dy;
+    int nx, ny;   // nano intervals (m - 1)
+    __device__ __forceinline__ real s(int a) const { return real(-0.5) * hx + real(a) * dx; }
+    __device__ __forceinline__ real t(int b) const { return real(-0.5) * hy + real(b) * dy; }
+};
+
+// d/dxi of (P - u0): the part of the Neumann data of eq. (edge) that the
+// quadratic lift does not carry.
+template <typename real>
+__device__ __forceinline__ real edge_gap_xi(const Poly<real>& c, real s, real t)
+{
+    return t * (real(2) * c.c21 * s + c.c12 * t + real(2) * c.c22 * s * t);
+}
+// d/deta of (P - u0)
+template <typename real>
+__device__ __forceinline__ real edge_gap_eta(const Poly<real>& c, real s, real t)
+{
+    return s * (c.c21 * s + real(2) * c.c12 * t + real(2) * c.c22 * s * t);
+}
+
+// Ghost-point value minus the quadratic lift extended to the ghost position
+// (a', b'), for the ghost rule: eta-ghost rows from the bottom/top Neumann data,
+// then xi-ghost columns (corners included) from the left/right data.
+template <typename real>
+__device__ __forceinline__ real ghost_offset(const Poly<real>& c, const PatchGeo<real>& g, int ap, int bp)
+{
+    real v = real(0);
+    int ain = ap;
+    if (ap < 0) { v -= real(2) * g.dx * edge_gap_xi(c, real(-0.5) * g.hx, g.t(bp)); ain = 1; }
+    else if (ap > g.nx) { v += real(2) * g.dx * edge_gap_xi(c, real(0.5) * g.hx, g.t(bp)); ain = g.nx - 1; }
+    if (bp < 0) v -= real(2) * g.dy * edge_gap_eta(c, g.s(ain), real(-0.5) * g.hy);
+    else if (bp > g.ny) v += real(2) * g.dy * edge_gap_eta(c, g.s(ain), real(0.5) * g.hy);
+    return v;
+}
+
+// Micro operator weights at one point (not scaled by dt).
+template <typename real>
+struct PointW {
+    real wE, wW, wN, wS, wX, wC;   // neighbour / centre weights of L_h
+    real ox, oy;                   // offset of the first-difference point (upwind: -+d/2)
+};
+
+template <typename real>
+__device__ __forceinline__ PointW<real> point_weights(real al, real be, real ga, real nu, real om, real ph,
+                                                      real dx, real dy, int conv)
+{
+    PointW<real> w;
+    real ax = al / (dx * dx), gy = ga / (dy * dy);
+    w.wX = be / (real(4) * dx * dy);
+    w.wC = -real(2) * ax - real(2) * gy + ph;
+    if (conv == PD_CONV_CENTRAL) {
+        w.wE = ax - nu / (real(2) * dx); w.wW = ax + nu / (real(2) * dx);
+        w.wN = gy - om / (real(2) * dy); w.wS = gy + om / (real(2) * dy);
+        w.ox = real(0); w.oy = real(0);
+    } else {
+        if (nu > real(0)) { w.wW = ax + nu / dx; w.wE = ax; w.wC -= nu / dx; w.ox = real(-0.5) * dx; }
+        else              { w.wE = ax - nu / dx; w.wW = ax; w.wC += nu / dx; w.ox = real(0.5) * dx; }
+        if (om > real(0)) { w.wS = gy + om / dy; w.wN = gy; w.wC -= om / dy; w.oy = real(-0.5) * dy; }
+        else              { w.wN = gy - om / dy; w.wS = gy; w.wC += om / dy; w.oy = real(0.5) * dy; }
+    }
+    return w;
+}
+
+// Burst forcing r = L_h(u0 with its ghost points) + s(T) G at micro point (a, b),
+// evaluated in closed form: the centred second and cross differences of the
+// quadratic lift are exact, a two-point difference of it is its derivative at
+// the midpoint, and every ghost neighbour adds weight * ghost_offset.  No
+// difference of nearly equal lifted values is formed, so FP32 evaluation keeps
+// full relative precision.
+template <typename real>
+__device__ __forceinline__ real burst_forcing(const Poly<real>& c, const PatchGeo<real>& g, int a, int b,
+                                              real al, real be, real ga, real nu, real om, real ph,
+                                              real G, real sT, const PointW<real>& w)
+{
+    real s = g.s(a), t = g.t(b);
+    real u0 = c.C0 + s * (c.c10 + s * c.c20 + t * c.c11) + t * (c.c01 + t * c.c02);
+    real ux = c.c10 + real(2) * c.c20 * (s + w.ox) + c.c11 * t;
+    real uy = c.c01 + real(2) * c.c02 * (t + w.oy) + c.c11 * s;
+    real r = real(2) * c.c20 * al + c.c11 * be + real(2) * c.c02 * ga - nu * ux - om * uy + ph * u0 + sT * G;
+    if (a == 0) r += w.wW * ghost_offset(c, g, -1, b);
+    if (a == g.nx) r += w.wE * ghost_offset(c, g, g.nx + 1, b);
+    if (b == 0) r += w.wS * ghost_offset(c, g, a, -1);
+    if (b == g.ny) r += w.wN * ghost_offset(c, g, a, g.ny + 1);
+    if (be != real(0) && (a == 0 || a == g.nx || b == 0 || b == g.ny)) {
+        auto out = [&](int ap, int bp) { return ap < 0 || ap > g.nx || bp < 0 || bp > g.ny; };
+        if (out(a + 1, b + 1)) r += w.wX * ghost_offset(c, g, a + 1, b + 1);
+        if (out(a - 1, b - 1)) r += w.wX * ghost_offset(c, g, a - 1, b - 1);
+        if (out(a + 1, b - 1)) r -= w.wX * ghost_offset(c, g, a + 1, b - 1);
+        if (out(a - 1, b + 1)) r -= w.wX * ghost_offset(c, g, a - 1, b + 1);
+    }
+    return r;
+}
+
+// time factor s(t) of the source
+__device__ __forceinline__ double time_factor(int kind, double c, double t)
+{
+    if (kind == PD_TIME_EXP) return exp(c * t);
+    if (kind == PD_TIME_SIN) return sin(c * t);
+    return 1.0;
+}
+
+__device__ __forceinline__ double exact_solution(int sol, double x, double y, double t)
+{
+    if (sol == PD_SOL_EXP_XYT) return exp(x + y + t);
+    if (sol == PD_SOL_SINPROD_DECAY) return exp(-t) * sinpi(x) * sinpi(y);
+    return 0.0;
+}
+
+enum ErrBits { ERR_NONFINITE = 1, ERR_JACOBIAN = 2, ERR_COEF = 4 };
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers (defined in the .cu files)
+struct StepLaunch {
+    const InstDev* inst_dev;   // device copy
+    const InstDev* inst_host;  // host copy
+    const double* Uc;
+    double* Un;
+    const double* tab;         // time table row of this macro step
+    double dtm;
+};
+
+cudaError_t launch_precompute(const InstDev& I, const pd_coeff_desc& c, const double* amp_dev,
+                              void* rec, int prec, unsigned long long* rate_max,
+                              unsigned long long* macro_rate_max, cudaStream_t st);
+cudaError_t launch_get_coeffs(const InstDev& I, int prec, double* out, cudaStream_t st);
+cudaError_t launch_init_field(const InstDev& I, const pd_coeff_desc& c, int kind, const double* prm,
+                              int n_prm, const double* mu, double t, double* U, cudaStream_t st);
+cudaError_t launch_time_table(const InstDev& I, double t0, double dtm, int n_steps, double* tab,
+                              cudaStream_t st);
+cudaError_t launch_fused_step(const InstDev& I, const InstDev* I_dev, int prec, const double* Uc,
+                              double* Un, const double* tab_row, double dtm, cudaStream_t st,
+                              int* n_launch);
+cudaError_t launch_lift(const InstDev& I, const InstDev* I_dev, int prec, const double* U, double t,
+                        char* state, const pd_info& lay, cudaStream_t st);
+cudaError_t launch_burst(const InstDev& I, const InstDev* I_dev, int prec, char* state,
+                         const pd_info& lay, double t, int k_steps, cudaStream_t st);
+cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const pd_info& lay,
+                            double* dU, cudaStream_t st);
+cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm,
+                           cudaStream_t st);
+bool fused_supported(const InstDev& I);
+
+}  // namespace pd

@@ -1,0 +1,539 @@
+// Hot path of one macro step (Section 3.3): edge data + lift, micro burst,
+// restriction and projective forward Euler.
+//
+// Resident micro burst.  A patch of M x M micro points lives in the registers of
+// M consecutive lanes of one warp: lane a holds micro column a (M values), and
+// P = 32 / M patches share a warp.  Neighbouring columns are exchanged with
+// warp shuffles, neighbouring rows are in the same thread, so a micro step needs
+// no shared memory and no barrier.  The Neumann ghost points of the departure
+// w = u - u_lift are mirrors (their edge data is carried by the lift, see
+// burst_forcing), so they are folded into the stencil weights once per burst.
+// The stencil weights, the per-point forcing and the source factor stay in
+// registers for all K micro steps.
+//
+// Precision: the monomial coefficients of the interpolant come from the FP64
+// macro field with FP64 dot products (one coefficient per lane); the burst runs
+// in `real` (float for PD_FP32, double for PD_FP64); the restricted change is
+// divided by tau and accumulated into U in FP64.
+#include "pd_internal.h"
+
+#include <math.h>
+
+namespace pd {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename real> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4; };
+
+template <typename real>
+__device__ __forceinline__ void load_record(const real* __restrict__ rec, long long idx, real v[8])
+{
+    using V = typename Vec4<real>::T;
+    const V* p = reinterpret_cast<const V*>(rec + idx * 8);
+    V lo = __ldg(p), hi = __ldg(p + 1);
+    v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+    v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+}
+
+template <>
+__device__ __forceinline__ void load_record<double>(const double* __restrict__ rec, long long idx, double v[8])
+{
+    const double2* p = reinterpret_cast<const double2*>(rec + idx * 8);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double2 q = __ldg(p + k);
+        v[2 * k] = q.x; v[2 * k + 1] = q.y;
+    }
+}
+
+__device__ __forceinline__ int wrap_col(const InstDev& I, int i)
+{
+    if (!I.periodic) return i;
+    return i < 0 ? i + I.nxp : (i >= I.nxp ? i - I.nxp : i);
+}
+
+enum { MODE_FUSED = 0, MODE_BURST = 1 };
+
+// One warp = P patches of one patch row.  MODE_FUSED: lift -> burst -> restrict
+// -> project for one macro step, writing U at T_next into Un.  MODE_BURST: load
+// (w, r) from the micro state, run k_steps, store w.
+template <int M, bool CROSS, bool TSRC, typename real, int MODE>
+__global__ void __launch_bounds__(128)
+patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __restrict__ Un,
+                  const double* __restrict__ tab, double dtm, int k_steps,
+                  real* __restrict__ st_w, const real* __restrict__ st_r, int n_item_warps)
+{
+    constexpr int P = 32 / M;
+    constexpr int NC = (9 + M - 1) / M;
+    __shared__ double lw_s[9][9];
+    __shared__ double tinfo[3];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    real* ds_s = reinterpret_cast<real*>(dyn_smem);   // TSRC: K entries
+
+    const int K = (MODE == MODE_FUSED) ? I.K : k_steps;
+    if (MODE == MODE_FUSED)
+        for (int t = threadIdx.x; t < 81; t += blockDim.x) lw_s[t / 9][t % 9] = I.lw[t / 9][t % 9];
+    if (TSRC)
+        for (int t = threadIdx.x; t < K; t += blockDim.x) ds_s[t] = (real)tab[t];
+    if (MODE == MODE_FUSED && threadIdx.x < 3) tinfo[threadIdx.x] = tab[K + threadIdx.x];
+    __syncthreads();
+
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (warp >= n_item_warps) {
+        if (MODE != MODE_FUSED) return;
+        // boundary nodes: Dirichlet data at T_next
+        int k = (warp - n_item_warps) * 32 + lane;
+        if (k < I.n_bnd) {
+            int2 ij = I.bnd_ij[k];
+            double2 xy = I.bnd_xy[k];
+            Un[(long long)ij.y * I.nxp + ij.x] = exact_solution(I.sol, xy.x, xy.y, tinfo[2]);
+        }
+        return;
+    }
+
+    const int wpr = (I.ncols + P - 1) / P;
+    const int jr = warp / wpr;
+    const int ic0 = (warp - jr * wpr) * P;
+    const int q = lane / M;
+    const int a = lane - q * M;
+    const int ic = ic0 + q;
+    const bool active = (q < P) && (ic < I.ncols);
+    const int icl = active ? ic : (I.ncols - 1);
+    const int i = I.i0 + icl, j = 1 + jr;
+    const int qbase = (q < P ? q : P - 1) * M;
+
+    PatchGeo<real> g;
+    g.hx = (real)I.hx; g.hy = (real)I.hy; g.dx = (real)I.dx; g.dy = (real)I.dy;
+    g.nx = M - 1; g.ny = M - 1;
+
+    Poly<real> c = {};
+    double bias = 0.0;
+    real w[M];
+    real Rr[M];
+    if (MODE == MODE_FUSED) {
+        // 3x3 macro stencil, st[(p+1)*3 + (q+1)] = U_{i+p, j+q}
+        double stv[9];
+#pragma unroll
+        for (int pp = -1; pp <= 1; ++pp) {
+            int ii = wrap_col(I, i + pp);
+#pragma unroll
+            for (int qq = -1; qq <= 1; ++qq) stv[(pp + 1) * 3 + (qq + 1)] = __ldg(Uc + (long long)(j + qq) * I.nxp + ii);
+        }
+        // one monomial coefficient per lane (FP64 dot product), then broadcast
+        double ck[NC];
+        real ckr[NC];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            int k = a + r * M;
+            double acc = 0.0;
+            if (k < 9) {
+#pragma unroll
+                for (int jj = 0; jj < 9; ++jj) acc = fma(lw_s[k][jj], stv[jj], acc);
+            }
+            ck[r] = acc;
+            ckr[r] = (real)acc;
+        }
+        real cv[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) cv[k] = __shfl_sync(FULL, ckr[k / M], (qbase + k % M) & 31);
+        c.C0 = cv[0]; c.c10 = cv[1]; c.c01 = cv[2]; c.c20 = cv[3]; c.c11 = cv[4];
+        c.c02 = cv[5]; c.c21 = cv[6]; c.c12 = cv[7]; c.c22 = cv[8];
+        if (I.restrict_mode == PD_RESTRICT_MACRO) {
+            // trapezoid average of the lift minus U_ij = (dxi^2 c20 + deta^2 c02) / 6
+            double c20 = __shfl_sync(FULL, ck[3 / M], (qbase + 3 % M) & 31);
+            double c02 = __shfl_sync(FULL, ck[5 / M], (qbase + 5 % M) & 31);
+            bias = (I.dx * I.dx * c20 + I.dy * I.dy * c02) / 6.0;
+        }
+    }
+
+    // per-point stencil weights (dt-scaled, ghost mirrors folded), forcing, source
+    real cE[M], cW[M], cN[M], cS[M], cC[M], cX[M], Gs[M];
+    const real dt = (real)I.dt;
+    const real sT = (MODE == MODE_FUSED) ? (real)tinfo[0] : real(0);
+    const real* rec = static_cast<const real*>(I.rec);
+    const long long rowstride = (long long)I.ncols * M;
+    const long long base = (long long)jr * M * rowstride + (long long)icl * M + a;
+    const long long sbase = ((long long)I.p_off + (long long)jr * I.ncols + icl) * (M * M) + a;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+        real v[8];
+        load_record<real>(rec, base + b * rowstride, v);
+        PointW<real> pw = point_weights<real>(v[0], v[1], v[2], v[3], v[4], v[5], g.dx, g.dy, I.conv);
+        real r;
+        if (MODE == MODE_FUSED) {
+            r = burst_forcing<real>(c, g, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
+            w[b] = real(0);
+        } else {
+            r = st_r[sbase + b * M];
+            w[b] = st_w[sbase + b * M];
+        }
+        real e = dt * pw.wE, ww = dt * pw.wW, n = dt * pw.wN, s = dt * pw.wS, x = dt * pw.wX;
+        real cc = real(1) + dt * pw.wC;
+        if (a == 0) { e += ww; ww = real(0); }
+        if (a == M - 1) { ww += e; e = real(0); }
+        if (b == 0) { n += s; s = real(0); }
+        if (b == M - 1) { s += n; n = real(0); }
+        if (a == 0 || a == M - 1 || b == 0 || b == M - 1) x = real(0);
+        if (!active) { e = ww = n = s = x = cc = real(0); r = real(0); v[6] = real(0); w[b] = real(0); }
+        cE[b] = e; cW[b] = ww; cN[b] = n; cS[b] = s; cX[b] = x; cC[b] = cc;
+        Rr[b] = dt * r;
+        Gs[b] = dt * v[6];
+    }
+
+    // K forward-Euler micro steps, all in registers
+    for (int k = 0; k < K; ++k) {
+        const real ds = TSRC ? ds_s[k] : real(0);
+        real e[M], v[M], d[M], nw[M];
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            e[b] = __shfl_down_sync(FULL, w[b], 1);
+            v[b] = __shfl_up_sync(FULL, w[b], 1);
+        }
+        if (CROSS) {
+#pragma unroll
+            for (int b = 0; b < M; ++b) d[b] = e[b] - v[b];
+        }
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            real acc = fma(cC[b], w[b], Rr[b]);
+            acc = fma(cE[b], e[b], acc);
+            acc = fma(cW[b], v[b], acc);
+            if (b + 1 < M) acc = fma(cN[b], w[b + 1], acc);
+            if (b > 0) acc = fma(cS[b], w[b - 1], acc);
+            if (CROSS && b > 0 && b + 1 < M) acc = fma(cX[b], d[b + 1] - d[b - 1], acc);
+            if (TSRC) acc = fma(ds, Gs[b], acc);
+            nw[b] = acc;
+        }
+#pragma unroll
+        for (int b = 0; b < M; ++b) w[b] = nw[b];
+    }
+
+    if (MODE == MODE_BURST) {
+        if (active) {
+#pragma unroll
+            for (int b = 0; b < M; ++b) st_w[sbase + b * M] = w[b];
+        }
+        return;
+    }
+
+    // trapezoid restriction of the departure, then eq. (Time_Derivative) and
+    // eq. (Extrapolation) in FP64
+    real col = real(0.5) * (w[0] + w[M - 1]);
+#pragma unroll
+    for (int b = 1; b < M - 1; ++b) col += w[b];
+    if (a == 0 || a == M - 1) col *= real(0.5);
+    if (!active) col = real(0);
+#pragma unroll
+    for (int off = 1; off < M; off <<= 1) {
+        real o = __shfl_down_sync(FULL, col, off);
+        if (a + off < M) col += o;
+    }
+    if (active && a == 0) {
+        double dU = (double)col / (double)((M - 1) * (M - 1)) + bias;
+        if (!isfinite(dU)) atomicOr(I.err, ERR_NONFINITE);
+        long long node = (long long)j * I.nxp + i;
+        Un[node] = Uc[node] + dtm * (dU / I.tau);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Generic kernels for the separate C-ABI passes (any m_xi, m_eta <= 32):
+// one block per patch.
+
+__device__ __forceinline__ void patch_ij(const InstDev& I, int p, int& i, int& j, int& ic, int& jr)
+{
+    ic = p % I.ncols; jr = p / I.ncols;
+    i = I.i0 + ic; j = 1 + jr;
+}
+
+__device__ __forceinline__ long long rec_index(const InstDev& I, int jr, int ic, int a, int b)
+{
+    return ((long long)(jr * I.my + b) * I.ncols + ic) * I.mx + a;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(128)
+lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restrict__ tab, double* u0,
+            real* r_out, real* w_out, double* edge, double* bias_out, int edge_stride)
+{
+    __shared__ double cs[9];
+    const int p = blockIdx.x;
+    int i, j, ic, jr;
+    patch_ij(I, p, i, j, ic, jr);
+    if (threadIdx.x < 9) {
+        double acc = 0.0;
+        for (int pp = -1; pp <= 1; ++pp)
+            for (int qq = -1; qq <= 1; ++qq)
+                acc = fma(I.lw[threadIdx.x][(pp + 1) * 3 + qq + 1], U[(long long)(j + qq) * I.nxp + wrap_col(I, i + pp)], acc);
+        cs[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    Poly<double> cd = { cs[0], cs[1], cs[2], cs[3], cs[4], cs[5], cs[6], cs[7], cs[8] };
+    Poly<real> cr = { (real)cs[0], (real)cs[1], (real)cs[2], (real)cs[3], (real)cs[4], (real)cs[5],
+                      (real)cs[6], (real)cs[7], (real)cs[8] };
+    PatchGeo<double> gd = { I.hx, I.hy, I.dx, I.dy, I.mx - 1, I.my - 1 };
+    PatchGeo<real> gr = { (real)I.hx, (real)I.hy, (real)I.dx, (real)I.dy, I.mx - 1, I.my - 1 };
+    const real* rec = static_cast<const real*>(I.rec);
+    const real sT = (real)tab[0];
+    const long long pg = (long long)I.p_off + p;
+    const int mm = I.mx * I.my;
+    for (int t = threadIdx.x; t < mm; t += blockDim.x) {
+        int a = t % I.mx, b = t / I.mx;
+        real v[8];
+        for (int k = 0; k < 8; ++k) v[k] = rec[rec_index(I, jr, ic, a, b) * 8 + k];
+        double s = gd.s(a), tt = gd.t(b);
+        u0[pg * mm + t] = cd.C0 + s * (cd.c10 + s * cd.c20 + tt * cd.c11) + tt * (cd.c01 + tt * cd.c02);
+        PointW<real> pw = point_weights<real>(v[0], v[1], v[2], v[3], v[4], v[5], gr.dx, gr.dy, I.conv);
+        r_out[pg * mm + t] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
+        w_out[pg * mm + t] = real(0);
+    }
+    // edge data of eq. (edge) = d/dxi, d/deta of the interpolant P at the edges
+    for (int t = threadIdx.x; t < 4 * edge_stride; t += blockDim.x) {
+        int side = t / edge_stride, e = t % edge_stride;
+        double val = 0.0;
+        if (side < 2 && e < I.my + 2) {
+            double s = (side == 0 ? -0.5 : 0.5) * I.hx, tt = gd.t(e - 1);
+            val = cd.c10 + 2.0 * cd.c20 * s + cd.c11 * tt + edge_gap_xi(cd, s, tt);
+        } else if (side >= 2 && e < I.mx + 2) {
+            double s = gd.s(e - 1), tt = (side == 2 ? -0.5 : 0.5) * I.hy;
+            val = cd.c01 + 2.0 * cd.c02 * tt + cd.c11 * s + edge_gap_eta(cd, s, tt);
+        }
+        edge[(pg * 4 + side) * edge_stride + e] = val;
+    }
+    if (threadIdx.x == 0)
+        bias_out[pg] = (I.restrict_mode == PD_RESTRICT_MACRO) ? (I.dx * I.dx * cd.c20 + I.dy * I.dy * cd.c02) / 6.0 : 0.0;
+}
+
+// generic burst: whole patch in shared memory, one thread per micro point
+template <typename real>
+__global__ void __launch_bounds__(256)
+burst_kernel(const InstDev I, const double* __restrict__ tab, int k_steps, real* w_io, const real* __restrict__ r_in)
+{
+    extern __shared__ unsigned char smem_raw[];
+    real* ws = reinterpret_cast<real*>(smem_raw);
+    real* ds = ws + 2 * I.mx * I.my;
+    const int p = blockIdx.x;
+    int i, j, ic, jr;
+    patch_ij(I, p, i, j, ic, jr);
+    const int mm = I.mx * I.my;
+    const long long pg = (long long)I.p_off + p;
+    const real* rec = static_cast<const real*>(I.rec);
+    const real dt = (real)I.dt;
+    for (int t = threadIdx.x; t < k_steps; t += blockDim.x) ds[t] = (real)tab[t];
+    // this thread's point (mm <= 1024 not needed: loop)
+    for (int t = threadIdx.x; t < mm; t += blockDim.x) ws[t] = w_io[pg * mm + t];
+    __syncthreads();
+    real* cur = ws;
+    real* nxt = ws + mm;
+    for (int k = 0; k < k_steps; ++k) {
+        for (int t = threadIdx.x; t < mm; t += blockDim.x) {
+            int a = t % I.mx, b = t / I.mx;
+            real v[8];
+            for (int q = 0; q < 8; ++q) v[q] = rec[rec_index(I, jr, ic, a, b) * 8 + q];
+            PointW<real> pw = point_weights<real>(v[0], v[1], v[2], v[3], v[4], v[5], (real)I.dx, (real)I.dy, I.conv);
+            // homogeneous mirrors for the departure
+            int aE = a + 1 > I.mx - 1 ? I.mx - 2 : a + 1;
+            int aW = a - 1 < 0 ? 1 : a - 1;
+            int bN = b + 1 > I.my - 1 ? I.my - 2 : b + 1;
+            int bS = b - 1 < 0 ? 1 : b - 1;
+            real L = pw.wC * cur[t] + pw.wE * cur[b * I.mx + aE] + pw.wW * cur[b * I.mx + aW]
+                   + pw.wN * cur[bN * I.mx + a] + pw.wS * cur[bS * I.mx + a]
+                   + pw.wX * (cur[bN * I.mx + aE] - cur[bS * I.mx + aE] - cur[bN * I.mx + aW] + cur[bS * I.mx + aW]);
+            nxt[t] = cur[t] + dt * (L + r_in[pg * mm + t] + ds[k] * v[6]);
+        }
+        __syncthreads();
+        real* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    for (int t = threadIdx.x; t < mm; t += blockDim.x) w_io[pg * mm + t] = cur[t];
+}
+
+// trapezoid restriction of the departure: one warp per patch
+template <typename real>
+__global__ void restrict_kernel(const InstDev I, const real* __restrict__ w, const double* __restrict__ bias,
+                                double* __restrict__ dU)
+{
+    int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (p >= I.n_patch) return;
+    const int mm = I.mx * I.my;
+    const long long pg = (long long)I.p_off + p;
+    double acc = 0.0;
+    for (int t = lane; t < mm; t += 32) {
+        int a = t % I.mx, b = t / I.mx;
+        double wt = ((a == 0 || a == I.mx - 1) ? 0.5 : 1.0) * ((b == 0 || b == I.my - 1) ? 0.5 : 1.0);
+        acc += wt * (double)w[pg * mm + t];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) {
+        double v = acc / ((double)(I.mx - 1) * (I.my - 1)) + bias[pg];
+        if (!isfinite(v)) atomicOr(I.err, ERR_NONFINITE);
+        dU[pg] = v;
+    }
+}
+
+// eq. (Extrapolation) on interior nodes + Dirichlet data at t + dt_macro
+__global__ void project_kernel(const InstDev I, double* __restrict__ U, const double* __restrict__ dU,
+                               double t_next, double dtm)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < I.n_patch) {
+        int i, j, ic, jr;
+        patch_ij(I, k, i, j, ic, jr);
+        long long node = (long long)j * I.nxp + i;
+        U[node] = U[node] + dtm * (dU[(long long)I.p_off + k] / I.tau);
+    } else if (k < I.n_patch + I.n_bnd) {
+        int q = k - I.n_patch;
+        int2 ij = I.bnd_ij[q];
+        double2 xy = I.bnd_xy[q];
+        U[(long long)ij.y * I.nxp + ij.x] = exact_solution(I.sol, xy.x, xy.y, t_next);
+    }
+}
+
+// ds table for a standalone burst: ds_k = s(t + k dt) - s(t_lift)
+__global__ void burst_table_kernel(int K, int tkind, double tc, double dt, double t, const double* t_lift,
+                                   double* tab)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K) tab[k] = time_factor(tkind, tc, t + k * dt) - time_factor(tkind, tc, *t_lift);
+}
+
+__global__ void lift_table_kernel(int tkind, double tc, double t, double* tab, double* t_lift)
+{
+    tab[0] = time_factor(tkind, tc, t);
+    *t_lift = t;
+}
+
+// ---------------------------------------------------------------------------
+// dispatch of the templated warp kernel
+
+template <int M, typename real, int MODE>
+cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const double* tab, double dtm,
+                        int k_steps, real* st_w, const real* st_r, cudaStream_t st)
+{
+    constexpr int P = 32 / M;
+    int wpr = (I.ncols + P - 1) / P;
+    int n_item_warps = wpr * I.nrows;
+    int n_bnd_warps = (MODE == MODE_FUSED) ? (I.n_bnd + 31) / 32 : 0;
+    int n_warps = n_item_warps + n_bnd_warps;
+    const int bs = 128;
+    unsigned nb = (unsigned)((n_warps * 32 + bs - 1) / bs);
+    bool cross = I.has_cross != 0, tsrc = I.has_tsrc != 0;
+    int K = (MODE == MODE_FUSED) ? I.K : k_steps;
+    size_t smem = tsrc ? sizeof(real) * (size_t)K : 0;
+#define PD_LAUNCH(CR, TS) patch_warp_kernel<M, CR, TS, real, MODE><<<nb, bs, smem, st>>>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, n_item_warps)
+    if (cross && tsrc) PD_LAUNCH(true, true);
+    else if (cross) PD_LAUNCH(true, false);
+    else if (tsrc) PD_LAUNCH(false, true);
+    else PD_LAUNCH(false, false);
+#undef PD_LAUNCH
+    return cudaGetLastError();
+}
+
+template <typename real, int MODE>
+cudaError_t dispatch_m(const InstDev& I, const double* Uc, double* Un, const double* tab, double dtm,
+                       int k_steps, real* st_w, const real* st_r, cudaStream_t st)
+{
+    switch (I.mx) {
+    case 3: return launch_warp<3, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
+    case 5: return launch_warp<5, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
+    case 7: return launch_warp<7, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
+    case 9: return launch_warp<9, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
+    case 11: return launch_warp<11, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool fused_supported(const InstDev& I)
+{
+    return I.mx == I.my && (I.mx == 3 || I.mx == 5 || I.mx == 7 || I.mx == 9 || I.mx == 11) && I.K <= kMaxK;
+}
+
+cudaError_t launch_fused_step(const InstDev& I, const InstDev*, int prec, const double* Uc, double* Un,
+                              const double* tab_row, double dtm, cudaStream_t st, int* n_launch)
+{
+    if (n_launch) ++*n_launch;
+    if (prec == PD_FP32)
+        return dispatch_m<float, MODE_FUSED>(I, Uc, Un, tab_row, dtm, 0, nullptr, nullptr, st);
+    return dispatch_m<double, MODE_FUSED>(I, Uc, Un, tab_row, dtm, 0, nullptr, nullptr, st);
+}
+
+cudaError_t launch_lift(const InstDev& I, const InstDev*, int prec, const double* U, double t, char* state,
+                        const pd_info& lay, cudaStream_t st)
+{
+    // header of the state buffer: [0] lift time, [1] scratch s(t)
+    double* hdr = reinterpret_cast<double*>(state);
+    lift_table_kernel<<<1, 1, 0, st>>>(I.tkind, I.tc, t, hdr + 1, hdr);
+    double* u0 = reinterpret_cast<double*>(state + lay.off_u0);
+    double* edge = reinterpret_cast<double*>(state + lay.off_edge);
+    double* bias = reinterpret_cast<double*>(state + lay.off_bias);
+    if (prec == PD_FP32)
+        lift_kernel<float><<<I.n_patch, 128, 0, st>>>(I, U, hdr + 1, u0, reinterpret_cast<float*>(state + lay.off_r),
+                                                      reinterpret_cast<float*>(state + lay.off_w), edge, bias, lay.edge_stride);
+    else
+        lift_kernel<double><<<I.n_patch, 128, 0, st>>>(I, U, hdr + 1, u0, reinterpret_cast<double*>(state + lay.off_r),
+                                                       reinterpret_cast<double*>(state + lay.off_w), edge, bias, lay.edge_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_burst(const InstDev& I, const InstDev*, int prec, char* state, const pd_info& lay, double t,
+                         int k_steps, cudaStream_t st)
+{
+    double* hdr = reinterpret_cast<double*>(state);
+    double* tab = hdr + 2;  // up to kMaxK entries live in the header block
+    burst_table_kernel<<<(k_steps + 127) / 128, 128, 0, st>>>(k_steps, I.tkind, I.tc, I.dt, t, hdr, tab);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (fused_supported(I)) {
+        if (prec == PD_FP32)
+            return dispatch_m<float, MODE_BURST>(I, nullptr, nullptr, tab, 0.0, k_steps,
+                                                 reinterpret_cast<float*>(state + lay.off_w),
+                                                 reinterpret_cast<const float*>(state + lay.off_r), st);
+        return dispatch_m<double, MODE_BURST>(I, nullptr, nullptr, tab, 0.0, k_steps,
+                                              reinterpret_cast<double*>(state + lay.off_w),
+                                              reinterpret_cast<const double*>(state + lay.off_r), st);
+    }
+    size_t es = prec == PD_FP32 ? sizeof(float) : sizeof(double);
+    size_t smem = (2 * (size_t)I.mx * I.my + k_steps) * es;
+    if (smem > 48 * 1024) {
+        cudaError_t a = prec == PD_FP32
+            ? cudaFuncSetAttribute(burst_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+            : cudaFuncSetAttribute(burst_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (a != cudaSuccess) return a;
+    }
+    if (prec == PD_FP32)
+        burst_kernel<float><<<I.n_patch, 256, smem, st>>>(I, tab, k_steps, reinterpret_cast<float*>(state + lay.off_w),
+                                                           reinterpret_cast<const float*>(state + lay.off_r));
+    else
+        burst_kernel<double><<<I.n_patch, 256, smem, st>>>(I, tab, k_steps, reinterpret_cast<double*>(state + lay.off_w),
+                                                            reinterpret_cast<const double*>(state + lay.off_r));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const pd_info& lay, double* dU,
+                            cudaStream_t st)
+{
+    const double* bias = reinterpret_cast<const double*>(state + lay.off_bias);
+    unsigned nb = (unsigned)((I.n_patch * 32 + 127) / 128);
+    if (prec == PD_FP32)
+        restrict_kernel<float><<<nb, 128, 0, st>>>(I, reinterpret_cast<const float*>(state + lay.off_w), bias, dU);
+    else
+        restrict_kernel<double><<<nb, 128, 0, st>>>(I, reinterpret_cast<const double*>(state + lay.off_w), bias, dU);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm, cudaStream_t st)
+{
+    int n = I.n_patch + I.n_bnd;
+    project_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, U, dU, t + dtm, dtm);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

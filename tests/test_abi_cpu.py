@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports
+every function include/pd.h declares (no device calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pd_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2405_08764_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for need in ("pd_create_grid", "pd_set_coeffs", "pd_lift", "pd_micro_burst", "pd_restrict",
+                 "pd_project", "pd_step", "pd_destroy_grid"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_abi_version_and_status_strings(lib):
+    lib.pd_abi_version.restype = ctypes.c_int
+    assert lib.pd_abi_version() == 1
+    lib.pd_status_str.restype = ctypes.c_char_p
+    lib.pd_status_str.argtypes = [ctypes.c_int]
+    assert lib.pd_status_str(0) == b"ok"
+    assert b"invalid" in lib.pd_status_str(1)
+
+
+def test_create_rejects_bad_descriptors_before_touching_the_device(lib):
+    from paper_2405_08764_gb300 import _native as N
+    from paper_2405_08764_gb300.api import grid_desc
+    from paper_2405_08764_gb300 import workloads as W
+    L = N.load()
+    for bad in (dict(m_xi=2), dict(h_ratio_xi=1.0), dict(k_micro=0), dict(n_xi=1), dict(cfl_micro=1.5),
+                dict(map="polar", map_p=(2.0, 1.0, 0, 0))):
+        p = W.base(**bad)
+        d = grid_desc(p, "fp32")
+        h = ctypes.c_void_p()
+        rc = L.pd_create_grid(ctypes.byref(d), 1, None, ctypes.byref(h))
+        assert rc == N.PD_EINVAL, bad
+
+
+def test_binding_fails_loudly_without_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2405_08764_gb300.api import Grid
+    from paper_2405_08764_gb300 import workloads as W
+    with pytest.raises(RuntimeError):
+        Grid(W.c1_manufactured())
+
+
+def test_oracle_is_not_imported_by_the_product():
+    pkg = os.path.join(ROOT, "paper_2405_08764_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "pd_oracle" not in txt, f
