@@ -200,6 +200,21 @@ pd_status pd_project(pd_grid* g, double* U_dev, const double* dU_dev, double t, 
 pd_status pd_step(pd_grid* g, double* U_dev, double t0, double dt_macro, int n_macro);
 pd_status pd_set_graph_mode(pd_grid* g, int enabled);
 
+/* Persistent dataflow execution of pd_step (default on).  When all patch warps
+ * of an instance fit on the device at once, a chunk of macro steps runs in one
+ * cooperative launch: each warp keeps its micro-stencil weights in registers and
+ * waits only for the neighbouring warps that produce its 3x3 macro stencil
+ * (per-warp step counters, release/acquire).  Every wait gives up after
+ * `wait_ns` nanoseconds (default 250 ms, pd_set_wait_limit); the kernel then sets a
+ * device flag and returns, and pd_sync reports PD_ETIMEOUT.  Otherwise pd_step
+ * launches one fused kernel per macro step. */
+pd_status pd_set_persistent(pd_grid* g, int enabled);
+pd_status pd_set_wait_limit(pd_grid* g, long long wait_ns);
+/* Test hook for the failure path: item warp `warp` of the persistent kernel
+ * never publishes its step counter, so its neighbours' bounded waits expire
+ * (-1 restores normal operation). */
+pd_status pd_test_silence_warp(pd_grid* g, int warp);
+
 /* Wait for the stream and report device-side errors (PD_ENUMERIC). */
 pd_status pd_sync(pd_grid* g);
 
@@ -214,12 +229,12 @@ pd_status pd_load_checkpoint(pd_grid* g, double* U_dev, double* t, long long* st
 long long pd_launch_count(const pd_grid* g);
 
 /* Kernel timing for roofline figures: when enabled, every pd_step records two
- * CUDA events on the grid's stream around its sequence of fused macro-step
- * kernels (after the time-table kernel).  pd_get_timing waits for the last
- * event and returns the summed event time in milliseconds and the number of
- * fused-kernel launches it covers; pd_set_timing(g, 1) also resets the sums. */
+ * CUDA events on the grid's stream around its macro-step kernels (after the
+ * time-table kernel).  pd_get_timing waits for the last event and returns the
+ * summed event time in milliseconds and the number of macro steps it covers;
+ * pd_set_timing(g, 1) also resets the sums. */
 pd_status pd_set_timing(pd_grid* g, int enabled);
-pd_status pd_get_timing(pd_grid* g, double* ms, long long* n_fused_launches);
+pd_status pd_get_timing(pd_grid* g, double* ms, long long* n_macro_steps);
 
 const char* pd_status_str(pd_status s);
 const char* pd_last_error(const pd_grid* g);

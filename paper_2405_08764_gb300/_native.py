@@ -74,6 +74,9 @@ SIGNATURES = {
     "pd_project": (C.c_int, [_GP, _VP, _VP, C.c_double, C.c_double]),
     "pd_step": (C.c_int, [_GP, _VP, C.c_double, C.c_double, C.c_int]),
     "pd_set_graph_mode": (C.c_int, [_GP, C.c_int]),
+    "pd_set_persistent": (C.c_int, [_GP, C.c_int]),
+    "pd_set_wait_limit": (C.c_int, [_GP, C.c_longlong]),
+    "pd_test_silence_warp": (C.c_int, [_GP, C.c_int]),
     "pd_sync": (C.c_int, [_GP]),
     "pd_save_checkpoint": (C.c_int, [_GP, _VP, C.c_double, C.c_longlong, C.c_char_p]),
     "pd_load_checkpoint": (C.c_int, [_GP, _VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_char_p]),

@@ -71,7 +71,7 @@ class Grid:
     the same micro size and precision).  prec: "fp32" (FP32 bursts, FP64
     restriction and projection) or "fp64"."""
 
-    def __init__(self, probs, prec: str = "fp32", graphs: bool = True):
+    def __init__(self, probs, prec: str = "fp32", graphs: bool = True, persistent: bool = True):
         _require_cuda()
         self.L = N.load()
         if isinstance(probs, dict):
@@ -88,6 +88,7 @@ class Grid:
             raise N.PDError(rc, "pd_create_grid rejected the descriptors")
         self.h = h
         self.L.pd_set_graph_mode(self.h, 1 if graphs else 0)
+        self.L.pd_set_persistent(self.h, 1 if persistent else 0)
         for k, p in enumerate(self.probs):
             c, amp = coeff_desc(p)
             N.check(self.L.pd_set_coeffs(self.h, k, C.byref(c)), self.h)
@@ -184,6 +185,13 @@ class Grid:
 
     def launches(self) -> int:
         return int(self.L.pd_launch_count(self.h))
+
+    def set_wait_limit(self, ns: int):
+        N.check(self.L.pd_set_wait_limit(self.h, int(ns)), self.h)
+
+    def silence_warp(self, warp: int):
+        """test hook: item warp `warp` of the persistent kernel never publishes"""
+        N.check(self.L.pd_test_silence_warp(self.h, int(warp)), self.h)
 
     def set_timing(self, enabled: bool):
         N.check(self.L.pd_set_timing(self.h, 1 if enabled else 0), self.h)

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <string>
@@ -23,6 +24,7 @@ struct Inst {
     pd_grid_desc d;
     InstDev I;                       // host copy (pointers are device pointers)
     void* rec = nullptr;             // coefficient records
+    void* brec = nullptr;            // burst records (weights, source, forcing basis)
     int2* bnd_ij = nullptr;
     double2* bnd_xy = nullptr;
     double* amp = nullptr;
@@ -30,6 +32,9 @@ struct Inst {
     bool coef_set = false;
     double dt = 0, tau = 0, dtm_sugg = 0;
     std::vector<int2> bnd_host;
+    int* bnd_off = nullptr;          // boundary nodes owned by each item warp (persistent kernel)
+    int* bnd_idx = nullptr;
+    int n_item = 0;
 };
 
 struct GraphEntry {
@@ -76,6 +81,11 @@ struct pd_grid {
     std::vector<cudaEvent_t> tfree;
     double t_ms = 0.0;
     long long t_launches = 0;
+    int* flags = nullptr;            // per-item-warp step counters (persistent kernel)
+    size_t flags_n = 0;
+    bool persist = true;
+    long long wait_ns = 250000000LL;
+    int silent_warp = -1;
 };
 
 namespace {
@@ -230,6 +240,13 @@ void layout(const pd_grid* g, const Inst& s, pd_info& o)
 
 pd_status ensure_step_buffers(pd_grid* g, int n_macro)
 {
+    size_t nf = 0;
+    for (auto& s : g->inst) nf = std::max(nf, (size_t)s.n_item);
+    if (nf > g->flags_n) {
+        if (g->flags) { cudaStreamSynchronize(g->stream); cudaFree(g->flags); }
+        PD_CUDA(g, cudaMalloc(&g->flags, sizeof(int) * nf));
+        g->flags_n = nf;
+    }
     if (!g->U_scratch) {
         PD_CUDA(g, cudaMalloc(&g->U_scratch, sizeof(double) * g->n_macro_total));
         g->U_scratch_n = (size_t)g->n_macro_total;
@@ -258,7 +275,29 @@ pd_status enqueue_steps(pd_grid* g, double* U, int n_macro, const std::vector<do
         const InstDev& I = s.I;
         double* bufs[2] = { U + I.u_off, g->U_scratch + I.u_off };
         int stride = I.K + kTabExtra;
-        if (fused_supported(I)) {
+        if (g->persist && persist_fits(I, s.d.prec)) {
+            int chunk = persist_max_steps(I, s.d.prec);
+            for (int s0 = 0; s0 < n_macro; s0 += chunk) {
+                PersistArgs pa;
+                pa.U0 = bufs[0]; pa.U1 = bufs[1];
+                pa.tab = g->tab + tab_off;
+                pa.s0 = s0; pa.n_steps = std::min(chunk, n_macro - s0);
+                pa.dtm = dtm[k];
+                pa.flags = g->flags;
+                pa.bnd_off = s.bnd_off; pa.bnd_idx = s.bnd_idx;
+                pa.wait_ns = g->wait_ns;
+                pa.silent_warp = g->silent_warp;
+                cudaError_t e = cudaMemsetAsync(g->flags, 0, sizeof(int) * s.n_item, st);
+                if (e == cudaSuccess) e = launch_persist(I, s.d.prec, pa, st);
+                if (e != cudaSuccess) return cuda_fail(g, e, "persistent step");
+                n_launch += 1;
+            }
+            if (n_macro & 1) {
+                cudaError_t e = cudaMemcpyAsync(bufs[0], bufs[1], sizeof(double) * (size_t)I.nxp * I.nyp,
+                                                cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return cuda_fail(g, e, "copy back");
+            }
+        } else if (fused_supported(I)) {
             for (int t = 0; t < n_macro; ++t) {
                 cudaError_t e = launch_fused_step(I, nullptr, s.d.prec, bufs[t & 1], bufs[(t + 1) & 1],
                                                   g->tab + tab_off + (size_t)t * stride, dtm[k], st, &n_launch);
@@ -361,11 +400,35 @@ pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_strea
         size_t es = s.d.prec == PD_FP32 ? 4 : 8;
         size_t npts = (size_t)s.I.n_patch * s.I.mx * s.I.my;
         e = cudaMalloc(&s.rec, npts * 8 * es);
+        if (e == cudaSuccess) e = cudaMalloc(&s.brec, npts * 16 * es);
         if (e == cudaSuccess) e = cudaMalloc(&s.bnd_ij, sizeof(int2) * (s.I.n_bnd + 1));
         if (e == cudaSuccess) e = cudaMalloc(&s.bnd_xy, sizeof(double2) * (s.I.n_bnd + 1));
         if (e == cudaSuccess && s.I.n_bnd)
             e = cudaMemcpy(s.bnd_ij, s.bnd_host.data(), sizeof(int2) * s.I.n_bnd, cudaMemcpyHostToDevice);
-        s.I.rec = s.rec; s.I.bnd_ij = s.bnd_ij; s.I.bnd_xy = s.bnd_xy; s.I.err = g->err;
+        if (e == cudaSuccess) {
+            // owner item warp of every boundary node: the warp of the nearest patch
+            int P = 32 / s.I.mx;
+            int wpr = (s.I.ncols + P - 1) / P;
+            s.n_item = wpr * s.I.nrows;
+            std::vector<std::vector<int>> own(s.n_item);
+            for (int k = 0; k < s.I.n_bnd; ++k) {
+                int ii = s.bnd_host[k].x, jj = s.bnd_host[k].y;
+                int ic = std::min(std::max(ii - s.I.i0, 0), s.I.ncols - 1);
+                int jr = std::min(std::max(jj - 1, 0), s.I.nrows - 1);
+                own[jr * wpr + ic / P].push_back(k);
+            }
+            std::vector<int> off(s.n_item + 1, 0), idx;
+            for (int w = 0; w < s.n_item; ++w) {
+                off[w + 1] = off[w] + (int)own[w].size();
+                idx.insert(idx.end(), own[w].begin(), own[w].end());
+            }
+            idx.push_back(0);
+            e = cudaMalloc(&s.bnd_off, sizeof(int) * off.size());
+            if (e == cudaSuccess) e = cudaMalloc(&s.bnd_idx, sizeof(int) * idx.size());
+            if (e == cudaSuccess) e = cudaMemcpy(s.bnd_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(s.bnd_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice);
+        }
+        s.I.rec = s.rec; s.I.brec = s.brec; s.I.bnd_ij = s.bnd_ij; s.I.bnd_xy = s.bnd_xy; s.I.err = g->err;
     }
     if (e != cudaSuccess) {
         pd_destroy_grid(g);
@@ -386,9 +449,9 @@ pd_status pd_destroy_grid(pd_grid* g)
     for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
     for (auto& pr : g->tev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto e : g->tfree) cudaEventDestroy(e);
-    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
+    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
     cudaFree(g->err); cudaFree(g->acc); cudaFree(g->U_scratch); cudaFree(g->tab);
-    cudaFree(g->state); cudaFree(g->dU);
+    cudaFree(g->state); cudaFree(g->dU); cudaFree(g->flags);
     if (g->cap) cudaStreamDestroy(g->cap);
     delete g;
     return PD_OK;
@@ -446,6 +509,11 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     s.tau = s.d.k_micro * s.dt;
     s.dtm_sugg = mrate > 0 ? 0.5 / mrate : s.tau;
     s.I.dt = s.dt; s.I.tau = s.tau;
+    s.I.inv_tau = 1.0 / s.tau;
+    s.I.inv_nn = 1.0 / ((double)(s.d.m_xi - 1) * (s.d.m_eta - 1));
+    PD_CUDA(g, launch_burst_records(s.I, s.d.prec, s.brec, g->stream));
+    g->launches += 1;
+    PD_CUDA(g, cudaStreamSynchronize(g->stream));
     // cross term present unless K^{xi eta} vanishes identically (orthogonal map, K = d m I,
     // or a separable map with M12 = 0)
     bool separable = s.d.map != PD_MAP_POLAR;
@@ -641,10 +709,36 @@ pd_status pd_step(pd_grid* g, double* U, double t0, double dt_macro, int n_macro
     if (g->timing) {
         PD_CUDA(g, cudaEventRecord(e1, g->stream));
         g->tev.emplace_back(e0, e1);
-        int nf = 0;
-        for (auto& s2 : g->inst) if (fused_supported(s2.I)) nf += n_macro;
-        g->t_launches += nf;
+        g->t_launches += n_macro;
     }
+    return PD_OK;
+}
+
+pd_status pd_set_persistent(pd_grid* g, int enabled)
+{
+    if (!g) return PD_EINVAL;
+    g->persist = enabled != 0;
+    for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+    g->gcache.clear();
+    return PD_OK;
+}
+
+pd_status pd_set_wait_limit(pd_grid* g, long long ns)
+{
+    if (!g) return PD_EINVAL;
+    if (ns < 1000) return fail(g, PD_EINVAL, "wait limit below 1 us");
+    g->wait_ns = ns;
+    for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+    g->gcache.clear();
+    return PD_OK;
+}
+
+pd_status pd_test_silence_warp(pd_grid* g, int warp)
+{
+    if (!g) return PD_EINVAL;
+    g->silent_warp = warp;
+    for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+    g->gcache.clear();
     return PD_OK;
 }
 
@@ -683,6 +777,10 @@ pd_status pd_sync(pd_grid* g)
     PD_CUDA(g, cudaStreamSynchronize(g->stream));
     int h = 0;
     PD_CUDA(g, cudaMemcpy(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & ERR_TIMEOUT) {
+        cudaMemset(g->err, 0, sizeof(int));
+        return fail(g, PD_ETIMEOUT, "a patch warp gave up waiting for its neighbours' macro step");
+    }
     if (h & ERR_NONFINITE) {
         cudaMemset(g->err, 0, sizeof(int));
         return fail(g, PD_ENUMERIC, "non-finite restricted change (unstable macro or micro step?)");

@@ -37,6 +37,9 @@ struct InstDev {
     long long u_off;             // offset of this instance in U (doubles)
     long long p_off;             // offset in patches (dU, micro state)
     const void* rec;             // coefficient records (float or double, 8 per point)
+    const void* brec;            // burst records (16 per point, see burst_record_kernel)
+    double inv_nn;               // 1 / ((m_xi - 1)(m_eta - 1))
+    double inv_tau;              // 1 / tau
     const int2* bnd_ij;          // boundary nodes (i, j)
     const double2* bnd_xy;       // their physical coordinates
     int* err;                    // device error flags
@@ -163,7 +166,7 @@ __device__ __forceinline__ double exact_solution(int sol, double x, double y, do
     return 0.0;
 }
 
-enum ErrBits { ERR_NONFINITE = 1, ERR_JACOBIAN = 2, ERR_COEF = 4 };
+enum ErrBits { ERR_NONFINITE = 1, ERR_JACOBIAN = 2, ERR_COEF = 4, ERR_TIMEOUT = 8 };
 
 // ---------------------------------------------------------------------------
 // host-side launch helpers (defined in the .cu files)
@@ -179,6 +182,7 @@ struct StepLaunch {
 cudaError_t launch_precompute(const InstDev& I, const pd_coeff_desc& c, const double* amp_dev,
                               void* rec, int prec, unsigned long long* rate_max,
                               unsigned long long* macro_rate_max, cudaStream_t st);
+cudaError_t launch_burst_records(const InstDev& I, int prec, void* brec, cudaStream_t st);
 cudaError_t launch_get_coeffs(const InstDev& I, int prec, double* out, cudaStream_t st);
 cudaError_t launch_init_field(const InstDev& I, const pd_coeff_desc& c, int kind, const double* prm,
                               int n_prm, const double* mu, double t, double* U, cudaStream_t st);
@@ -196,5 +200,23 @@ cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const
 cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm,
                            cudaStream_t st);
 bool fused_supported(const InstDev& I);
+
+// Persistent dataflow launch of n_steps macro steps (see pd_persist.cu).
+struct PersistArgs {
+    double* U0;            // buffer of even steps (the caller's field)
+    double* U1;            // buffer of odd steps (library scratch)
+    const double* tab;     // time table of the whole pd_step call
+    int s0, n_steps;       // first step of this chunk, steps in this chunk
+    double dtm;
+    int* flags;            // one step counter per item warp (zeroed before the launch)
+    const int* bnd_off;    // CSR: boundary nodes owned by each item warp
+    const int* bnd_idx;
+    long long wait_ns;     // give up a neighbour wait after this many ns
+    int silent_warp;       // test hook: this item warp never publishes (-1: none)
+};
+int persist_item_warps(const InstDev& I);
+int persist_max_steps(const InstDev& I, int prec);
+bool persist_fits(const InstDev& I, int prec);
+cudaError_t launch_persist(const InstDev& I, int prec, const PersistArgs& a, cudaStream_t st);
 
 }  // namespace pd

@@ -15,7 +15,7 @@
 // macro field with FP64 dot products (one coefficient per lane); the burst runs
 // in `real` (float for PD_FP32, double for PD_FP64); the restricted change is
 // divided by tau and accumulated into U in FP64.
-#include "pd_internal.h"
+#include "pd_device.cuh"
 
 #include <math.h>
 
@@ -23,48 +23,58 @@ namespace pd {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
-
-template <typename real> struct Vec4;
-template <> struct Vec4<float> { using T = float4; };
-template <> struct Vec4<double> { using T = double4; };
-
-template <typename real>
-__device__ __forceinline__ void load_record(const real* __restrict__ rec, long long idx, real v[8])
-{
-    using V = typename Vec4<real>::T;
-    const V* p = reinterpret_cast<const V*>(rec + idx * 8);
-    V lo = __ldg(p), hi = __ldg(p + 1);
-    v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
-    v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
-}
-
-template <>
-__device__ __forceinline__ void load_record<double>(const double* __restrict__ rec, long long idx, double v[8])
-{
-    const double2* p = reinterpret_cast<const double2*>(rec + idx * 8);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        double2 q = __ldg(p + k);
-        v[2 * k] = q.x; v[2 * k + 1] = q.y;
-    }
-}
-
-__device__ __forceinline__ int wrap_col(const InstDev& I, int i)
-{
-    if (!I.periodic) return i;
-    return i < 0 ? i + I.nxp : (i >= I.nxp ? i - I.nxp : i);
-}
+constexpr unsigned FULL = kFull;
 
 enum { MODE_FUSED = 0, MODE_BURST = 1 };
+
+// Burst record of one micro point (16 values, dt-scaled):
+//   0..5  stencil weights cE, cW, cN, cS, cX, cC with the mirror ghosts of the
+//         departure folded in (edge columns/rows take the outer weight on the
+//         inner neighbour; the cross weight vanishes on the patch boundary),
+//   6     Gs = dt G,
+//   7..15 B_k = dt * d r / d c_k, the forcing r = L_h(u_lift) + s(T) G being
+//         linear in the 9 monomial coefficients c_k of the interpolant;
+//         B_k is obtained by evaluating burst_forcing at the unit vector e_k.
+// Then per macro step R = dt r = sum_k B_k c_k + s(T) Gs.
+template <typename real>
+__global__ void burst_record_kernel(const InstDev I, const real* __restrict__ rec, real* __restrict__ brec)
+{
+    long long n = (long long)I.n_patch * I.mx * I.my;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    int a = (int)(idx % I.mx);
+    long long r1 = idx / I.mx;
+    int b = (int)((r1 / I.ncols) % I.my);
+    double v[8];
+    for (int k = 0; k < 8; ++k) v[k] = (double)rec[idx * 8 + k];
+    PatchGeo<double> g = { I.hx, I.hy, I.dx, I.dy, I.mx - 1, I.my - 1 };
+    PointW<double> pw = point_weights<double>(v[0], v[1], v[2], v[3], v[4], v[5], I.dx, I.dy, I.conv);
+    double dt = I.dt;
+    double e = dt * pw.wE, ww = dt * pw.wW, nn = dt * pw.wN, s = dt * pw.wS, x = dt * pw.wX;
+    double cc = 1.0 + dt * pw.wC;
+    if (a == 0) { e += ww; ww = 0.0; }
+    if (a == I.mx - 1) { ww += e; e = 0.0; }
+    if (b == 0) { nn += s; s = 0.0; }
+    if (b == I.my - 1) { s += nn; nn = 0.0; }
+    if (a == 0 || a == I.mx - 1 || b == 0 || b == I.my - 1) x = 0.0;
+    real* o = brec + idx * 16;
+    o[0] = (real)e; o[1] = (real)ww; o[2] = (real)nn; o[3] = (real)s; o[4] = (real)x; o[5] = (real)cc;
+    o[6] = (real)(dt * v[6]);
+    for (int k = 0; k < 9; ++k) {
+        double u[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
+        u[k] = 1.0;
+        Poly<double> ek = { u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8] };
+        o[7 + k] = (real)(dt * burst_forcing<double>(ek, g, a, b, v[0], v[1], v[2], v[3], v[4], v[5], 0.0, 0.0, pw));
+    }
+}
 
 // One warp = P patches of one patch row.  MODE_FUSED: lift -> burst -> restrict
 // -> project for one macro step, writing U at T_next into Un.  MODE_BURST: load
 // (w, r) from the micro state, run k_steps, store w.
 template <int M, bool CROSS, bool TSRC, typename real, int MODE>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, (sizeof(real) == 4 ? 4 : 1))
 patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __restrict__ Un,
-                  const double* __restrict__ tab, double dtm, int k_steps,
+                  const double* __restrict__ tab, double upd_scale, double bias_scale, int k_steps,
                   real* __restrict__ st_w, const real* __restrict__ st_r, int n_item_warps)
 {
     constexpr int P = 32 / M;
@@ -108,16 +118,10 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     const int i = I.i0 + icl, j = 1 + jr;
     const int qbase = (q < P ? q : P - 1) * M;
 
-    PatchGeo<real> g;
-    g.hx = (real)I.hx; g.hy = (real)I.hy; g.dx = (real)I.dx; g.dy = (real)I.dy;
-    g.nx = M - 1; g.ny = M - 1;
-
-    Poly<real> c = {};
+    real cv[9];
     double bias = 0.0;
-    real w[M];
-    real Rr[M];
     if (MODE == MODE_FUSED) {
-        // 3x3 macro stencil, st[(p+1)*3 + (q+1)] = U_{i+p, j+q}
+        // 3x3 macro stencil, stv[(p+1)*3 + (q+1)] = U_{i+p, j+q}
         double stv[9];
 #pragma unroll
         for (int pp = -1; pp <= 1; ++pp) {
@@ -139,79 +143,80 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
             ck[r] = acc;
             ckr[r] = (real)acc;
         }
-        real cv[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) cv[k] = __shfl_sync(FULL, ckr[k / M], (qbase + k % M) & 31);
-        c.C0 = cv[0]; c.c10 = cv[1]; c.c01 = cv[2]; c.c20 = cv[3]; c.c11 = cv[4];
-        c.c02 = cv[5]; c.c21 = cv[6]; c.c12 = cv[7]; c.c22 = cv[8];
         if (I.restrict_mode == PD_RESTRICT_MACRO) {
             // trapezoid average of the lift minus U_ij = (dxi^2 c20 + deta^2 c02) / 6
             double c20 = __shfl_sync(FULL, ck[3 / M], (qbase + 3 % M) & 31);
             double c02 = __shfl_sync(FULL, ck[5 / M], (qbase + 5 % M) & 31);
-            bias = (I.dx * I.dx * c20 + I.dy * I.dy * c02) / 6.0;
+            bias = (I.dx * I.dx * c20 + I.dy * I.dy * c02) * (1.0 / 6.0);
         }
     }
 
-    // per-point stencil weights (dt-scaled, ghost mirrors folded), forcing, source
+    // per-point stencil weights, forcing and source from the burst records
+    real w[M], Rr[M];
     real cE[M], cW[M], cN[M], cS[M], cC[M], cX[M], Gs[M];
-    const real dt = (real)I.dt;
     const real sT = (MODE == MODE_FUSED) ? (real)tinfo[0] : real(0);
-    const real* rec = static_cast<const real*>(I.rec);
+    const real dt = (real)I.dt;
+    const real* brec = static_cast<const real*>(I.brec);
     const long long rowstride = (long long)I.ncols * M;
     const long long base = (long long)jr * M * rowstride + (long long)icl * M + a;
     const long long sbase = ((long long)I.p_off + (long long)jr * I.ncols + icl) * (M * M) + a;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
-        real v[8];
-        load_record<real>(rec, base + b * rowstride, v);
-        PointW<real> pw = point_weights<real>(v[0], v[1], v[2], v[3], v[4], v[5], g.dx, g.dy, I.conv);
+        const real* p = brec + (base + b * rowstride) * 16;
+        real e, ww, n, s, x, cc, g, B0, B1, B2, B3, B4, B5, B6, B7, B8;
+        load_vec4<real>(p, e, ww, n, s);
+        load_vec4<real>(p + 4, x, cc, g, B0);
+        load_vec4<real>(p + 8, B1, B2, B3, B4);
+        load_vec4<real>(p + 12, B5, B6, B7, B8);
         real r;
         if (MODE == MODE_FUSED) {
-            r = burst_forcing<real>(c, g, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
+            r = sT * g;
+            r = fma(B0, cv[0], r); r = fma(B1, cv[1], r); r = fma(B2, cv[2], r);
+            r = fma(B3, cv[3], r); r = fma(B4, cv[4], r); r = fma(B5, cv[5], r);
+            r = fma(B6, cv[6], r); r = fma(B7, cv[7], r); r = fma(B8, cv[8], r);
             w[b] = real(0);
         } else {
-            r = st_r[sbase + b * M];
+            r = dt * st_r[sbase + b * M];
             w[b] = st_w[sbase + b * M];
         }
-        real e = dt * pw.wE, ww = dt * pw.wW, n = dt * pw.wN, s = dt * pw.wS, x = dt * pw.wX;
-        real cc = real(1) + dt * pw.wC;
-        if (a == 0) { e += ww; ww = real(0); }
-        if (a == M - 1) { ww += e; e = real(0); }
-        if (b == 0) { n += s; s = real(0); }
-        if (b == M - 1) { s += n; n = real(0); }
-        if (a == 0 || a == M - 1 || b == 0 || b == M - 1) x = real(0);
-        if (!active) { e = ww = n = s = x = cc = real(0); r = real(0); v[6] = real(0); w[b] = real(0); }
+        if (!active) { e = ww = n = s = x = cc = g = r = real(0); w[b] = real(0); }
         cE[b] = e; cW[b] = ww; cN[b] = n; cS[b] = s; cX[b] = x; cC[b] = cc;
-        Rr[b] = dt * r;
-        Gs[b] = dt * v[6];
+        Gs[b] = g;
+        Rr[b] = r;
     }
 
-    // K forward-Euler micro steps, all in registers
+    // K forward-Euler micro steps, all in registers.  Rows are swept upwards
+    // with a rolling window: the east/west neighbours of row b+1 are fetched
+    // (shuffles of the old values) before row b is overwritten, and the old
+    // value of row b-1 is kept in w_prev.
     for (int k = 0; k < K; ++k) {
         const real ds = TSRC ? ds_s[k] : real(0);
-        real e[M], v[M], d[M], nw[M];
+        real e_n = __shfl_down_sync(FULL, w[0], 1);
+        real v_n = __shfl_up_sync(FULL, w[0], 1);
+        real d_n = e_n - v_n, d_c = d_n, d_p = d_n;
+        real w_prev = real(0);
 #pragma unroll
         for (int b = 0; b < M; ++b) {
-            e[b] = __shfl_down_sync(FULL, w[b], 1);
-            v[b] = __shfl_up_sync(FULL, w[b], 1);
-        }
-        if (CROSS) {
-#pragma unroll
-            for (int b = 0; b < M; ++b) d[b] = e[b] - v[b];
-        }
-#pragma unroll
-        for (int b = 0; b < M; ++b) {
+            const real e_c = e_n, v_c = v_n;
+            d_p = d_c;
+            d_c = d_n;
+            if (b + 1 < M) {
+                e_n = __shfl_down_sync(FULL, w[b + 1], 1);
+                v_n = __shfl_up_sync(FULL, w[b + 1], 1);
+                if (CROSS) d_n = e_n - v_n;
+            }
             real acc = fma(cC[b], w[b], Rr[b]);
-            acc = fma(cE[b], e[b], acc);
-            acc = fma(cW[b], v[b], acc);
+            acc = fma(cE[b], e_c, acc);
+            acc = fma(cW[b], v_c, acc);
             if (b + 1 < M) acc = fma(cN[b], w[b + 1], acc);
-            if (b > 0) acc = fma(cS[b], w[b - 1], acc);
-            if (CROSS && b > 0 && b + 1 < M) acc = fma(cX[b], d[b + 1] - d[b - 1], acc);
+            if (b > 0) acc = fma(cS[b], w_prev, acc);
+            if (CROSS && b > 0 && b + 1 < M) acc = fma(cX[b], d_n - d_p, acc);
             if (TSRC) acc = fma(ds, Gs[b], acc);
-            nw[b] = acc;
+            w_prev = w[b];
+            w[b] = acc;
         }
-#pragma unroll
-        for (int b = 0; b < M; ++b) w[b] = nw[b];
     }
 
     if (MODE == MODE_BURST) {
@@ -223,7 +228,7 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     }
 
     // trapezoid restriction of the departure, then eq. (Time_Derivative) and
-    // eq. (Extrapolation) in FP64
+    // eq. (Extrapolation) in FP64:  U_next = U + dt_macro (sum / n^2 + bias) / tau
     real col = real(0.5) * (w[0] + w[M - 1]);
 #pragma unroll
     for (int b = 1; b < M - 1; ++b) col += w[b];
@@ -235,10 +240,10 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
         if (a + off < M) col += o;
     }
     if (active && a == 0) {
-        double dU = (double)col / (double)((M - 1) * (M - 1)) + bias;
-        if (!isfinite(dU)) atomicOr(I.err, ERR_NONFINITE);
+        double inc = fma((double)col, upd_scale, bias * bias_scale);
+        if (!isfinite(inc)) atomicOr(I.err, ERR_NONFINITE);
         long long node = (long long)j * I.nxp + i;
-        Un[node] = Uc[node] + dtm * (dU / I.tau);
+        Un[node] = Uc[node] + inc;
     }
 }
 
@@ -416,6 +421,9 @@ template <int M, typename real, int MODE>
 cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const double* tab, double dtm,
                         int k_steps, real* st_w, const real* st_r, cudaStream_t st)
 {
+    // dt_macro / tau scales the restricted change; the trapezoid sum also carries 1 / n^2
+    double bias_scale = dtm * I.inv_tau;
+    double upd_scale = bias_scale * I.inv_nn;
     constexpr int P = 32 / M;
     int wpr = (I.ncols + P - 1) / P;
     int n_item_warps = wpr * I.nrows;
@@ -426,7 +434,7 @@ cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const do
     bool cross = I.has_cross != 0, tsrc = I.has_tsrc != 0;
     int K = (MODE == MODE_FUSED) ? I.K : k_steps;
     size_t smem = tsrc ? sizeof(real) * (size_t)K : 0;
-#define PD_LAUNCH(CR, TS) patch_warp_kernel<M, CR, TS, real, MODE><<<nb, bs, smem, st>>>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, n_item_warps)
+#define PD_LAUNCH(CR, TS) patch_warp_kernel<M, CR, TS, real, MODE><<<nb, bs, smem, st>>>(I, Uc, Un, tab, upd_scale, bias_scale, k_steps, st_w, st_r, n_item_warps)
     if (cross && tsrc) PD_LAUNCH(true, true);
     else if (cross) PD_LAUNCH(true, false);
     else if (tsrc) PD_LAUNCH(false, true);
@@ -450,6 +458,17 @@ cudaError_t dispatch_m(const InstDev& I, const double* Uc, double* Un, const dou
 }
 
 }  // namespace
+
+cudaError_t launch_burst_records(const InstDev& I, int prec, void* brec, cudaStream_t st)
+{
+    long long n = (long long)I.n_patch * I.mx * I.my;
+    unsigned nb = (unsigned)((n + 127) / 128);
+    if (prec == PD_FP32)
+        burst_record_kernel<float><<<nb, 128, 0, st>>>(I, (const float*)I.rec, (float*)brec);
+    else
+        burst_record_kernel<double><<<nb, 128, 0, st>>>(I, (const double*)I.rec, (double*)brec);
+    return cudaGetLastError();
+}
 
 bool fused_supported(const InstDev& I)
 {

@@ -64,7 +64,7 @@ def test_coefficients_match_oracle(env, orc, name):
         want[:, 6] *= np.repeat(p["src_amp"], o.mx * o.my)
     # identically-zero channels (beta on orthogonal maps with isotropic K) are
     # compared on the scale of the diffusion coefficients
-    floor = 1e-3 * np.abs(want[:, [0, 2]]).max()
+    floor = np.abs(want[:, [0, 2]]).max()
     for k in range(7):
         scale = max(np.abs(want[:, k]).max(), floor if k < 6 else 1e-300)
         assert np.abs(got[:, k] - want[:, k]).max() <= 1e-13 * scale, (name, k)
