@@ -288,9 +288,11 @@ def run_gpu(args):
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
         "frac": (achieved / pk["fp32_tflops"]) if achieved else None, "traffic": traffic,
-        "kernel": "patch_warp_kernel<11,cross,tsrc,float,fused> (one macro step per launch)",
+        "kernel": ("patch_persist_kernel<11,cross,tsrc,float> (cooperative, %d macro steps per launch)"
+                   % info["chunk_steps"] if info["exec_path"] == 2 else
+                   "patch_warp_kernel<11,cross,tsrc,float,fused> (one macro step per launch)"),
         "flop_per_point_update": FLOP_PER_UPDATE,
-        "kernel_ms_per_launch": kern_ms / kern_n if kern_n else None,
+        "kernel_ms_per_macro_step": kern_ms / kern_n if kern_n else None,
         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (
             pk["sm_max_mhz"], pk["source"]),
     }

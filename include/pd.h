@@ -127,6 +127,9 @@ typedef struct {
     size_t state_bytes;           /* whole micro-state buffer (all instances) */
     size_t off_u0, off_r, off_w, off_edge, off_bias; /* section offsets, 256-byte aligned */
     int edge_stride;              /* max(m_xi, m_eta) + 2 */
+    int exec_path;                /* pd_step path: 0 separate passes, 1 one fused kernel per
+                                     macro step, 2 persistent dataflow kernel */
+    int chunk_steps;              /* macro steps per persistent launch (path 2) */
 } pd_info;
 
 /* Create a grid of n_inst instances, descs[0..n_inst-1] (host array, copied).

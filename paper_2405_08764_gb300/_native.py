@@ -6,7 +6,7 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpd.so")
+LIB_PATH = os.environ.get("PD_LIB_PATH") or os.path.join(HERE, "libpd.so")
 
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ECUDA, PD_ESTATE, PD_EUNSTABLE, PD_ETIMEOUT, PD_ENUMERIC = range(8)
 PD_FP64, PD_FP32 = 0, 1
@@ -53,7 +53,7 @@ class Info(C.Structure):
         ("dt_micro", C.c_double), ("tau", C.c_double), ("dt_macro_suggested", C.c_double),
         ("state_bytes", C.c_size_t), ("off_u0", C.c_size_t), ("off_r", C.c_size_t),
         ("off_w", C.c_size_t), ("off_edge", C.c_size_t), ("off_bias", C.c_size_t),
-        ("edge_stride", C.c_int),
+        ("edge_stride", C.c_int), ("exec_path", C.c_int), ("chunk_steps", C.c_int),
     ]
 
 

@@ -5,6 +5,7 @@ or PyTorch fallback."""
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 import torch
@@ -71,8 +72,13 @@ class Grid:
     the same micro size and precision).  prec: "fp32" (FP32 bursts, FP64
     restriction and projection) or "fp64"."""
 
-    def __init__(self, probs, prec: str = "fp32", graphs: bool = True, persistent: bool = True):
+    def __init__(self, probs, prec: str = "fp32", graphs: bool = True, persistent: bool | None = None):
+        """persistent: None follows the PD_PERSISTENT environment variable (default on;
+        "0" selects one fused launch per macro step, e.g. for kernel profilers that
+        cannot replay cooperative launches)."""
         _require_cuda()
+        if persistent is None:
+            persistent = os.environ.get("PD_PERSISTENT", "1") != "0"
         self.L = N.load()
         if isinstance(probs, dict):
             probs = [probs]

@@ -149,6 +149,24 @@ void poly_weights(InstDev& I)
     // row 0: C0 = c00 - h_xi^2 c20 / 12 - h_eta^2 c02 / 12 (eq. C_0)
     for (int jj = 0; jj < 9; ++jj)
         I.lw[0][jj] -= I.hx * I.hx / 12.0 * I.lw[3][jj] + I.hy * I.hy / 12.0 * I.lw[5][jj];
+    // two-phase form over the differences (slot: 0 S-, 1 S0, 2 S+, 3 D-, 4 D0, 5 D+, 6 T, 7 V, 8 U00):
+    // S_q = U(-1,q) - 2U(0,q) + U(1,q), D_q = U(1,q) - U(-1,q), T = U(0,1) - U(0,-1),
+    // V = U(0,-1) - 2U(0,0) + U(0,1)
+    const double Dx = I.Dx, Dy = I.Dy;
+    const int sl[9][3] = { {8, 1, 7}, {4, 4, 4}, {6, 6, 6}, {1, 1, 1}, {5, 3, 3}, {7, 7, 7}, {2, 0, 0}, {5, 3, 4}, {2, 0, 1} };
+    const double ww[9][3] = {
+        { -I.hx * I.hx / (24.0 * Dx * Dx), -I.hy * I.hy / (24.0 * Dy * Dy), 1.0 },   // C0
+        { 0.0, 0.0, 1.0 / (2.0 * Dx) },                                              // c10
+        { 0.0, 0.0, 1.0 / (2.0 * Dy) },                                              // c01
+        { 0.0, 0.0, 1.0 / (2.0 * Dx * Dx) },                                         // c20
+        { -1.0, 0.0, 1.0 / (4.0 * Dx * Dy) },                                        // c11
+        { 0.0, 0.0, 1.0 / (2.0 * Dy * Dy) },                                         // c02
+        { -1.0, 0.0, 1.0 / (4.0 * Dx * Dx * Dy) },                                   // c21
+        { 1.0, -2.0, 1.0 / (4.0 * Dx * Dy * Dy) },                                   // c12
+        { 1.0, -2.0, 1.0 / (4.0 * Dx * Dx * Dy * Dy) },                              // c22
+    };
+    for (int k = 0; k < 9; ++k)
+        for (int c = 0; c < 3; ++c) { I.c2slot[k][c] = sl[k][c]; I.c2w[k][c] = ww[k][c]; }
 }
 
 void fill_inst(Inst& s, long long u_off, long long p_off)
@@ -540,6 +558,8 @@ pd_status pd_query(const pd_grid* gc, int inst, pd_info* o)
     o->patch_offset = s.I.p_off;
     o->dt_micro = s.dt; o->tau = s.tau; o->dt_macro_suggested = s.dtm_sugg;
     layout(g, s, *o);
+    o->exec_path = !fused_supported(s.I) ? 0 : (g->persist && s.coef_set && persist_fits(s.I, s.d.prec)) ? 2 : 1;
+    o->chunk_steps = o->exec_path == 2 ? persist_max_steps(s.I, s.d.prec) : 1;
     return PD_OK;
 }
 

@@ -26,4 +26,121 @@ __device__ __forceinline__ int wrap_col(const InstDev& I, int i)
     return i < 0 ? i + I.nxp : (i >= I.nxp ? i - I.nxp : i);
 }
 
+// K forward-Euler micro steps of the departure w, everything in registers.
+// Lane a holds micro column a; east/west neighbours come from the adjacent lanes
+// by shuffles, north/south from the same thread.  Rows are swept upwards with a
+// rolling window: the neighbours of row b+1 are fetched (shuffles of the old
+// values) before row b is overwritten, and the old value of row b-1 is kept in
+// w_prev.  ds[k] = s(t_k) - s(T) for the time-dependent source.
+template <int M, bool CROSS, bool TSRC, typename real>
+__device__ __forceinline__ void burst_steps(real (&w)[M], const real (&cE)[M], const real (&cW)[M],
+                                            const real (&cN)[M], const real (&cS)[M], const real (&cC)[M],
+                                            const real (&cX)[M], const real (&Gs)[M], const real (&Rr)[M],
+                                            const real* __restrict__ ds, int K)
+{
+    for (int k = 0; k < K; ++k) {
+        const real dsk = TSRC ? ds[k] : real(0);
+        real e_n = __shfl_down_sync(kFull, w[0], 1);
+        real v_n = __shfl_up_sync(kFull, w[0], 1);
+        real d_n = e_n - v_n, d_c = d_n, d_p = d_n;
+        real w_prev = real(0);
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const real e_c = e_n, v_c = v_n;
+            d_p = d_c;
+            d_c = d_n;
+            if (b + 1 < M) {
+                e_n = __shfl_down_sync(kFull, w[b + 1], 1);
+                v_n = __shfl_up_sync(kFull, w[b + 1], 1);
+                if (CROSS) d_n = e_n - v_n;
+            }
+            real acc = fma(cC[b], w[b], Rr[b]);
+            acc = fma(cE[b], e_c, acc);
+            acc = fma(cW[b], v_c, acc);
+            if (b + 1 < M) acc = fma(cN[b], w[b + 1], acc);
+            if (b > 0) acc = fma(cS[b], w_prev, acc);
+            if (CROSS && b > 0 && b + 1 < M) acc = fma(cX[b], d_n - d_p, acc);
+            if (TSRC) acc = fma(dsk, Gs[b], acc);
+            w_prev = w[b];
+            w[b] = acc;
+        }
+    }
+}
+
+// Monomial coefficients of the patch's interpolant from the FP64 macro field,
+// one coefficient per lane (lanes qbase + k, k < 9), in two FP64 phases:
+//   phase 1: lane s forms difference s of the 3x3 stencil (three loads, one
+//            add and one fma);
+//   phase 2: lane k combines up to three differences (two fma, one multiply).
+// Micro sizes below 9 use the 9-term dot product with the weights lw.
+// Returns this lane's FP64 coefficient (k = a) and broadcasts the FP32/FP64
+// copies cv[0..8].
+template <int M, typename real, bool L2LOAD>
+__device__ __forceinline__ void macro_coeffs(const InstDev& I, const double* __restrict__ Uc, int i, int j, int a,
+                                             int qbase, const double (*lw)[9], const int (*slot)[3],
+                                             const double (*cw)[3], real cv[9], double& c20, double& c02,
+                                             double& u00)
+{
+    auto ld = [&](int di, int dj) -> double {
+        const double* p = Uc + (long long)(j + dj) * I.nxp + wrap_col(I, i + di);
+        return L2LOAD ? __ldcg(p) : __ldg(p);
+    };
+    if constexpr (M >= 9) {
+        int ai = 0, aj = 0, bi = 0, bj = 0, ci = 0, cj = 0;
+        double wB = 0.0;
+        bool neg = false, zeroC = false;
+        switch (a) {
+        case 0: ai = -1; aj = -1; bi = 0; bj = -1; ci = 1; cj = -1; wB = -2.0; break;
+        case 1: ai = -1; aj = 0;  bi = 0; bj = 0;  ci = 1; cj = 0;  wB = -2.0; break;
+        case 2: ai = -1; aj = 1;  bi = 0; bj = 1;  ci = 1; cj = 1;  wB = -2.0; break;
+        case 3: ai = 1;  aj = -1; ci = -1; cj = -1; neg = true; break;
+        case 4: ai = 1;  aj = 0;  ci = -1; cj = 0;  neg = true; break;
+        case 5: ai = 1;  aj = 1;  ci = -1; cj = 1;  neg = true; break;
+        case 6: ai = 0;  aj = 1;  ci = 0;  cj = -1; neg = true; break;
+        case 7: ai = 0;  aj = -1; bi = 0; bj = 0;  ci = 0; cj = 1;  wB = -2.0; break;
+        default: zeroC = true; break;   // slot 8: U(0,0)
+        }
+        double A = ld(ai, aj), B = ld(bi, bj), Cv = ld(ci, cj);
+        if (neg) Cv = -Cv;
+        if (zeroC) Cv = 0.0;
+        double x1 = fma(wB, B, A + Cv);
+        int k = a < 9 ? a : 8;
+        double P = __shfl_sync(kFull, x1, (qbase + slot[k][0]) & 31);
+        double Q = __shfl_sync(kFull, x1, (qbase + slot[k][1]) & 31);
+        double R = __shfl_sync(kFull, x1, (qbase + slot[k][2]) & 31);
+        double ck = fma(cw[k][1], R, fma(cw[k][0], Q, P)) * cw[k][2];
+        real ckr = (real)ck;
+#pragma unroll
+        for (int kk = 0; kk < 9; ++kk) cv[kk] = __shfl_sync(kFull, ckr, (qbase + kk) & 31);
+        c20 = __shfl_sync(kFull, ck, (qbase + 3) & 31);
+        c02 = __shfl_sync(kFull, ck, (qbase + 5) & 31);
+        u00 = __shfl_sync(kFull, x1, (qbase + 8) & 31);
+    } else {
+        constexpr int NC = (9 + M - 1) / M;
+        double stv[9];
+#pragma unroll
+        for (int pp = -1; pp <= 1; ++pp)
+#pragma unroll
+            for (int qq = -1; qq <= 1; ++qq) stv[(pp + 1) * 3 + (qq + 1)] = ld(pp, qq);
+        double ck[NC];
+        real ckr[NC];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            int k = a + r * M;
+            double acc = 0.0;
+            if (k < 9) {
+#pragma unroll
+                for (int jj = 0; jj < 9; ++jj) acc = fma(lw[k][jj], stv[jj], acc);
+            }
+            ck[r] = acc;
+            ckr[r] = (real)acc;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 9; ++kk) cv[kk] = __shfl_sync(kFull, ckr[kk / M], (qbase + kk % M) & 31);
+        c20 = __shfl_sync(kFull, ck[3 / M], (qbase + 3 % M) & 31);
+        c02 = __shfl_sync(kFull, ck[5 / M], (qbase + 5 % M) & 31);
+        u00 = stv[4];
+    }
+}
+
 }  // namespace pd

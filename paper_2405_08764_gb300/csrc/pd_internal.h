@@ -15,7 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/pd.h"
+#include "pd.h"
 
 namespace pd {
 
@@ -34,6 +34,10 @@ struct InstDev {
     double map_p[4];
     double xi1, eta1;
     double lw[9][9];             // monomial coefficients of the 3x3 interpolant, see poly_weights
+    // two-phase form of the same coefficients (micro sizes >= 9): coefficient k =
+    // scale_k * (P + w1_k Q + w2_k R) over first/second macro differences, see macro_coeffs
+    int c2slot[9][3];
+    double c2w[9][3];
     long long u_off;             // offset of this instance in U (doubles)
     long long p_off;             // offset in patches (dU, micro state)
     const void* rec;             // coefficient records (float or double, 8 per point)
@@ -215,6 +219,7 @@ struct PersistArgs {
     int silent_warp;       // test hook: this item warp never publishes (-1: none)
 };
 int persist_item_warps(const InstDev& I);
+size_t persist_smem_bytes(const InstDev& I, size_t es, int n_steps);
 int persist_max_steps(const InstDev& I, int prec);
 bool persist_fits(const InstDev& I, int prec);
 cudaError_t launch_persist(const InstDev& I, int prec, const PersistArgs& a, cudaStream_t st);

@@ -80,13 +80,17 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     constexpr int P = 32 / M;
     constexpr int NC = (9 + M - 1) / M;
     __shared__ double lw_s[9][9];
+    __shared__ int slot_s[9][3];
+    __shared__ double cw_s[9][3];
     __shared__ double tinfo[3];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     real* ds_s = reinterpret_cast<real*>(dyn_smem);   // TSRC: K entries
 
     const int K = (MODE == MODE_FUSED) ? I.K : k_steps;
-    if (MODE == MODE_FUSED)
+    if (MODE == MODE_FUSED) {
         for (int t = threadIdx.x; t < 81; t += blockDim.x) lw_s[t / 9][t % 9] = I.lw[t / 9][t % 9];
+        for (int t = threadIdx.x; t < 27; t += blockDim.x) { slot_s[t / 3][t % 3] = I.c2slot[t / 3][t % 3]; cw_s[t / 3][t % 3] = I.c2w[t / 3][t % 3]; }
+    }
     if (TSRC)
         for (int t = threadIdx.x; t < K; t += blockDim.x) ds_s[t] = (real)tab[t];
     if (MODE == MODE_FUSED && threadIdx.x < 3) tinfo[threadIdx.x] = tab[K + threadIdx.x];
@@ -119,36 +123,12 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     const int qbase = (q < P ? q : P - 1) * M;
 
     real cv[9];
-    double bias = 0.0;
+    double bias = 0.0, u00 = 0.0;
     if (MODE == MODE_FUSED) {
-        // 3x3 macro stencil, stv[(p+1)*3 + (q+1)] = U_{i+p, j+q}
-        double stv[9];
-#pragma unroll
-        for (int pp = -1; pp <= 1; ++pp) {
-            int ii = wrap_col(I, i + pp);
-#pragma unroll
-            for (int qq = -1; qq <= 1; ++qq) stv[(pp + 1) * 3 + (qq + 1)] = __ldg(Uc + (long long)(j + qq) * I.nxp + ii);
-        }
-        // one monomial coefficient per lane (FP64 dot product), then broadcast
-        double ck[NC];
-        real ckr[NC];
-#pragma unroll
-        for (int r = 0; r < NC; ++r) {
-            int k = a + r * M;
-            double acc = 0.0;
-            if (k < 9) {
-#pragma unroll
-                for (int jj = 0; jj < 9; ++jj) acc = fma(lw_s[k][jj], stv[jj], acc);
-            }
-            ck[r] = acc;
-            ckr[r] = (real)acc;
-        }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) cv[k] = __shfl_sync(FULL, ckr[k / M], (qbase + k % M) & 31);
+        double c20, c02;
+        macro_coeffs<M, real, false>(I, Uc, i, j, a, qbase, lw_s, slot_s, cw_s, cv, c20, c02, u00);
         if (I.restrict_mode == PD_RESTRICT_MACRO) {
             // trapezoid average of the lift minus U_ij = (dxi^2 c20 + deta^2 c02) / 6
-            double c20 = __shfl_sync(FULL, ck[3 / M], (qbase + 3 % M) & 31);
-            double c02 = __shfl_sync(FULL, ck[5 / M], (qbase + 5 % M) & 31);
             bias = (I.dx * I.dx * c20 + I.dy * I.dy * c02) * (1.0 / 6.0);
         }
     }
@@ -168,14 +148,20 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
         real e, ww, n, s, x, cc, g, B0, B1, B2, B3, B4, B5, B6, B7, B8;
         load_vec4<real>(p, e, ww, n, s);
         load_vec4<real>(p + 4, x, cc, g, B0);
-        load_vec4<real>(p + 8, B1, B2, B3, B4);
-        load_vec4<real>(p + 12, B5, B6, B7, B8);
         real r;
         if (MODE == MODE_FUSED) {
+            load_vec4<real>(p + 8, B1, B2, B3, B4);
             r = sT * g;
             r = fma(B0, cv[0], r); r = fma(B1, cv[1], r); r = fma(B2, cv[2], r);
-            r = fma(B3, cv[3], r); r = fma(B4, cv[4], r); r = fma(B5, cv[5], r);
-            r = fma(B6, cv[6], r); r = fma(B7, cv[7], r); r = fma(B8, cv[8], r);
+            r = fma(B3, cv[3], r); r = fma(B4, cv[4], r);
+            // B5..B8: c02 and the edge-gap terms; B6..B8 vanish away from the ghosts
+            if (b == 0 || b == M - 1 || a == 0 || a == M - 1) {
+                load_vec4<real>(p + 12, B5, B6, B7, B8);
+                r = fma(B5, cv[5], r); r = fma(B6, cv[6], r); r = fma(B7, cv[7], r); r = fma(B8, cv[8], r);
+            } else {
+                B5 = p[12];
+                r = fma(B5, cv[5], r);
+            }
             w[b] = real(0);
         } else {
             r = dt * st_r[sbase + b * M];
@@ -187,37 +173,7 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
         Rr[b] = r;
     }
 
-    // K forward-Euler micro steps, all in registers.  Rows are swept upwards
-    // with a rolling window: the east/west neighbours of row b+1 are fetched
-    // (shuffles of the old values) before row b is overwritten, and the old
-    // value of row b-1 is kept in w_prev.
-    for (int k = 0; k < K; ++k) {
-        const real ds = TSRC ? ds_s[k] : real(0);
-        real e_n = __shfl_down_sync(FULL, w[0], 1);
-        real v_n = __shfl_up_sync(FULL, w[0], 1);
-        real d_n = e_n - v_n, d_c = d_n, d_p = d_n;
-        real w_prev = real(0);
-#pragma unroll
-        for (int b = 0; b < M; ++b) {
-            const real e_c = e_n, v_c = v_n;
-            d_p = d_c;
-            d_c = d_n;
-            if (b + 1 < M) {
-                e_n = __shfl_down_sync(FULL, w[b + 1], 1);
-                v_n = __shfl_up_sync(FULL, w[b + 1], 1);
-                if (CROSS) d_n = e_n - v_n;
-            }
-            real acc = fma(cC[b], w[b], Rr[b]);
-            acc = fma(cE[b], e_c, acc);
-            acc = fma(cW[b], v_c, acc);
-            if (b + 1 < M) acc = fma(cN[b], w[b + 1], acc);
-            if (b > 0) acc = fma(cS[b], w_prev, acc);
-            if (CROSS && b > 0 && b + 1 < M) acc = fma(cX[b], d_n - d_p, acc);
-            if (TSRC) acc = fma(ds, Gs[b], acc);
-            w_prev = w[b];
-            w[b] = acc;
-        }
-    }
+    burst_steps<M, CROSS, TSRC, real>(w, cE, cW, cN, cS, cC, cX, Gs, Rr, ds_s, K);
 
     if (MODE == MODE_BURST) {
         if (active) {
@@ -243,7 +199,7 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
         double inc = fma((double)col, upd_scale, bias * bias_scale);
         if (!isfinite(inc)) atomicOr(I.err, ERR_NONFINITE);
         long long node = (long long)j * I.nxp + i;
-        Un[node] = Uc[node] + inc;
+        Un[node] = u00 + inc;
     }
 }
 

@@ -24,6 +24,8 @@ namespace pd {
 
 namespace {
 
+constexpr int kPersistBlock = 64;   // two item warps per block: even load across SMs
+
 __device__ __forceinline__ int ld_acquire(const int* p)
 {
     int v;
@@ -44,20 +46,28 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 template <int M, bool CROSS, bool TSRC, typename real>
-__global__ void __launch_bounds__(128, (sizeof(real) == 4 ? 4 : 1))
+__global__ void __launch_bounds__(kPersistBlock, (sizeof(real) == 4 ? 8 : 2))
 patch_persist_kernel(const InstDev I, const PersistArgs A, double upd_scale, double bias_scale, int n_item_warps)
 {
     constexpr int P = 32 / M;
     constexpr int NC = (9 + M - 1) / M;
+    constexpr int LANES = P * M;                          // lanes holding a micro column
     __shared__ double lw_s[9][9];
+    __shared__ int slot_s[9][3];
+    __shared__ double cw_s[9][3];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    real* ds_s = reinterpret_cast<real*>(dyn_smem);     // [n_steps][K]: s(t_k) - s(T_n)
-    real* sT_s = ds_s + (TSRC ? A.n_steps * I.K : 0);    // [n_steps]: s(T_n)
+    // [warp in block][row b][lane < LANES][12]: forcing basis B_0..B_8 (+3 pad)
+    real* Bs = reinterpret_cast<real*>(dyn_smem);
+    real* ds_s = Bs + (size_t)(blockDim.x / 32) * M * LANES * 12;   // [n_steps][K]: s(t_k) - s(T_n)
+    real* sT_s = ds_s + (TSRC ? A.n_steps * I.K : 0);                 // [n_steps]: s(T_n)
+    __shared__ double tn_s[64];                                        // T_{n+1} (first 64 steps)
 
     const int K = I.K;
     const int stride = K + kTabExtra;
     for (int t = threadIdx.x; t < 81; t += blockDim.x) lw_s[t / 9][t % 9] = I.lw[t / 9][t % 9];
+    for (int t = threadIdx.x; t < 27; t += blockDim.x) { slot_s[t / 3][t % 3] = I.c2slot[t / 3][t % 3]; cw_s[t / 3][t % 3] = I.c2w[t / 3][t % 3]; }
     for (int t = threadIdx.x; t < A.n_steps; t += blockDim.x) sT_s[t] = (real)A.tab[(size_t)(A.s0 + t) * stride + K];
+    for (int t = threadIdx.x; t < A.n_steps && t < 64; t += blockDim.x) tn_s[t] = A.tab[(size_t)(A.s0 + t) * stride + K + 2];
     if (TSRC)
         for (int t = threadIdx.x; t < A.n_steps * K; t += blockDim.x)
             ds_s[t] = (real)A.tab[(size_t)(A.s0 + t / K) * stride + (t % K)];
@@ -92,15 +102,24 @@ patch_persist_kernel(const InstDev I, const PersistArgs A, double upd_scale, dou
     const long long rowstride = (long long)I.ncols * M;
     const long long base = (long long)jr * M * rowstride + (long long)icl * M + a;
     real cE[M], cW[M], cN[M], cS[M], cC[M], cX[M], Gs[M];
+    real* Bw = Bs + (size_t)(threadIdx.x >> 5) * M * LANES * 12;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
         const real* p = brec + (base + b * rowstride) * 16;
-        real e, ww, n, s, x, cc, g, B0;
+        real e, ww, n, s, x, cc, g, B0, B1, B2, B3, B4, B5, B6, B7, B8;
         load_vec4<real>(p, e, ww, n, s);
         load_vec4<real>(p + 4, x, cc, g, B0);
-        if (!active) { e = ww = n = s = x = cc = g = real(0); }
+        load_vec4<real>(p + 8, B1, B2, B3, B4);
+        load_vec4<real>(p + 12, B5, B6, B7, B8);
+        if (!active) { e = ww = n = s = x = cc = g = real(0); B0 = B1 = B2 = B3 = B4 = B5 = B6 = B7 = B8 = real(0); }
         cE[b] = e; cW[b] = ww; cN[b] = n; cS[b] = s; cX[b] = x; cC[b] = cc; Gs[b] = g;
+        if (lane < LANES) {
+            real* o = Bw + ((size_t)b * LANES + lane) * 12;
+            o[0] = B0; o[1] = B1; o[2] = B2; o[3] = B3; o[4] = B4; o[5] = B5; o[6] = real(0); o[7] = real(0);
+            o[8] = B6; o[9] = B7; o[10] = B8; o[11] = real(0);
+        }
     }
+    __syncwarp();
     const int bo0 = A.bnd_off[warp], bo1 = A.bnd_off[warp + 1];
 
     for (int ls = 0; ls < A.n_steps; ++ls) {
@@ -115,9 +134,12 @@ patch_persist_kernel(const InstDev I, const PersistArgs A, double upd_scale, dou
                 const int* f = A.flags + nbw;
                 if (ld_acquire(f) < ls) {
                     unsigned long long t0 = global_ns();
+                    unsigned polls = 0;
                     while (ld_acquire(f) < ls) {
-                        __nanosleep(64);
-                        if (global_ns() - t0 > (unsigned long long)A.wait_ns) { late = true; break; }
+                        if ((++polls & 127) == 0) {
+                            if (global_ns() - t0 > (unsigned long long)A.wait_ns) { late = true; break; }
+                            __nanosleep(16);
+                        }
                     }
                 }
             }
@@ -125,88 +147,38 @@ patch_persist_kernel(const InstDev I, const PersistArgs A, double upd_scale, dou
                 if (lane == 0) atomicOr(I.err, ERR_TIMEOUT);
                 return;
             }
+            // the acquire loads of lanes 0..8 are ordered before the whole
+            // warp's stencil loads by the warp barrier
             __syncwarp();
-            __threadfence();
         }
 
-        // 3x3 stencil (L2 loads: the field changes during the kernel)
-        double stv[9];
-#pragma unroll
-        for (int pp = -1; pp <= 1; ++pp) {
-            int ii = wrap_col(I, i + pp);
-#pragma unroll
-            for (int qq = -1; qq <= 1; ++qq) stv[(pp + 1) * 3 + (qq + 1)] = __ldcg(Uc + (long long)(j + qq) * I.nxp + ii);
-        }
-        double ck[NC];
-        real ckr[NC];
-#pragma unroll
-        for (int r = 0; r < NC; ++r) {
-            int k = a + r * M;
-            double acc = 0.0;
-            if (k < 9) {
-#pragma unroll
-                for (int jj = 0; jj < 9; ++jj) acc = fma(lw_s[k][jj], stv[jj], acc);
-            }
-            ck[r] = acc;
-            ckr[r] = (real)acc;
-        }
         real cv[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) cv[k] = __shfl_sync(kFull, ckr[k / M], (qbase + k % M) & 31);
+        double c20, c02, u00;
+        macro_coeffs<M, real, true>(I, Uc, i, j, a, qbase, lw_s, slot_s, cw_s, cv, c20, c02, u00);
         double bias = 0.0;
-        if (I.restrict_mode == PD_RESTRICT_MACRO) {
-            double c20 = __shfl_sync(kFull, ck[3 / M], (qbase + 3 % M) & 31);
-            double c02 = __shfl_sync(kFull, ck[5 / M], (qbase + 5 % M) & 31);
+        if (I.restrict_mode == PD_RESTRICT_MACRO)
             bias = (I.dx * I.dx * c20 + I.dy * I.dy * c02) * (1.0 / 6.0);
-        }
 
         // forcing R = sum_k B_k c_k + s(T) Gs
         const real sT = sT_s[ls];
         real w[M], Rr[M];
 #pragma unroll
         for (int b = 0; b < M; ++b) {
-            const real* p = brec + (base + b * rowstride) * 16;
-            real t0, t1, t2, B0, B1, B2, B3, B4, B5, B6, B7, B8;
-            load_vec4<real>(p + 4, t0, t1, t2, B0);
-            load_vec4<real>(p + 8, B1, B2, B3, B4);
-            load_vec4<real>(p + 12, B5, B6, B7, B8);
+            const real* o = Bw + ((size_t)b * LANES + (lane < LANES ? lane : 0)) * 12;
+            real B0 = o[0], B1 = o[1], B2 = o[2], B3 = o[3], B4 = o[4], B5 = o[5];
             real r = sT * Gs[b];
             r = fma(B0, cv[0], r); r = fma(B1, cv[1], r); r = fma(B2, cv[2], r);
             r = fma(B3, cv[3], r); r = fma(B4, cv[4], r); r = fma(B5, cv[5], r);
-            r = fma(B6, cv[6], r); r = fma(B7, cv[7], r); r = fma(B8, cv[8], r);
+            // the edge-gap terms (c21, c12, c22) enter only at points next to a ghost
+            if (b == 0 || b == M - 1 || a == 0 || a == M - 1) {
+                real B6 = o[8], B7 = o[9], B8 = o[10];
+                r = fma(B6, cv[6], r); r = fma(B7, cv[7], r); r = fma(B8, cv[8], r);
+            }
             Rr[b] = active ? r : real(0);
             w[b] = real(0);
         }
 
-        // K micro steps (rolling row window, as in the per-step kernel)
-        const real* dsr = ds_s + (TSRC ? ls * K : 0);
-        for (int k = 0; k < K; ++k) {
-            const real ds = TSRC ? dsr[k] : real(0);
-            real e_n = __shfl_down_sync(kFull, w[0], 1);
-            real v_n = __shfl_up_sync(kFull, w[0], 1);
-            real d_n = e_n - v_n, d_c = d_n, d_p = d_n;
-            real w_prev = real(0);
-#pragma unroll
-            for (int b = 0; b < M; ++b) {
-                const real e_c = e_n, v_c = v_n;
-                d_p = d_c;
-                d_c = d_n;
-                if (b + 1 < M) {
-                    e_n = __shfl_down_sync(kFull, w[b + 1], 1);
-                    v_n = __shfl_up_sync(kFull, w[b + 1], 1);
-                    if (CROSS) d_n = e_n - v_n;
-                }
-                real acc = fma(cC[b], w[b], Rr[b]);
-                acc = fma(cE[b], e_c, acc);
-                acc = fma(cW[b], v_c, acc);
-                if (b + 1 < M) acc = fma(cN[b], w[b + 1], acc);
-                if (b > 0) acc = fma(cS[b], w_prev, acc);
-                if (CROSS && b > 0 && b + 1 < M) acc = fma(cX[b], d_n - d_p, acc);
-                if (TSRC) acc = fma(ds, Gs[b], acc);
-                w_prev = w[b];
-                w[b] = acc;
-            }
-        }
+        burst_steps<M, CROSS, TSRC, real>(w, cE, cW, cN, cS, cC, cX, Gs, Rr, ds_s + (TSRC ? ls * K : 0), K);
 
         // restriction, time derivative, projective step into the other buffer
         real col = real(0.5) * (w[0] + w[M - 1]);
@@ -223,11 +195,11 @@ patch_persist_kernel(const InstDev I, const PersistArgs A, double upd_scale, dou
             double inc = fma((double)col, upd_scale, bias * bias_scale);
             if (!isfinite(inc)) atomicOr(I.err, ERR_NONFINITE);
             long long node = (long long)j * I.nxp + i;
-            Un[node] = __ldcg(Uc + node) + inc;
+            Un[node] = u00 + inc;
         }
         // Dirichlet data at T_{n+1} on the boundary nodes this warp owns
         if (bo1 > bo0) {
-            double tn = A.tab[(size_t)n * stride + K + 2];
+            double tn = ls < 64 ? tn_s[ls] : A.tab[(size_t)n * stride + K + 2];
             for (int k = bo0 + lane; k < bo1; k += 32) {
                 int idx = A.bnd_idx[k];
                 int2 ij = I.bnd_ij[idx];
@@ -235,11 +207,10 @@ patch_persist_kernel(const InstDev I, const PersistArgs A, double upd_scale, dou
                 Un[(long long)ij.y * I.nxp + ij.x] = exact_solution(I.sol, xy.x, xy.y, tn);
             }
         }
+        // the warp barrier orders every lane's stores of U before lane 0's
+        // release store (release is cumulative)
         __syncwarp();
-        if (lane == 0 && warp != A.silent_warp) {
-            __threadfence();
-            st_release(A.flags + warp, ls + 1);
-        }
+        if (lane == 0 && warp != A.silent_warp) st_release(A.flags + warp, ls + 1);
     }
 }
 
@@ -247,9 +218,9 @@ template <int M, typename real>
 cudaError_t launch_m(const InstDev& I, const PersistArgs& A, cudaStream_t st)
 {
     int n_item = persist_item_warps(I);
-    int bs = 128;
+    int bs = kPersistBlock;
     unsigned nb = (unsigned)((n_item * 32 + bs - 1) / bs);
-    size_t smem = sizeof(real) * ((size_t)A.n_steps * (I.has_tsrc ? I.K : 0) + A.n_steps);
+    size_t smem = persist_smem_bytes(I, sizeof(real), A.n_steps);
     double bias_scale = A.dtm * I.inv_tau;
     double upd_scale = bias_scale * I.inv_nn;
     cudaLaunchConfig_t cfg = {};
@@ -263,6 +234,12 @@ cudaError_t launch_m(const InstDev& I, const PersistArgs& A, cudaStream_t st)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     bool cross = I.has_cross != 0, tsrc = I.has_tsrc != 0;
+    cudaError_t e = cudaSuccess;
+    if (cross && tsrc) e = cudaFuncSetAttribute(patch_persist_kernel<M, true, true, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (cross) e = cudaFuncSetAttribute(patch_persist_kernel<M, true, false, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (tsrc) e = cudaFuncSetAttribute(patch_persist_kernel<M, false, true, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else e = cudaFuncSetAttribute(patch_persist_kernel<M, false, false, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     if (cross && tsrc) return cudaLaunchKernelEx(&cfg, patch_persist_kernel<M, true, true, real>, I, A, upd_scale, bias_scale, n_item);
     if (cross) return cudaLaunchKernelEx(&cfg, patch_persist_kernel<M, true, false, real>, I, A, upd_scale, bias_scale, n_item);
     if (tsrc) return cudaLaunchKernelEx(&cfg, patch_persist_kernel<M, false, true, real>, I, A, upd_scale, bias_scale, n_item);
@@ -275,10 +252,15 @@ int max_blocks_per_sm(const InstDev& I, size_t smem)
     int nb = 0;
     bool cross = I.has_cross != 0, tsrc = I.has_tsrc != 0;
     cudaError_t e;
-    if (cross && tsrc) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_persist_kernel<M, true, true, real>, 128, smem);
-    else if (cross) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_persist_kernel<M, true, false, real>, 128, smem);
-    else if (tsrc) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_persist_kernel<M, false, true, real>, 128, smem);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_persist_kernel<M, false, false, real>, 128, smem);
+    if (cross && tsrc) e = cudaFuncSetAttribute(patch_persist_kernel<M, true, true, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (cross) e = cudaFuncSetAttribute(patch_persist_kernel<M, true, false, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (tsrc) e = cudaFuncSetAttribute(patch_persist_kernel<M, false, true, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else e = cudaFuncSetAttribute(patch_persist_kernel<M, false, false, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return 0;
+    if (cross && tsrc) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_persist_kernel<M, true, true, real>, kPersistBlock, smem);
+    else if (cross) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_persist_kernel<M, true, false, real>, kPersistBlock, smem);
+    else if (tsrc) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_persist_kernel<M, false, true, real>, kPersistBlock, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_persist_kernel<M, false, false, real>, kPersistBlock, smem);
     return e == cudaSuccess ? nb : 0;
 }
 
@@ -302,11 +284,23 @@ int persist_item_warps(const InstDev& I)
     return ((I.ncols + P - 1) / P) * I.nrows;
 }
 
+// dynamic shared memory of one 4-warp block: forcing basis + time table of the chunk
+size_t persist_smem_bytes(const InstDev& I, size_t es, int n_steps)
+{
+    int P = 32 / I.mx;
+    size_t basis = (size_t)(kPersistBlock / 32) * I.mx * (P * I.mx) * 12 * es;
+    return basis + es * ((size_t)n_steps * (I.has_tsrc ? I.K : 0) + n_steps);
+}
+
 int persist_max_steps(const InstDev& I, int prec)
 {
+    // keep eight two-warp blocks per SM: about 27 KB of shared memory per block
     size_t es = prec == PD_FP32 ? 4 : 8;
+    size_t budget = 27 * 1024;
+    size_t base = persist_smem_bytes(I, es, 0);
     size_t per_step = es * ((I.has_tsrc ? I.K : 0) + 1);
-    return (int)((32 * 1024) / per_step);
+    if (base + per_step > budget) budget = base + 16 * per_step;   // FP64: fewer blocks per SM anyway
+    return (int)((budget - base) / per_step);
 }
 
 bool persist_fits(const InstDev& I, int prec)
@@ -315,12 +309,12 @@ bool persist_fits(const InstDev& I, int prec)
     int steps = persist_max_steps(I, prec);
     if (steps < 1) return false;
     size_t es = prec == PD_FP32 ? 4 : 8;
-    size_t smem = es * ((size_t)steps * ((I.has_tsrc ? I.K : 0) + 1));
+    size_t smem = persist_smem_bytes(I, es, steps);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = prec == PD_FP32 ? blocks_per_sm<float>(I, smem) : blocks_per_sm<double>(I, smem);
-    long long blocks = ((long long)persist_item_warps(I) * 32 + 127) / 128;
+    long long blocks = ((long long)persist_item_warps(I) * 32 + kPersistBlock - 1) / kPersistBlock;
     return per_sm > 0 && blocks <= (long long)per_sm * nsm;
 }
 
