@@ -120,19 +120,23 @@ typedef struct {
     int nxp, nyp;                 /* macro nodes along xi, eta */
     int m_xi, m_eta, k_micro, prec;
     long long u_offset;           /* offset (in doubles) of this instance in U_dev */
-    long long patch_offset;       /* offset (in patches) of this instance in dU_dev */
+    long long patch_offset;       /* offset (in patches) of this instance in dU_dev and the bias section */
+    long long point_offset;       /* offset (in micro points) of this instance in the u0, r, w sections */
+    long long edge_offset;        /* offset (in entries) of this instance in the edge section */
     double dt_micro;              /* micro forward-Euler step (reading G8) */
     double tau;                   /* burst length K * dt_micro */
     double dt_macro_suggested;    /* half the macro explicit bound (reading G9) */
     size_t state_bytes;           /* whole micro-state buffer (all instances) */
     size_t off_u0, off_r, off_w, off_edge, off_bias; /* section offsets, 256-byte aligned */
-    int edge_stride;              /* max(m_xi, m_eta) + 2 */
+    int edge_stride;              /* max(m_xi, m_eta) + 2 of this instance */
     int exec_path;                /* pd_step path: 0 separate passes, 1 one fused kernel per
-                                     macro step, 2 persistent dataflow kernel */
+                                     macro step, 2 persistent dataflow kernel, 3 batched
+                                     work-queue kernel (several instances or table storage) */
     int chunk_steps;              /* macro steps per persistent launch (path 2) */
 } pd_info;
 
-/* Create a grid of n_inst instances, descs[0..n_inst-1] (host array, copied).
+/* Create a grid of n_inst instances, descs[0..n_inst-1] (host array, copied);
+ * instances may differ in every field except the precision.
  * `cuda_stream` is a cudaStream_t (NULL = default stream).  Allocates the
  * per-instance coefficient and scratch buffers on the current device.
  * Errors: PD_EINVAL (bad descriptor), PD_ENOMEM, PD_ECUDA. */
@@ -202,6 +206,22 @@ pd_status pd_project(pd_grid* g, double* U_dev, const double* dU_dev, double t, 
  * Errors: PD_EINVAL, PD_ESTATE (coefficients missing), PD_ECUDA. */
 pd_status pd_step(pd_grid* g, double* U_dev, double t0, double dt_macro, int n_macro);
 pd_status pd_set_graph_mode(pd_grid* g, int enabled);
+
+/* Coefficient storage (call before pd_set_coeffs): 0 auto (default: 1-D metric
+ * tables for constant-coefficient, source-free instances when the grid holds
+ * several instances, else per-point records), 1 records, 2 tables where
+ * possible.  Table storage needs O(N m) memory per instance instead of O(N^2 m^2). */
+pd_status pd_set_coeff_storage(pd_grid* g, int mode);
+
+/* Batched execution (grids with several instances, or table storage): one
+ * kernel per macro step over all instances, warps pulling patch groups from a
+ * device work queue (costliest micro size first).  The autotuner times
+ * n_trial_steps macro steps of each candidate (64/128/256 threads per block x
+ * full/half patches per warp) on scratch fields and keeps the fastest; it runs
+ * on the first batched pd_step unless disabled with pd_set_autotune(g, 0, ...),
+ * which fixes the configuration instead. */
+pd_status pd_autotune(pd_grid* g, int n_trial_steps, int* block, int* half_patches);
+pd_status pd_set_autotune(pd_grid* g, int enabled, int block, int half_patches);
 
 /* Persistent dataflow execution of pd_step (default on).  When all patch warps
  * of an instance fit on the device at once, a chunk of macro steps runs in one

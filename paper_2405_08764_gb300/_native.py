@@ -50,6 +50,7 @@ class Info(C.Structure):
         ("n_patch", C.c_int), ("n_macro", C.c_int), ("nxp", C.c_int), ("nyp", C.c_int),
         ("m_xi", C.c_int), ("m_eta", C.c_int), ("k_micro", C.c_int), ("prec", C.c_int),
         ("u_offset", C.c_longlong), ("patch_offset", C.c_longlong),
+        ("point_offset", C.c_longlong), ("edge_offset", C.c_longlong),
         ("dt_micro", C.c_double), ("tau", C.c_double), ("dt_macro_suggested", C.c_double),
         ("state_bytes", C.c_size_t), ("off_u0", C.c_size_t), ("off_r", C.c_size_t),
         ("off_w", C.c_size_t), ("off_edge", C.c_size_t), ("off_bias", C.c_size_t),
@@ -75,6 +76,9 @@ SIGNATURES = {
     "pd_step": (C.c_int, [_GP, _VP, C.c_double, C.c_double, C.c_int]),
     "pd_set_graph_mode": (C.c_int, [_GP, C.c_int]),
     "pd_set_persistent": (C.c_int, [_GP, C.c_int]),
+    "pd_set_coeff_storage": (C.c_int, [_GP, C.c_int]),
+    "pd_autotune": (C.c_int, [_GP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pd_set_autotune": (C.c_int, [_GP, C.c_int, C.c_int, C.c_int]),
     "pd_set_wait_limit": (C.c_int, [_GP, C.c_longlong]),
     "pd_test_silence_warp": (C.c_int, [_GP, C.c_int]),
     "pd_sync": (C.c_int, [_GP]),

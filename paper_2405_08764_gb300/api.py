@@ -72,7 +72,8 @@ class Grid:
     the same micro size and precision).  prec: "fp32" (FP32 bursts, FP64
     restriction and projection) or "fp64"."""
 
-    def __init__(self, probs, prec: str = "fp32", graphs: bool = True, persistent: bool | None = None):
+    def __init__(self, probs, prec: str = "fp32", graphs: bool = True, persistent: bool | None = None,
+                 storage: str = "auto", autotune: bool = True):
         """persistent: None follows the PD_PERSISTENT environment variable (default on;
         "0" selects one fused launch per macro step, e.g. for kernel profilers that
         cannot replay cooperative launches)."""
@@ -95,6 +96,9 @@ class Grid:
         self.h = h
         self.L.pd_set_graph_mode(self.h, 1 if graphs else 0)
         self.L.pd_set_persistent(self.h, 1 if persistent else 0)
+        N.check(self.L.pd_set_coeff_storage(self.h, {"auto": 0, "records": 1, "tables": 2}[storage]), self.h)
+        if not autotune:
+            N.check(self.L.pd_set_autotune(self.h, 0, 128, 0), self.h)
         for k, p in enumerate(self.probs):
             c, amp = coeff_desc(p)
             N.check(self.L.pd_set_coeffs(self.h, k, C.byref(c)), self.h)
@@ -128,20 +132,22 @@ class Grid:
         return torch.zeros(self.state_bytes, dtype=torch.uint8, device=self.device)
 
     def state_views(self, state: torch.Tensor, inst: int = 0) -> dict:
-        """typed views of the micro-state sections (all instances)."""
+        """typed views of instance `inst`'s parts of the micro-state sections."""
         i = self.info(inst)
-        P, mx, my, es = self.n_patch_total, i["m_xi"], i["m_eta"], i["edge_stride"]
+        P, mx, my, es = i["n_patch"], i["m_xi"], i["m_eta"], i["edge_stride"]
         rdt = torch.float32 if self.prec == "fp32" else torch.float64
         rb = 4 if self.prec == "fp32" else 8
 
-        def sec(off, n, dt, b):
-            return state[off:off + n * b].view(dt)
+        def sec(off, start, n, dt, b):
+            o = off + start * b
+            return state[o:o + n * b].view(dt)
+        pt, eo, po = i["point_offset"], i["edge_offset"], i["patch_offset"]
         return {
-            "u0": sec(i["off_u0"], P * mx * my, torch.float64, 8).view(P, my, mx),
-            "r": sec(i["off_r"], P * mx * my, rdt, rb).view(P, my, mx),
-            "w": sec(i["off_w"], P * mx * my, rdt, rb).view(P, my, mx),
-            "edge": sec(i["off_edge"], P * 4 * es, torch.float64, 8).view(P, 4, es),
-            "bias": sec(i["off_bias"], P, torch.float64, 8),
+            "u0": sec(i["off_u0"], pt, P * mx * my, torch.float64, 8).view(P, my, mx),
+            "r": sec(i["off_r"], pt, P * mx * my, rdt, rb).view(P, my, mx),
+            "w": sec(i["off_w"], pt, P * mx * my, rdt, rb).view(P, my, mx),
+            "edge": sec(i["off_edge"], eo, P * 4 * es, torch.float64, 8).view(P, 4, es),
+            "bias": sec(i["off_bias"], po, P, torch.float64, 8),
         }
 
     # -- C-ABI entry points ----------------------------------------------------
@@ -191,6 +197,11 @@ class Grid:
 
     def launches(self) -> int:
         return int(self.L.pd_launch_count(self.h))
+
+    def autotune(self, n_trial_steps: int = 2):
+        b, h = C.c_int(), C.c_int()
+        N.check(self.L.pd_autotune(self.h, int(n_trial_steps), C.byref(b), C.byref(h)), self.h)
+        return b.value, bool(h.value)
 
     def set_wait_limit(self, ns: int):
         N.check(self.L.pd_set_wait_limit(self.h, int(ns)), self.h)

@@ -32,6 +32,8 @@ struct Inst {
     bool coef_set = false;
     double dt = 0, tau = 0, dtm_sugg = 0;
     std::vector<int2> bnd_host;
+    double* col_tab = nullptr;       // table coefficient mode
+    double* row_tab = nullptr;
     int* bnd_off = nullptr;          // boundary nodes owned by each item warp (persistent kernel)
     int* bnd_idx = nullptr;
     int n_item = 0;
@@ -86,6 +88,22 @@ struct pd_grid {
     bool persist = true;
     long long wait_ns = 250000000LL;
     int silent_warp = -1;
+    // batched execution (many instances or table-mode coefficients)
+    int storage = 0;                 // 0 auto, 1 records, 2 tables
+    InstDev* insts_dev = nullptr;
+    BatchItem* items_dev = nullptr;
+    int n_items = 0;
+    bool batch_dirty = true;
+    double* dtm_dev = nullptr;
+    std::vector<double> dtm_host;
+    long long* tab_off_dev = nullptr;
+    int* counters = nullptr;
+    size_t counters_n = 0;
+    int bt_block = 128;
+    bool bt_half = false;
+    bool bt_tuned = false;
+    bool autotune = true;
+    std::vector<double> tune_log;   // ms per macro step of each candidate
 };
 
 namespace {
@@ -169,7 +187,7 @@ void poly_weights(InstDev& I)
         for (int c = 0; c < 3; ++c) { I.c2slot[k][c] = sl[k][c]; I.c2w[k][c] = ww[k][c]; }
 }
 
-void fill_inst(Inst& s, long long u_off, long long p_off)
+void fill_inst(Inst& s, long long u_off, long long p_off, long long pt_off, long long e_off)
 {
     const pd_grid_desc& d = s.d;
     InstDev& I = s.I;
@@ -191,7 +209,13 @@ void fill_inst(Inst& s, long long u_off, long long p_off)
     I.dx = I.hx / (d.m_xi - 1);
     I.dy = I.hy / (d.m_eta - 1);
     for (int k = 0; k < 4; ++k) I.map_p[k] = d.map_p[k];
-    I.u_off = u_off; I.p_off = p_off;
+    I.u_off = u_off; I.p_off = p_off; I.pt_off = pt_off; I.e_off = e_off;
+    I.inv_dx = 1.0 / I.dx; I.inv_dy = 1.0 / I.dy;
+    I.inv_dx2 = 1.0 / (I.dx * I.dx); I.inv_dy2 = 1.0 / (I.dy * I.dy);
+    I.inv_4dxdy = 1.0 / (4.0 * I.dx * I.dy);
+    I.ppw = 32 / d.m_xi;
+    I.coef_mode = COEF_RECORDS;
+    I.edge_stride = (d.m_xi > d.m_eta ? d.m_xi : d.m_eta) + 2;
     poly_weights(I);
     s.bnd_host.clear();
     for (int j = 0; j < I.nyp; ++j)
@@ -241,19 +265,24 @@ pd_status all_coeffs_set(pd_grid* g)
     return PD_OK;
 }
 
+// micro-state layout over all instances: section of each kind holds every
+// instance's patches back to back (per-instance offsets pt_off / e_off / p_off)
 void layout(const pd_grid* g, const Inst& s, pd_info& o)
 {
-    long long P = g->n_patch_total;
-    int mm = s.d.m_xi * s.d.m_eta;
-    size_t es = s.d.prec == PD_FP32 ? 4 : 8;
-    // all instances of a grid share m and precision in the state buffer layout
-    o.edge_stride = (s.d.m_xi > s.d.m_eta ? s.d.m_xi : s.d.m_eta) + 2;
+    long long pts = 0, edges = 0;
+    bool fp32 = s.d.prec == PD_FP32;
+    for (auto& t : g->inst) {
+        pts += (long long)t.I.n_patch * t.I.mx * t.I.my;
+        edges += (long long)t.I.n_patch * 4 * t.I.edge_stride;
+    }
+    size_t es = fp32 ? 4 : 8;
+    o.edge_stride = s.I.edge_stride;
     o.off_u0 = align256(kStateHeader);
-    o.off_r = align256(o.off_u0 + (size_t)P * mm * 8);
-    o.off_w = align256(o.off_r + (size_t)P * mm * es);
-    o.off_edge = align256(o.off_w + (size_t)P * mm * es);
-    o.off_bias = align256(o.off_edge + (size_t)P * 4 * o.edge_stride * 8);
-    o.state_bytes = align256(o.off_bias + (size_t)P * 8);
+    o.off_r = align256(o.off_u0 + (size_t)pts * 8);
+    o.off_w = align256(o.off_r + (size_t)pts * es);
+    o.off_edge = align256(o.off_w + (size_t)pts * es);
+    o.off_bias = align256(o.off_edge + (size_t)edges * 8);
+    o.state_bytes = align256(o.off_bias + (size_t)g->n_patch_total * 8);
 }
 
 pd_status ensure_step_buffers(pd_grid* g, int n_macro)
@@ -358,6 +387,265 @@ pd_status step_fallback(pd_grid* g, double* U, double t0, const std::vector<doub
     return PD_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// batched execution
+
+bool use_batch(const pd_grid* g)
+{
+    if (g->inst.size() > 1) return true;
+    for (auto& s : g->inst) if (s.I.coef_mode != COEF_RECORDS) return true;
+    return false;
+}
+
+bool all_batch_supported(const pd_grid* g)
+{
+    for (auto& s : g->inst) if (!batch_supported(s.I)) return false;
+    return true;
+}
+
+pd_status prepare_batch(pd_grid* g)
+{
+    if (!g->batch_dirty) return PD_OK;
+    PD_CUDA(g, cudaStreamSynchronize(g->stream));   // no kernel may still read the old tables
+    size_t n = g->inst.size();
+    std::vector<InstDev> host(n);
+    std::vector<BatchItem> items;
+    for (size_t k = 0; k < n; ++k) {
+        Inst& s = g->inst[k];
+        int P = 32 / s.I.mx;
+        s.I.ppw = g->bt_half ? std::max(1, (P + 1) / 2) : P;
+        host[k] = s.I;
+    }
+    // patch groups, costliest micro size first so the tail of the queue holds small items
+    std::vector<size_t> order(n);
+    for (size_t k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return g->inst[x].I.mx > g->inst[y].I.mx; });
+    for (size_t k : order) {
+        const InstDev& I = g->inst[k].I;
+        int wpr = (I.ncols + I.ppw - 1) / I.ppw;
+        for (int jr = 0; jr < I.nrows; ++jr)
+            for (int wc = 0; wc < wpr; ++wc) items.push_back(BatchItem{ (int)k, 0, jr, wc });
+    }
+    for (size_t k = 0; k < n; ++k) {
+        int chunks = (g->inst[k].I.n_bnd + 31) / 32;
+        for (int c = 0; c < chunks; ++c) items.push_back(BatchItem{ (int)k, 1, c, 0 });
+    }
+    if (!g->insts_dev) PD_CUDA(g, cudaMalloc(&g->insts_dev, sizeof(InstDev) * n));
+    PD_CUDA(g, cudaMemcpy(g->insts_dev, host.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice));
+    cudaFree(g->items_dev);
+    PD_CUDA(g, cudaMalloc(&g->items_dev, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)));
+    PD_CUDA(g, cudaMemcpy(g->items_dev, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+    g->n_items = (int)items.size();
+    g->batch_dirty = false;
+    for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+    g->gcache.clear();
+    return PD_OK;
+}
+
+bool batch_needs_tables(const pd_grid* g)
+{
+    for (auto& s : g->inst) if (s.I.has_tsrc || s.I.sol != PD_SOL_NONE) return true;
+    return false;
+}
+
+bool batch_tsrc(const pd_grid* g)
+{
+    for (auto& s : g->inst) if (s.I.has_tsrc) return true;
+    return false;
+}
+
+pd_status batch_buffers(pd_grid* g, int n_macro, const std::vector<double>& dtm)
+{
+    size_t n = g->inst.size();
+    if (!g->dtm_dev) PD_CUDA(g, cudaMalloc(&g->dtm_dev, sizeof(double) * n));
+    if (g->dtm_host != dtm) {
+        PD_CUDA(g, cudaStreamSynchronize(g->stream));
+        PD_CUDA(g, cudaMemcpy(g->dtm_dev, dtm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        g->dtm_host = dtm;
+    }
+    if ((size_t)n_macro > g->counters_n) {
+        if (g->counters) { cudaStreamSynchronize(g->stream); cudaFree(g->counters); }
+        PD_CUDA(g, cudaMalloc(&g->counters, sizeof(int) * n_macro));
+        g->counters_n = n_macro;
+        for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+        g->gcache.clear();
+    }
+    if (!g->U_scratch) {
+        PD_CUDA(g, cudaMalloc(&g->U_scratch, sizeof(double) * g->n_macro_total));
+        g->U_scratch_n = (size_t)g->n_macro_total;
+    }
+    return PD_OK;
+}
+
+// time tables of every instance for n_macro steps (only when some instance has a
+// time-dependent source or Dirichlet data)
+pd_status batch_time_tables(pd_grid* g, double t0, int n_macro, const std::vector<double>& dtm)
+{
+    size_t n = g->inst.size();
+    std::vector<long long> off(n + 1, 0);
+    for (size_t k = 0; k < n; ++k) off[k + 1] = off[k] + (long long)n_macro * (g->inst[k].I.K + kTabExtra);
+    size_t need = (size_t)off[n];
+    if (need > g->tab_n) {
+        if (g->tab) { cudaStreamSynchronize(g->stream); cudaFree(g->tab); }
+        PD_CUDA(g, cudaMalloc(&g->tab, sizeof(double) * need));
+        g->tab_n = need;
+        for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
+        g->gcache.clear();
+    }
+    if (!g->tab_off_dev) PD_CUDA(g, cudaMalloc(&g->tab_off_dev, sizeof(long long) * (n + 1)));
+    PD_CUDA(g, cudaStreamSynchronize(g->stream));
+    PD_CUDA(g, cudaMemcpy(g->tab_off_dev, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+    PD_CUDA(g, launch_batch_time_tables(g->insts_dev, (int)n, g->dtm_dev, t0, n_macro, g->tab_off_dev, g->tab, off[n], g->stream));
+    g->launches += 1;
+    return PD_OK;
+}
+
+int batch_grid(const pd_grid* g, int block)
+{
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
+    int per = batch_blocks_per_sm(g->inst[0].d.prec, batch_tsrc(g), block);
+    return std::max(1, per) * nsm;
+}
+
+pd_status enqueue_batch(pd_grid* g, double* U, int n_macro, cudaStream_t st, int& n_launch, bool tables)
+{
+    PD_CUDA(g, cudaMemsetAsync(g->counters, 0, sizeof(int) * n_macro, st));
+    int block = g->bt_block;
+    int grid = batch_grid(g, block);
+    for (int t = 0; t < n_macro; ++t) {
+        BatchArgs a;
+        a.insts = g->insts_dev; a.items = g->items_dev; a.n_items = g->n_items;
+        a.counter = g->counters + t;
+        a.Ubase = U; a.Sbase = g->U_scratch; a.parity = t & 1;
+        a.dtm = g->dtm_dev;
+        a.tab = tables ? g->tab : nullptr;
+        a.tab_off = tables ? g->tab_off_dev : nullptr;
+        a.step = t;
+        cudaError_t e = launch_batch(g->inst[0].d.prec, batch_tsrc(g), a, block, grid, st);
+        if (e != cudaSuccess) return cuda_fail(g, e, "batched step");
+        n_launch += 1;
+    }
+    if (n_macro & 1) {
+        cudaError_t e = cudaMemcpyAsync(U, g->U_scratch, sizeof(double) * g->n_macro_total, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(g, e, "copy back");
+    }
+    return PD_OK;
+}
+
+// Autotuner: time a few macro steps of every candidate (threads per block x
+// patches per warp) on scratch buffers and keep the fastest.
+pd_status batch_autotune(pd_grid* g, int n_trial)
+{
+    std::vector<double> dtm(g->inst.size());
+    for (size_t k = 0; k < g->inst.size(); ++k) dtm[k] = g->inst[k].dtm_sugg;
+    pd_status rc = batch_buffers(g, n_trial, dtm);
+    if (rc) return rc;
+    double* trial = nullptr;
+    PD_CUDA(g, cudaMalloc(&trial, sizeof(double) * g->n_macro_total));
+    PD_CUDA(g, cudaMemsetAsync(trial, 0, sizeof(double) * g->n_macro_total, g->stream));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    int best_block = g->bt_block;
+    bool best_half = g->bt_half;
+    g->tune_log.clear();
+    const int blocks[3] = { 64, 128, 256 };
+    for (int hv = 0; hv < 2; ++hv) {
+        g->bt_half = hv != 0;
+        g->batch_dirty = true;
+        rc = prepare_batch(g);
+        if (rc) break;
+        bool tables = batch_needs_tables(g);
+        if (tables) { rc = batch_time_tables(g, 0.0, n_trial, dtm); if (rc) break; }
+        for (int bi = 0; bi < 3; ++bi) {
+            g->bt_block = blocks[bi];
+            int nl = 0;
+            rc = enqueue_batch(g, trial, 1, g->stream, nl, tables);   // warm-up
+            if (rc) break;
+            cudaEventRecord(e0, g->stream);
+            rc = enqueue_batch(g, trial, n_trial, g->stream, nl, tables);
+            if (rc) break;
+            cudaEventRecord(e1, g->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            double per = ms / n_trial;
+            g->tune_log.push_back(per);
+            if (per < best) { best = per; best_block = blocks[bi]; best_half = g->bt_half; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(g->stream);
+    cudaFree(trial);
+    int herr = 0;
+    cudaMemcpy(&herr, g->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (herr) cudaMemset(g->err, 0, sizeof(int));   // trial runs on zero fields; nothing to report
+    g->bt_block = best_block;
+    g->bt_half = best_half;
+    g->batch_dirty = true;
+    g->bt_tuned = true;
+    if (rc) return rc;
+    return prepare_batch(g);
+}
+
+pd_status step_batch(pd_grid* g, double* U, double t0, const std::vector<double>& dtm, int n_macro)
+{
+    if (g->autotune && !g->bt_tuned) {
+        pd_status rc = batch_autotune(g, 2);
+        if (rc) return rc;
+    }
+    pd_status rc = prepare_batch(g);
+    if (rc) return rc;
+    rc = batch_buffers(g, n_macro, dtm);
+    if (rc) return rc;
+    bool tables = batch_needs_tables(g);
+    if (tables) { rc = batch_time_tables(g, t0, n_macro, dtm); if (rc) return rc; }
+    if (!g->graphs) {
+        int nl = 0;
+        rc = enqueue_batch(g, U, n_macro, g->stream, nl, tables);
+        g->launches += nl;
+        return rc;
+    }
+    GraphKey key{ (uintptr_t)U, n_macro, dtm };
+    auto it = g->gcache.find(key);
+    if (it == g->gcache.end()) {
+        GraphEntry ge;
+        PD_CUDA(g, cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+        int nl = 0;
+        rc = enqueue_batch(g, U, n_macro, g->cap, nl, tables);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(g, e, "graph instantiate"); }
+        ge.graph = graph;
+        ge.n_nodes = nl;
+        it = g->gcache.emplace(key, ge).first;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (g->timing) {
+        for (cudaEvent_t* e : { &e0, &e1 }) {
+            if (!g->tfree.empty()) { *e = g->tfree.back(); g->tfree.pop_back(); }
+            else PD_CUDA(g, cudaEventCreate(e));
+        }
+        PD_CUDA(g, cudaEventRecord(e0, g->stream));
+    }
+    PD_CUDA(g, cudaGraphLaunch(it->second.exec, g->stream));
+    g->launches += it->second.n_nodes;
+    if (g->timing) {
+        PD_CUDA(g, cudaEventRecord(e1, g->stream));
+        g->tev.emplace_back(e0, e1);
+        g->t_launches += n_macro;
+    }
+    return PD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -390,7 +678,7 @@ pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_strea
     pd_grid* g = new pd_grid();
     g->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&g->device);
-    long long u_off = 0, p_off = 0;
+    long long u_off = 0, p_off = 0, pt_off = 0, e_off = 0;
     g->inst.resize(n_inst);
     for (int k = 0; k < n_inst; ++k) {
         std::string why;
@@ -398,14 +686,16 @@ pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_strea
             delete g;
             return PD_EINVAL;
         }
-        if (k > 0 && (descs[k].m_xi != descs[0].m_xi || descs[k].m_eta != descs[0].m_eta || descs[k].prec != descs[0].prec)) {
+        if (k > 0 && descs[k].prec != descs[0].prec) {
             delete g;
             return PD_EINVAL;
         }
         g->inst[k].d = descs[k];
-        fill_inst(g->inst[k], u_off, p_off);
+        fill_inst(g->inst[k], u_off, p_off, pt_off, e_off);
         u_off += (long long)g->inst[k].I.nxp * g->inst[k].I.nyp;
         p_off += g->inst[k].I.n_patch;
+        pt_off += (long long)g->inst[k].I.n_patch * g->inst[k].I.mx * g->inst[k].I.my;
+        e_off += (long long)g->inst[k].I.n_patch * 4 * g->inst[k].I.edge_stride;
     }
     g->n_macro_total = u_off;
     g->n_patch_total = p_off;
@@ -415,11 +705,7 @@ pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_strea
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
     for (int k = 0; k < n_inst && e == cudaSuccess; ++k) {
         Inst& s = g->inst[k];
-        size_t es = s.d.prec == PD_FP32 ? 4 : 8;
-        size_t npts = (size_t)s.I.n_patch * s.I.mx * s.I.my;
-        e = cudaMalloc(&s.rec, npts * 8 * es);
-        if (e == cudaSuccess) e = cudaMalloc(&s.brec, npts * 16 * es);
-        if (e == cudaSuccess) e = cudaMalloc(&s.bnd_ij, sizeof(int2) * (s.I.n_bnd + 1));
+        e = cudaMalloc(&s.bnd_ij, sizeof(int2) * (s.I.n_bnd + 1));
         if (e == cudaSuccess) e = cudaMalloc(&s.bnd_xy, sizeof(double2) * (s.I.n_bnd + 1));
         if (e == cudaSuccess && s.I.n_bnd)
             e = cudaMemcpy(s.bnd_ij, s.bnd_host.data(), sizeof(int2) * s.I.n_bnd, cudaMemcpyHostToDevice);
@@ -467,9 +753,10 @@ pd_status pd_destroy_grid(pd_grid* g)
     for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
     for (auto& pr : g->tev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto e : g->tfree) cudaEventDestroy(e);
-    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
+    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.col_tab); cudaFree(s.row_tab); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
     cudaFree(g->err); cudaFree(g->acc); cudaFree(g->U_scratch); cudaFree(g->tab);
     cudaFree(g->state); cudaFree(g->dU); cudaFree(g->flags);
+    cudaFree(g->insts_dev); cudaFree(g->items_dev); cudaFree(g->dtm_dev); cudaFree(g->tab_off_dev); cudaFree(g->counters);
     if (g->cap) cudaStreamDestroy(g->cap);
     delete g;
     return PD_OK;
@@ -508,11 +795,42 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     s.coef = *c;
     s.coef.src_amp = nullptr;
     s.I.sol = c->sol; s.I.tkind = c->tkind; s.I.tc = c->tc;
+    // coefficient storage: 1-D metric tables when K, v, f are constant and there is
+    // no source (constant-coefficient instances on separable or polar maps), else
+    // per-point records
+    bool tabular = c->dx == 0 && c->dy == 0 && c->ds == 0 && c->n_four == 0 && c->va[1] == 0 && c->va[2] == 0
+                && c->vb[1] == 0 && c->vb[2] == 0 && c->src == PD_SRC_NONE;
+    bool use_tables = tabular && (g->storage == 2 || (g->storage == 0 && g->inst.size() > 1));
+    size_t es = s.d.prec == PD_FP32 ? 4 : 8;
+    size_t npts = (size_t)s.I.n_patch * s.I.mx * s.I.my;
+    if (use_tables) {
+        s.I.coef_mode = s.d.map == PD_MAP_POLAR ? COEF_POLAR : COEF_SEPARABLE;
+        if (!s.col_tab) PD_CUDA(g, cudaMalloc(&s.col_tab, sizeof(double) * 2 * (size_t)s.I.ncols * s.I.mx));
+        if (!s.row_tab) PD_CUDA(g, cudaMalloc(&s.row_tab, sizeof(double) * 4 * (size_t)s.I.nrows * s.I.my));
+        s.I.col_tab = s.col_tab; s.I.row_tab = s.row_tab;
+        s.I.K11 = c->d0 * c->M11; s.I.K12 = c->d0 * c->M12; s.I.K22 = c->d0 * c->M22;
+        s.I.v1 = c->va[0]; s.I.v2 = c->vb[0]; s.I.f0 = c->f0;
+        cudaFree(s.rec); cudaFree(s.brec);
+        s.rec = s.brec = nullptr;
+    } else {
+        s.I.coef_mode = COEF_RECORDS;
+        if (!s.rec) {
+            cudaError_t ea = cudaMalloc(&s.rec, npts * 8 * es);
+            if (ea == cudaSuccess) ea = cudaMalloc(&s.brec, npts * 16 * es);
+            if (ea != cudaSuccess) return fail(g, ea == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA, "coefficient records");
+        }
+    }
+    s.I.rec = s.rec; s.I.brec = s.brec;
+    g->batch_dirty = true;
     s.I.has_tsrc = (c->src != PD_SRC_NONE && c->tkind != PD_TIME_CONST) ? 1 : 0;
     PD_CUDA(g, cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long) * 4, g->stream));
     PD_CUDA(g, cudaMemsetAsync(g->err, 0, sizeof(int) * 4, g->stream));
     PD_CUDA(g, launch_precompute(s.I, *c, s.amp, s.rec, s.d.prec, g->acc, g->acc + 1, g->stream));
     g->launches += 3;
+    if (use_tables) {
+        PD_CUDA(g, launch_tables(s.I, s.col_tab, s.row_tab, nullptr, nullptr, g->stream));
+        g->launches += 1;
+    }
     unsigned long long h[2];
     int herr = 0;
     PD_CUDA(g, cudaMemcpyAsync(h, g->acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
@@ -529,8 +847,10 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     s.I.dt = s.dt; s.I.tau = s.tau;
     s.I.inv_tau = 1.0 / s.tau;
     s.I.inv_nn = 1.0 / ((double)(s.d.m_xi - 1) * (s.d.m_eta - 1));
-    PD_CUDA(g, launch_burst_records(s.I, s.d.prec, s.brec, g->stream));
-    g->launches += 1;
+    if (!use_tables) {
+        PD_CUDA(g, launch_burst_records(s.I, s.d.prec, s.brec, g->stream));
+        g->launches += 1;
+    }
     PD_CUDA(g, cudaStreamSynchronize(g->stream));
     // cross term present unless K^{xi eta} vanishes identically (orthogonal map, K = d m I,
     // or a separable map with M12 = 0)
@@ -556,9 +876,12 @@ pd_status pd_query(const pd_grid* gc, int inst, pd_info* o)
     o->m_xi = s.d.m_xi; o->m_eta = s.d.m_eta; o->k_micro = s.d.k_micro; o->prec = s.d.prec;
     o->u_offset = s.I.u_off;
     o->patch_offset = s.I.p_off;
+    o->point_offset = s.I.pt_off;
+    o->edge_offset = s.I.e_off;
     o->dt_micro = s.dt; o->tau = s.tau; o->dt_macro_suggested = s.dtm_sugg;
     layout(g, s, *o);
-    o->exec_path = !fused_supported(s.I) ? 0 : (g->persist && s.coef_set && persist_fits(s.I, s.d.prec)) ? 2 : 1;
+    if (use_batch(g)) o->exec_path = all_batch_supported(g) ? 3 : 0;
+    else o->exec_path = !fused_supported(s.I) ? 0 : (g->persist && s.coef_set && persist_fits(s.I, s.d.prec)) ? 2 : 1;
     o->chunk_steps = o->exec_path == 2 ? persist_max_steps(s.I, s.d.prec) : 1;
     return PD_OK;
 }
@@ -579,7 +902,8 @@ pd_status pd_get_coeffs(pd_grid* g, int inst, double* out)
     Inst& s = g->inst[inst];
     if (!s.coef_set) return fail(g, PD_ESTATE, "coefficients not set");
     if (!out) return fail(g, PD_EINVAL, "null output");
-    PD_CUDA(g, launch_get_coeffs(s.I, s.d.prec, out, g->stream));
+    if (s.I.coef_mode != COEF_RECORDS) PD_CUDA(g, launch_table_get_coeffs(s.I, out, g->stream));
+    else PD_CUDA(g, launch_get_coeffs(s.I, s.d.prec, out, g->stream));
     g->launches += 1;
     return PD_OK;
 }
@@ -679,6 +1003,10 @@ pd_status pd_step(pd_grid* g, double* U, double t0, double dt_macro, int n_macro
     cudaSetDevice(g->device);
     std::vector<double> dtm(g->inst.size());
     for (size_t k = 0; k < g->inst.size(); ++k) dtm[k] = dt_macro > 0 ? dt_macro : g->inst[k].dtm_sugg;
+    if (use_batch(g)) {
+        if (all_batch_supported(g)) return step_batch(g, U, t0, dtm, n_macro);
+        return step_fallback(g, U, t0, dtm, n_macro);
+    }
     bool all_fused = true;
     for (auto& s : g->inst) all_fused &= fused_supported(s.I);
     if (!all_fused) return step_fallback(g, U, t0, dtm, n_macro);
@@ -731,6 +1059,40 @@ pd_status pd_step(pd_grid* g, double* U, double t0, double dt_macro, int n_macro
         g->tev.emplace_back(e0, e1);
         g->t_launches += n_macro;
     }
+    return PD_OK;
+}
+
+pd_status pd_set_coeff_storage(pd_grid* g, int mode)
+{
+    if (!g) return PD_EINVAL;
+    if (mode < 0 || mode > 2) return fail(g, PD_EINVAL, "storage mode must be 0 (auto), 1 (records) or 2 (tables)");
+    for (auto& s : g->inst) if (s.coef_set) return fail(g, PD_ESTATE, "set the storage mode before pd_set_coeffs");
+    g->storage = mode;
+    return PD_OK;
+}
+
+pd_status pd_autotune(pd_grid* g, int n_trial_steps, int* block, int* half_patches)
+{
+    if (!g) return PD_EINVAL;
+    pd_status rc = all_coeffs_set(g);
+    if (rc) return rc;
+    if (!use_batch(g) || !all_batch_supported(g)) return fail(g, PD_ESTATE, "autotuning applies to batched grids");
+    rc = batch_autotune(g, std::max(1, n_trial_steps));
+    if (rc) return rc;
+    if (block) *block = g->bt_block;
+    if (half_patches) *half_patches = g->bt_half ? 1 : 0;
+    return PD_OK;
+}
+
+pd_status pd_set_autotune(pd_grid* g, int enabled, int block, int half_patches)
+{
+    if (!g) return PD_EINVAL;
+    if (block != 64 && block != 128 && block != 256) return fail(g, PD_EINVAL, "block must be 64, 128 or 256");
+    g->autotune = enabled != 0;
+    g->bt_block = block;
+    g->bt_half = half_patches != 0;
+    g->bt_tuned = false;
+    g->batch_dirty = true;
     return PD_OK;
 }
 

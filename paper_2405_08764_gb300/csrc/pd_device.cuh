@@ -32,14 +32,14 @@ __device__ __forceinline__ int wrap_col(const InstDev& I, int i)
 // rolling window: the neighbours of row b+1 are fetched (shuffles of the old
 // values) before row b is overwritten, and the old value of row b-1 is kept in
 // w_prev.  ds[k] = s(t_k) - s(T) for the time-dependent source.
-template <int M, bool CROSS, bool TSRC, typename real>
+template <int M, bool CROSS, bool TSRC, typename real, typename Tds>
 __device__ __forceinline__ void burst_steps(real (&w)[M], const real (&cE)[M], const real (&cW)[M],
                                             const real (&cN)[M], const real (&cS)[M], const real (&cC)[M],
                                             const real (&cX)[M], const real (&Gs)[M], const real (&Rr)[M],
-                                            const real* __restrict__ ds, int K)
+                                            const Tds* __restrict__ ds, int K)
 {
     for (int k = 0; k < K; ++k) {
-        const real dsk = TSRC ? ds[k] : real(0);
+        const real dsk = TSRC ? (real)ds[k] : real(0);
         real e_n = __shfl_down_sync(kFull, w[0], 1);
         real v_n = __shfl_up_sync(kFull, w[0], 1);
         real d_n = e_n - v_n, d_c = d_n, d_p = d_n;

@@ -39,7 +39,10 @@ struct InstDev {
     int c2slot[9][3];
     double c2w[9][3];
     long long u_off;             // offset of this instance in U (doubles)
-    long long p_off;             // offset in patches (dU, micro state)
+    long long p_off;             // offset in patches (dU, bias)
+    long long pt_off;            // offset in micro points (u0, r, w of the micro state)
+    long long e_off;             // offset in edge entries (4 * edge_stride per patch)
+    int edge_stride;             // max(mx, my) + 2
     const void* rec;             // coefficient records (float or double, 8 per point)
     const void* brec;            // burst records (16 per point, see burst_record_kernel)
     double inv_nn;               // 1 / ((m_xi - 1)(m_eta - 1))
@@ -47,7 +50,63 @@ struct InstDev {
     const int2* bnd_ij;          // boundary nodes (i, j)
     const double2* bnd_xy;       // their physical coordinates
     int* err;                    // device error flags
+    // coefficient storage: records (per micro point) or 1-D metric tables for
+    // constant K, v, f on separable or polar maps (see table_coeffs)
+    int coef_mode;
+    const double* col_tab;       // [ncols][mx][2]
+    const double* row_tab;       // [nrows][my][4]
+    double K11, K12, K22, v1, v2, f0;
+    // reciprocals of the nano steps (division-free stencil weights)
+    double inv_dx, inv_dy, inv_dx2, inv_dy2, inv_4dxdy;
+    int ppw;                     // patches per warp in the batched kernel (<= 32 / mx)
 };
+
+enum CoefMode { COEF_RECORDS = 0, COEF_SEPARABLE = 1, COEF_POLAR = 2 };
+
+// Transformed coefficients (alpha, beta, gamma, nu, omega, phi) for constant K, v,
+// f from 1-D metric tables (eq. Computational_Problem with the operator of the
+// derived form used by precompute_kernel, specialised by hand):
+//  separable maps x = X(xi), y = Y(eta): col = (1/X', X''/X'^3), row = (1/Y', Y''/Y'^3):
+//    alpha = K11/X'^2, beta = 2 K12/(X'Y'), gamma = K22/Y'^2,
+//    nu = v1/X' + K11 X''/X'^3, omega = v2/Y' + K22 Y''/Y'^3, phi = f;
+//  polar map x = R cos xi, y = R sin xi: col = (sin xi, cos xi), row = (1/R, 1/R', R R''/R'^2):
+//    A = s^2 K11 - 2sc K12 + c^2 K22, B = sc (K22 - K11) + (c^2 - s^2) K12,
+//    C = c^2 K11 + 2sc K12 + s^2 K22, B' = (c^2 - s^2)(K22 - K11) - 4sc K12,
+//    alpha = A/R^2, beta = 2B/(R R'), gamma = C/R'^2,
+//    nu = (-s v1 + c v2)/R + 2B/R^2, omega = (c v1 + s v2)/R' - (B' + C (1 - R R''/R'^2))/(R R'),
+//    phi = f.
+template <typename real>
+__device__ __forceinline__ void table_coeffs(const InstDev& I, int ic, int a, int jr, int b, real c[6])
+{
+    const double* ct = I.col_tab + ((size_t)ic * I.mx + a) * 2;
+    const double* rt = I.row_tab + ((size_t)jr * I.my + b) * 4;
+    const real K11 = (real)I.K11, K12 = (real)I.K12, K22 = (real)I.K22;
+    const real v1 = (real)I.v1, v2 = (real)I.v2;
+    if (I.coef_mode == COEF_SEPARABLE) {
+        real ia = (real)ct[0], ia2 = (real)ct[1], ib = (real)rt[0], ib2 = (real)rt[1];
+        c[0] = K11 * ia * ia;
+        c[1] = real(2) * K12 * ia * ib;
+        c[2] = K22 * ib * ib;
+        c[3] = v1 * ia + K11 * ia2;
+        c[4] = v2 * ib + K22 * ib2;
+    } else {
+        real s = (real)ct[0], co = (real)ct[1];
+        real iR = (real)rt[0], iRp = (real)rt[1], q = (real)rt[2];
+        real ss = s * s, cc = co * co, sc = s * co;
+        real A = ss * K11 - real(2) * sc * K12 + cc * K22;
+        real B = sc * (K22 - K11) + (cc - ss) * K12;
+        real C = cc * K11 + real(2) * sc * K12 + ss * K22;
+        real Bp = (cc - ss) * (K22 - K11) - real(4) * sc * K12;
+        c[0] = A * iR * iR;
+        c[1] = real(2) * B * iR * iRp;
+        c[2] = C * iRp * iRp;
+        c[3] = (-s * v1 + co * v2) * iR + real(2) * B * iR * iR;
+        c[4] = (co * v1 + s * v2) * iRp - (Bp + C * (real(1) - q)) * iR * iRp;
+    }
+    c[5] = (real)I.f0;
+}
+
+
 
 // Monomial coefficients of the biquadratic interpolant P(s, t) of eq.
 // (Lagrange_2D) around the patch centre, c_kl of s^k t^l, plus the lift
@@ -121,6 +180,47 @@ __device__ __forceinline__ PointW<real> point_weights(real al, real be, real ga,
         else              { w.wE = ax - nu / dx; w.wW = ax; w.wC += nu / dx; w.ox = real(0.5) * dx; }
         if (om > real(0)) { w.wS = gy + om / dy; w.wN = gy; w.wC -= om / dy; w.oy = real(-0.5) * dy; }
         else              { w.wN = gy - om / dy; w.wS = gy; w.wC += om / dy; w.oy = real(0.5) * dy; }
+    }
+    return w;
+}
+
+// raw coefficients (alpha, beta, gamma, nu, omega, phi, G, 0) of micro point (a, b)
+// of patch (ic, jr), from the tables or the per-point records
+template <typename real>
+__device__ __forceinline__ void point_coeffs(const InstDev& I, int jr, int ic, int a, int b, real v[8])
+{
+    if (I.coef_mode != COEF_RECORDS) {
+        real c[6];
+        table_coeffs<real>(I, ic, a, jr, b, c);
+        for (int k = 0; k < 6; ++k) v[k] = c[k];
+        v[6] = real(0); v[7] = real(0);
+    } else {
+        const real* r = static_cast<const real*>(I.rec) + ((((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a) * 8;
+        for (int k = 0; k < 8; ++k) v[k] = r[k];
+    }
+}
+
+// stencil weights of L_h without divisions (reciprocal nano steps from InstDev)
+template <typename real>
+__device__ __forceinline__ PointW<real> point_weights_fast(const InstDev& I, real al, real be, real ga, real nu,
+                                                           real om, real ph)
+{
+    PointW<real> w;
+    const real idx = (real)I.inv_dx, idy = (real)I.inv_dy;
+    real ax = al * (real)I.inv_dx2, gy = ga * (real)I.inv_dy2;
+    w.wX = be * (real)I.inv_4dxdy;
+    w.wC = -real(2) * ax - real(2) * gy + ph;
+    if (I.conv == PD_CONV_CENTRAL) {
+        real hn = real(0.5) * nu * idx, ho = real(0.5) * om * idy;
+        w.wE = ax - hn; w.wW = ax + hn;
+        w.wN = gy - ho; w.wS = gy + ho;
+        w.ox = real(0); w.oy = real(0);
+    } else {
+        real nx = nu * idx, oy = om * idy;
+        if (nu > real(0)) { w.wW = ax + nx; w.wE = ax; w.wC -= nx; w.ox = real(-0.5) * (real)I.dx; }
+        else              { w.wE = ax - nx; w.wW = ax; w.wC += nx; w.ox = real(0.5) * (real)I.dx; }
+        if (om > real(0)) { w.wS = gy + oy; w.wN = gy; w.wC -= oy; w.oy = real(-0.5) * (real)I.dy; }
+        else              { w.wN = gy - oy; w.wS = gy; w.wC += oy; w.oy = real(0.5) * (real)I.dy; }
     }
     return w;
 }
@@ -204,6 +304,7 @@ cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const
 cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm,
                            cudaStream_t st);
 bool fused_supported(const InstDev& I);
+bool batch_supported(const InstDev& I);
 
 // Persistent dataflow launch of n_steps macro steps (see pd_persist.cu).
 struct PersistArgs {
@@ -218,6 +319,32 @@ struct PersistArgs {
     long long wait_ns;     // give up a neighbour wait after this many ns
     int silent_warp;       // test hook: this item warp never publishes (-1: none)
 };
+// 1-D metric tables (table coefficient mode) and batched execution
+cudaError_t launch_tables(const InstDev& I, double* col_tab, double* row_tab, unsigned long long* rate_max,
+                          unsigned long long* macro_rate_max, cudaStream_t st);
+cudaError_t launch_table_get_coeffs(const InstDev& I, double* out, cudaStream_t st);
+struct BatchItem {
+    int inst;      // instance index
+    int kind;      // 0: patch group (row jr, warp column wc), 1: 32 boundary nodes (chunk jr)
+    int jr, wc;
+};
+struct BatchArgs {
+    const InstDev* insts;      // device array
+    const BatchItem* items;
+    int n_items;
+    int* counter;              // work-queue counter of this macro step (zeroed)
+    double* Ubase;             // caller's field (all instances)
+    double* Sbase;             // scratch field
+    int parity;                // step parity: reads Ubase if 0
+    const double* dtm;         // per-instance macro step
+    const double* tab;         // per-instance time tables (nullable)
+    const long long* tab_off;  // per-instance offset of the table of this pd_step
+    int step;                  // macro step index within the pd_step call
+};
+cudaError_t launch_batch(int prec, bool tsrc, const BatchArgs& a, int block, int grid, cudaStream_t st);
+int batch_blocks_per_sm(int prec, bool tsrc, int block);
+cudaError_t launch_batch_time_tables(const InstDev* insts, int n_inst, const double* dtm, double t0, int n_macro,
+                                     const long long* tab_off, double* tab, long long total, cudaStream_t st);
 int persist_item_warps(const InstDev& I);
 size_t persist_smem_bytes(const InstDev& I, size_t es, int n_steps);
 int persist_max_steps(const InstDev& I, int prec);

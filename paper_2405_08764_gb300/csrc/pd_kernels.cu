@@ -141,7 +141,7 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     const real* brec = static_cast<const real*>(I.brec);
     const long long rowstride = (long long)I.ncols * M;
     const long long base = (long long)jr * M * rowstride + (long long)icl * M + a;
-    const long long sbase = ((long long)I.p_off + (long long)jr * I.ncols + icl) * (M * M) + a;
+    const long long sbase = I.pt_off + ((long long)jr * I.ncols + icl) * (M * M) + a;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
         const real* p = brec + (base + b * rowstride) * 16;
@@ -244,15 +244,16 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
     const real sT = (real)tab[0];
     const long long pg = (long long)I.p_off + p;
     const int mm = I.mx * I.my;
+    const long long pp0 = I.pt_off + (long long)p * mm;
     for (int t = threadIdx.x; t < mm; t += blockDim.x) {
         int a = t % I.mx, b = t / I.mx;
         real v[8];
-        for (int k = 0; k < 8; ++k) v[k] = rec[rec_index(I, jr, ic, a, b) * 8 + k];
+        point_coeffs<real>(I, jr, ic, a, b, v);
         double s = gd.s(a), tt = gd.t(b);
-        u0[pg * mm + t] = cd.C0 + s * (cd.c10 + s * cd.c20 + tt * cd.c11) + tt * (cd.c01 + tt * cd.c02);
+        u0[pp0 + t] = cd.C0 + s * (cd.c10 + s * cd.c20 + tt * cd.c11) + tt * (cd.c01 + tt * cd.c02);
         PointW<real> pw = point_weights<real>(v[0], v[1], v[2], v[3], v[4], v[5], gr.dx, gr.dy, I.conv);
-        r_out[pg * mm + t] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
-        w_out[pg * mm + t] = real(0);
+        r_out[pp0 + t] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
+        w_out[pp0 + t] = real(0);
     }
     // edge data of eq. (edge) = d/dxi, d/deta of the interpolant P at the edges
     for (int t = threadIdx.x; t < 4 * edge_stride; t += blockDim.x) {
@@ -265,7 +266,7 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
             double s = gd.s(e - 1), tt = (side == 2 ? -0.5 : 0.5) * I.hy;
             val = cd.c01 + 2.0 * cd.c02 * tt + cd.c11 * s + edge_gap_eta(cd, s, tt);
         }
-        edge[(pg * 4 + side) * edge_stride + e] = val;
+        edge[I.e_off + ((long long)p * 4 + side) * edge_stride + e] = val;
     }
     if (threadIdx.x == 0)
         bias_out[pg] = (I.restrict_mode == PD_RESTRICT_MACRO) ? (I.dx * I.dx * cd.c20 + I.dy * I.dy * cd.c02) / 6.0 : 0.0;
@@ -283,12 +284,12 @@ burst_kernel(const InstDev I, const double* __restrict__ tab, int k_steps, real*
     int i, j, ic, jr;
     patch_ij(I, p, i, j, ic, jr);
     const int mm = I.mx * I.my;
-    const long long pg = (long long)I.p_off + p;
+    const long long pp0 = I.pt_off + (long long)p * mm;
     const real* rec = static_cast<const real*>(I.rec);
     const real dt = (real)I.dt;
     for (int t = threadIdx.x; t < k_steps; t += blockDim.x) ds[t] = (real)tab[t];
     // this thread's point (mm <= 1024 not needed: loop)
-    for (int t = threadIdx.x; t < mm; t += blockDim.x) ws[t] = w_io[pg * mm + t];
+    for (int t = threadIdx.x; t < mm; t += blockDim.x) ws[t] = w_io[pp0 + t];
     __syncthreads();
     real* cur = ws;
     real* nxt = ws + mm;
@@ -296,7 +297,7 @@ burst_kernel(const InstDev I, const double* __restrict__ tab, int k_steps, real*
         for (int t = threadIdx.x; t < mm; t += blockDim.x) {
             int a = t % I.mx, b = t / I.mx;
             real v[8];
-            for (int q = 0; q < 8; ++q) v[q] = rec[rec_index(I, jr, ic, a, b) * 8 + q];
+            point_coeffs<real>(I, jr, ic, a, b, v);
             PointW<real> pw = point_weights<real>(v[0], v[1], v[2], v[3], v[4], v[5], (real)I.dx, (real)I.dy, I.conv);
             // homogeneous mirrors for the departure
             int aE = a + 1 > I.mx - 1 ? I.mx - 2 : a + 1;
@@ -306,12 +307,12 @@ burst_kernel(const InstDev I, const double* __restrict__ tab, int k_steps, real*
             real L = pw.wC * cur[t] + pw.wE * cur[b * I.mx + aE] + pw.wW * cur[b * I.mx + aW]
                    + pw.wN * cur[bN * I.mx + a] + pw.wS * cur[bS * I.mx + a]
                    + pw.wX * (cur[bN * I.mx + aE] - cur[bS * I.mx + aE] - cur[bN * I.mx + aW] + cur[bS * I.mx + aW]);
-            nxt[t] = cur[t] + dt * (L + r_in[pg * mm + t] + ds[k] * v[6]);
+            nxt[t] = cur[t] + dt * (L + r_in[pp0 + t] + ds[k] * v[6]);
         }
         __syncthreads();
         real* tmp = cur; cur = nxt; nxt = tmp;
     }
-    for (int t = threadIdx.x; t < mm; t += blockDim.x) w_io[pg * mm + t] = cur[t];
+    for (int t = threadIdx.x; t < mm; t += blockDim.x) w_io[pp0 + t] = cur[t];
 }
 
 // trapezoid restriction of the departure: one warp per patch
@@ -324,11 +325,12 @@ __global__ void restrict_kernel(const InstDev I, const real* __restrict__ w, con
     if (p >= I.n_patch) return;
     const int mm = I.mx * I.my;
     const long long pg = (long long)I.p_off + p;
+    const long long pp0 = I.pt_off + (long long)p * mm;
     double acc = 0.0;
     for (int t = lane; t < mm; t += 32) {
         int a = t % I.mx, b = t / I.mx;
         double wt = ((a == 0 || a == I.mx - 1) ? 0.5 : 1.0) * ((b == 0 || b == I.my - 1) ? 0.5 : 1.0);
-        acc += wt * (double)w[pg * mm + t];
+        acc += wt * (double)w[pp0 + t];
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
     if (lane == 0) {
@@ -426,6 +428,11 @@ cudaError_t launch_burst_records(const InstDev& I, int prec, void* brec, cudaStr
     return cudaGetLastError();
 }
 
+bool batch_supported(const InstDev& I)
+{
+    return I.mx == I.my && (I.mx == 3 || I.mx == 5 || I.mx == 7 || I.mx == 9 || I.mx == 11) && I.K <= kMaxK;
+}
+
 bool fused_supported(const InstDev& I)
 {
     return I.mx == I.my && (I.mx == 3 || I.mx == 5 || I.mx == 7 || I.mx == 9 || I.mx == 11) && I.K <= kMaxK;
@@ -466,7 +473,7 @@ cudaError_t launch_burst(const InstDev& I, const InstDev*, int prec, char* state
     burst_table_kernel<<<(k_steps + 127) / 128, 128, 0, st>>>(k_steps, I.tkind, I.tc, I.dt, t, hdr, tab);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (fused_supported(I)) {
+    if (fused_supported(I) && I.coef_mode == COEF_RECORDS) {
         if (prec == PD_FP32)
             return dispatch_m<float, MODE_BURST>(I, nullptr, nullptr, tab, 0.0, k_steps,
                                                  reinterpret_cast<float*>(state + lay.off_w),

@@ -258,10 +258,12 @@ __global__ void precompute_kernel(const InstDev I, const CoefDev C, const double
         for (int k = 0; k < 6; ++k) bad |= !isfinite(c[k]);
         bad |= !isfinite(G);
         if (bad) atomicOr(I.err, ERR_JACOBIAN);
-        real* o = rec + idx * 8;
-        for (int k = 0; k < 6; ++k) o[k] = (real)c[k];
-        o[6] = (real)G;
-        o[7] = (real)0;
+        if (rec) {
+            real* o = rec + idx * 8;
+            for (int k = 0; k < 6; ++k) o[k] = (real)c[k];
+            o[6] = (real)G;
+            o[7] = (real)0;
+        }
         rate = 2.0 * fabs(c[0]) / (I.dx * I.dx) + 2.0 * fabs(c[2]) / (I.dy * I.dy)
              + fabs(c[1]) / (I.dx * I.dy) + fabs(c[5]);
         if (I.conv == PD_CONV_UPWIND) rate += fabs(c[3]) / I.dx + fabs(c[4]) / I.dy;
@@ -360,6 +362,61 @@ __global__ void init_field_kernel(const InstDev I, const CoefDev C, const InitPa
     U[k] = v;
 }
 
+// 1-D metric tables of the table coefficient mode (FP64)
+__global__ void table_build_kernel(const InstDev I, double* col_tab, double* row_tab)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int ncol = I.ncols * I.mx, nrow = I.nrows * I.my;
+    if (t < ncol) {
+        int ic = t / I.mx, a = t % I.mx;
+        double xi = (I.xi0 + (I.i0 + ic) * I.Dx) - 0.5 * I.hx + a * I.dx;
+        double* o = col_tab + (size_t)t * 2;
+        if (I.coef_mode == COEF_POLAR) {
+            double s, c;
+            sincos(xi, &s, &c);
+            o[0] = s; o[1] = c;
+        } else {
+            Jet m = eval_map(I, xi, I.eta0);
+            double ia = 1.0 / m.x_a;
+            o[0] = ia; o[1] = m.x_aa * ia * ia * ia;
+        }
+    } else if (t < ncol + nrow) {
+        int u = t - ncol;
+        int jr = u / I.my, b = u % I.my;
+        double eta = (I.eta0 + (1 + jr) * I.Dy) - 0.5 * I.hy + b * I.dy;
+        double* o = row_tab + (size_t)u * 4;
+        if (I.coef_mode == COEF_POLAR) {
+            Jet m = eval_map(I, 0.0, eta);   // at xi = 0: x = R, x_eta = R', x_etaeta = R''
+            double R = m.x, R1 = m.x_b, R2 = m.x_bb;
+            o[0] = 1.0 / R; o[1] = 1.0 / R1; o[2] = R * R2 / (R1 * R1); o[3] = 0.0;
+        } else {
+            Jet m = eval_map(I, I.xi0, eta);
+            double ib = 1.0 / m.y_b;
+            o[0] = ib; o[1] = m.y_bb * ib * ib * ib; o[2] = 0.0; o[3] = 0.0;
+        }
+    }
+}
+
+// coefficients of a table-mode instance at every micro point, [p][b][a][8]
+__global__ void table_get_coeffs_kernel(const InstDev I, double* __restrict__ out)
+{
+    long long n = (long long)I.n_patch * I.mx * I.my;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    int a = (int)(idx % I.mx);
+    long long r1 = idx / I.mx;
+    int ic = (int)(r1 % I.ncols);
+    long long r2 = r1 / I.ncols;
+    int b = (int)(r2 % I.my);
+    int jr = (int)(r2 / I.my);
+    double c[6];
+    table_coeffs<double>(I, ic, a, jr, b, c);
+    long long p = (long long)jr * I.ncols + ic;
+    double* o = out + ((p * I.my + b) * I.mx + a) * 8;
+    for (int k = 0; k < 6; ++k) o[k] = c[k];
+    o[6] = 0.0; o[7] = 0.0;
+}
+
 // row s: ds_k = s(T + k dt) - s(T) (k < K), s(T), T, T_next with T = t0 + s dtm
 __global__ void time_table_kernel(int K, int tkind, double tc, double dt, double t0, double dtm,
                                   int n_steps, double* tab)
@@ -377,7 +434,42 @@ __global__ void time_table_kernel(int K, int tkind, double tc, double dt, double
     tab[idx] = v;
 }
 
+__global__ void batch_time_table_kernel(const InstDev* __restrict__ insts, int n_inst, const double* __restrict__ dtm,
+                                        double t0, int n_macro, const long long* __restrict__ tab_off, double* tab,
+                                        long long total)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    // find the instance of this entry (tab_off is increasing; n_inst + 1 entries)
+    int lo = 0, hi = n_inst;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (tab_off[mid] <= idx) lo = mid; else hi = mid;
+    }
+    const InstDev& I = insts[lo];
+    int stride = I.K + kTabExtra;
+    long long loc = idx - tab_off[lo];
+    int s = (int)(loc / stride), k = (int)(loc % stride);
+    double d = dtm[lo];
+    double T = t0 + s * d;
+    double v;
+    if (k < I.K) v = time_factor(I.tkind, I.tc, T + k * I.dt) - time_factor(I.tkind, I.tc, T);
+    else if (k == I.K) v = time_factor(I.tkind, I.tc, T);
+    else if (k == I.K + 1) v = T;
+    else v = t0 + (s + 1) * d;
+    tab[idx] = v;
+    (void)n_macro;
+}
+
 }  // namespace
+
+cudaError_t launch_batch_time_tables(const InstDev* insts, int n_inst, const double* dtm, double t0, int n_macro,
+                                     const long long* tab_off, double* tab, long long total, cudaStream_t st)
+{
+    if (total <= 0) return cudaSuccess;
+    batch_time_table_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(insts, n_inst, dtm, t0, n_macro, tab_off, tab, total);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_precompute(const InstDev& I, const pd_coeff_desc& c, const double* amp_dev, void* rec,
                               int prec, unsigned long long* rate_max, unsigned long long* macro_rate_max,
@@ -394,6 +486,22 @@ cudaError_t launch_precompute(const InstDev& I, const pd_coeff_desc& c, const do
     macro_rate_kernel<<<(I.n_patch + 127) / 128, 128, 0, st>>>(I, C, macro_rate_max);
     if (I.n_bnd > 0)
         boundary_xy_kernel<<<(I.n_bnd + 127) / 128, 128, 0, st>>>(I, const_cast<double2*>(I.bnd_xy));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const InstDev& I, double* col_tab, double* row_tab, unsigned long long* rate_max,
+                          unsigned long long* macro_rate_max, cudaStream_t st)
+{
+    (void)rate_max; (void)macro_rate_max;
+    int n = I.ncols * I.mx + I.nrows * I.my;
+    table_build_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, col_tab, row_tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_get_coeffs(const InstDev& I, double* out, cudaStream_t st)
+{
+    long long n = (long long)I.n_patch * I.mx * I.my;
+    table_get_coeffs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(I, out);
     return cudaGetLastError();
 }
 
