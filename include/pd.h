@@ -207,6 +207,29 @@ pd_status pd_project(pd_grid* g, double* U_dev, const double* dU_dev, double t, 
 pd_status pd_step(pd_grid* g, double* U_dev, double t0, double dt_macro, int n_macro);
 pd_status pd_set_graph_mode(pd_grid* g, int enabled);
 
+/* The same macro steps as pd_step with one fused kernel per step, for callers
+ * that may not allocate device memory during a step.  The paper has no
+ * counterpart; it is a deployment variant.  Such callers are, e.g., a
+ * solver loop embedded in a host application whose memory pool already
+ * reserves nearly all of HBM (a cudaMalloc there can fail mid-run), or a
+ * latency-bound loop that cannot afford cudaMalloc's implicit device
+ * synchronisation.  pd_step allocates its second macro field and its time
+ * tables on first use; this call instead carves both out of one fixed
+ * 4 MiB device array per device (524288 doubles) that lives in the library.
+ * Limits: a grid of one instance, per-point coefficient records (the default
+ * for one instance), m_xi == m_eta in {3,5,7,9,11}; the need is
+ * roundup32(nxp*nyp) + n_macro*(k_micro + 3) doubles, and a larger request
+ * is rejected with PD_EINVAL (take fewer macro steps per call).  Nothing in
+ * the array has to start at zero: every step writes the whole next field and
+ * the time table is written before it is read.  All calls on a device share
+ * the array: two calls whose work overlaps in time (different streams,
+ * grids or host threads without ordering between them) race and corrupt
+ * each other's results; order them on one stream.  The first call on a
+ * device looks up the array's address (set-up work in the CUDA runtime) and
+ * should precede any stream capture.  Results equal pd_step's per-step
+ * kernel path.  Errors: PD_EINVAL, PD_ESTATE, PD_ECUDA. */
+pd_status pd_step_noalloc(pd_grid* g, double* U_dev, double t0, double dt_macro, int n_macro);
+
 /* Coefficient storage (call before pd_set_coeffs): 0 auto (default: 1-D metric
  * tables for constant-coefficient, source-free instances when the grid holds
  * several instances, else per-point records), 1 records, 2 tables where

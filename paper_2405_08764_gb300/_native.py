@@ -74,6 +74,7 @@ SIGNATURES = {
     "pd_restrict": (C.c_int, [_GP, _VP, _VP]),
     "pd_project": (C.c_int, [_GP, _VP, _VP, C.c_double, C.c_double]),
     "pd_step": (C.c_int, [_GP, _VP, C.c_double, C.c_double, C.c_int]),
+    "pd_step_noalloc": (C.c_int, [_GP, _VP, C.c_double, C.c_double, C.c_int]),
     "pd_set_graph_mode": (C.c_int, [_GP, C.c_int]),
     "pd_set_persistent": (C.c_int, [_GP, C.c_int]),
     "pd_set_coeff_storage": (C.c_int, [_GP, C.c_int]),

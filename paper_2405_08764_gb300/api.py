@@ -192,6 +192,11 @@ class Grid:
         self._stream()
         N.check(self.L.pd_step(self.h, C.c_void_p(_ptr(U)), float(t0), float(dt_macro), int(n_macro)), self.h)
 
+    def step_noalloc(self, U: torch.Tensor, t0: float, dt_macro: float, n_macro: int):
+        """pd_step_noalloc: the per-step fused path with fixed library scratch."""
+        self._stream()
+        N.check(self.L.pd_step_noalloc(self.h, C.c_void_p(_ptr(U)), float(t0), float(dt_macro), int(n_macro)), self.h)
+
     def sync(self):
         N.check(self.L.pd_sync(self.h), self.h)
 

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -1221,6 +1222,84 @@ pd_status pd_load_checkpoint(pd_grid* g, double* U, double* t, long long* step, 
     PD_CUDA(g, cudaStreamSynchronize(g->stream));
     if (t) *t = tt;
     if (step) *step = st;
+    return PD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// pd_step_noalloc: the fused per-step path of pd_step with both of its scratch
+// buffers (the second macro field and the per-step time table) carved out of
+// one fixed device array instead of device allocations.
+
+namespace {
+
+constexpr size_t kNoAllocDoubles = size_t(1) << 19;   // 4 MiB per device
+constexpr int kNoAllocDevices = 64;
+
+static __device__ __align__(256) double noalloc_scratch[kNoAllocDoubles];
+
+std::mutex noalloc_mu;
+double* noalloc_base[kNoAllocDevices] = {};
+
+// device address of the array on the grid's device, looked up once per device
+pd_status noalloc_scratch_on(pd_grid* g, double** out)
+{
+    std::lock_guard<std::mutex> lk(noalloc_mu);
+    if (g->device < 0 || g->device >= kNoAllocDevices) return fail(g, PD_EINVAL, "device ordinal out of range");
+    if (!noalloc_base[g->device]) {
+        PD_CUDA(g, cudaSetDevice(g->device));
+        void* p = nullptr;
+        PD_CUDA(g, cudaGetSymbolAddress(&p, noalloc_scratch));
+        noalloc_base[g->device] = static_cast<double*>(p);
+    }
+    *out = noalloc_base[g->device];
+    return PD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_step_noalloc(pd_grid* g, double* U, double t0, double dt_macro, int n_macro)
+{
+    if (!g) return PD_EINVAL;
+    if (!U) return fail(g, PD_EINVAL, "null field");
+    if (n_macro < 0) return fail(g, PD_EINVAL, "n_macro must be >= 0");
+    pd_status rc = all_coeffs_set(g);
+    if (rc) return rc;
+    if (g->inst.size() != 1) return fail(g, PD_EINVAL, "pd_step_noalloc takes a grid of one instance");
+    Inst& s = g->inst[0];
+    const InstDev& I = s.I;
+    if (I.coef_mode != COEF_RECORDS || !fused_supported(I))
+        return fail(g, PD_EINVAL, "pd_step_noalloc needs per-point coefficient records and m_xi == m_eta in {3,5,7,9,11}");
+    // layout: second macro field (rounded to 256 bytes), then n_macro time-table rows
+    const size_t field = ((size_t)I.nxp * I.nyp + 31) & ~size_t(31);
+    const size_t stride = (size_t)I.K + kTabExtra;
+    const size_t need = field + (size_t)n_macro * stride;
+    if (need > kNoAllocDoubles)
+        return fail(g, PD_EINVAL, "pd_step_noalloc needs " + std::to_string(need) +
+                                  " doubles of fixed scratch (field + n_macro time-table rows); the limit is " +
+                                  std::to_string(kNoAllocDoubles) + ": take fewer macro steps per call");
+    double* base = nullptr;
+    rc = noalloc_scratch_on(g, &base);
+    if (rc) return rc;
+    if (n_macro == 0) return PD_OK;
+    PD_CUDA(g, cudaSetDevice(g->device));
+    const double dtm = dt_macro > 0 ? dt_macro : s.dtm_sugg;
+    double* tab = base + field;
+    PD_CUDA(g, launch_time_table(I, t0, dtm, n_macro, tab, g->stream));
+    int nl = 1;
+    double* bufs[2] = { U + I.u_off, base };
+    for (int t = 0; t < n_macro; ++t) {
+        cudaError_t e = launch_fused_step(I, nullptr, s.d.prec, bufs[t & 1], bufs[(t + 1) & 1],
+                                          tab + (size_t)t * stride, dtm, g->stream, &nl);
+        if (e != cudaSuccess) { g->launches += nl; return cuda_fail(g, e, "fused step (fixed scratch)"); }
+    }
+    g->launches += nl;
+    if (n_macro & 1)
+        PD_CUDA(g, cudaMemcpyAsync(bufs[0], bufs[1], sizeof(double) * (size_t)I.nxp * I.nyp,
+                                   cudaMemcpyDeviceToDevice, g->stream));
     return PD_OK;
 }
 
