@@ -141,24 +141,28 @@ def loss(theta, X, t):
     return float(np.mean((y - t) ** 2))
 
 
-def gradient(theta, X, t):
+def gradient(theta, X, t, round_bf16: bool = False):
     """Gradient of loss() with respect to the flat parameters, by the chain
-    rule through the four layers."""
+    rule through the four layers.  With round_bf16 the forward pass rounds as
+    in forward(), and the back-propagated dZ of each layer is rounded to BF16
+    before it enters the weight and input gradients (the device stores dZ in
+    BF16 as a tensor-core operand); the bias gradients then sum the rounded dZ."""
     p = unflatten(theta)
-    y, c = forward(theta, X)
+    r = bf16 if round_bf16 else (lambda a: a)
+    y, c = forward(theta, X, round_bf16)
     n = len(t)
     dy = 2.0 * (y - np.asarray(t, dtype=np.float64)) / n
     g = {}
     g["w4"] = c["h3"].T @ dy
     g["b4"] = np.array([dy.sum()])
-    dz3 = np.outer(dy, p["w4"]) * gelu_grad(c["z3"])
+    dz3 = r(np.outer(dy, r(p["w4"])) * gelu_grad(c["z3"]))
     g["W3"] = dz3.T @ c["h2"]
     g["b3"] = dz3.sum(0)
-    dz2 = (dz3 @ p["W3"]) * gelu_grad(c["z2"])
+    dz2 = r((dz3 @ r(p["W3"])) * gelu_grad(c["z2"]))
     g["W2"] = dz2.T @ c["h1"]
     g["b2"] = dz2.sum(0)
-    dz1 = (dz2 @ p["W2"]) * gelu_grad(c["z1"])
-    g["W1"] = dz1.T @ c["X"]
+    dz1 = r((dz2 @ r(p["W2"])) * gelu_grad(c["z1"]))
+    g["W1"] = dz1.T @ r(c["X"])
     g["b1"] = dz1.sum(0)
     return flatten(g)
 

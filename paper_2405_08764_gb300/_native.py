@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/pd.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/pd.h and include/pd_surrogate.h
+(argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes as C
@@ -91,7 +92,25 @@ SIGNATURES = {
     "pd_status_str": (C.c_char_p, [C.c_int]),
     "pd_last_error": (C.c_char_p, [_GP]),
     "pd_abi_version": (C.c_int, []),
+    # learned surrogate (include/pd_surrogate.h)
+    "pd_mlp_create": (C.c_int, [C.c_int, _VP, C.POINTER(_VP)]),
+    "pd_mlp_destroy": (C.c_int, [_VP]),
+    "pd_mlp_set_stream": (C.c_int, [_VP, _VP]),
+    "pd_mlp_set_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.c_int]),
+    "pd_mlp_get_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.c_int]),
+    "pd_mlp_set_norm": (C.c_int, [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float]),
+    "pd_mlp_get_norm": (C.c_int, [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "pd_mlp_fit_norm": (C.c_int, [_VP, _VP, _VP, C.c_longlong]),
+    "pd_mlp_pack": (C.c_int, [_VP, _VP, _VP, C.c_longlong, _VP, _VP]),
+    "pd_mlp_forward": (C.c_int, [_VP, _VP, C.c_longlong, _VP]),
+    "pd_mlp_gradient": (C.c_int, [_VP, _VP, _VP, C.c_int, _VP, C.POINTER(C.c_float)]),
+    "pd_mlp_train": (C.c_int, [_VP, _VP, _VP, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_ulonglong,
+                               C.POINTER(C.c_float)]),
+    "pd_mlp_adam_step": (C.c_int, [_VP, C.c_float]),
+    "pd_mlp_sync": (C.c_int, [_VP]),
+    "pd_mlp_last_error": (C.c_char_p, [_VP]),
 }
+MLP_N_IN, MLP_N_PAD, MLP_WIDTH, MLP_N_PARAM = 35, 64, 256, 148481
 
 _lock = threading.Lock()
 _lib = None
@@ -123,4 +142,10 @@ class PDError(RuntimeError):
 def check(status: int, grid=None):
     if status != PD_OK:
         msg = load().pd_last_error(grid).decode() if grid else ""
+        raise PDError(status, msg)
+
+
+def check_mlp(status: int, net=None):
+    if status != PD_OK:
+        msg = load().pd_mlp_last_error(net).decode() if net else ""
         raise PDError(status, msg)

@@ -235,3 +235,101 @@ class Grid:
         N.check(self.L.pd_load_checkpoint(self.h, C.c_void_p(_ptr(U)), C.byref(t), C.byref(s),
                                           path.encode()), self.h)
         return t.value, s.value
+
+
+class MLP:
+    """The surrogate network of include/pd_surrogate.h on the current CUDA
+    device (35 -> 256 -> 256 -> 256 -> 1, BF16 tensor-core GEMMs).  Inputs
+    are BF16 tensors [n, 64]; parameters are a flat FP32 vector."""
+
+    N_PARAM = N.MLP_N_PARAM
+
+    def __init__(self, max_batch: int = 8192):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the surrogate network needs a CUDA device")
+        self.L = N.load()
+        h = C.c_void_p()
+        N.check_mlp(self.L.pd_mlp_create(int(max_batch), C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                         C.byref(h)))
+        self.h = h
+        self.max_batch = int(max_batch)
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.pd_mlp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def _stream(self):
+        self.L.pd_mlp_set_stream(self.h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def _chk(self, rc):
+        N.check_mlp(rc, self.h)
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        self._stream()
+        self._chk(self.L.pd_mlp_set_params(self.h, th.ctypes.data_as(C.POINTER(C.c_float)), th.size))
+
+    def params(self) -> np.ndarray:
+        th = np.zeros(self.N_PARAM, dtype=np.float32)
+        self._stream()
+        self._chk(self.L.pd_mlp_get_params(self.h, th.ctypes.data_as(C.POINTER(C.c_float)), th.size))
+        return th
+
+    def set_norm(self, mu, sigma, y_scale: float):
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        sg = np.ascontiguousarray(sigma, dtype=np.float32)
+        self._stream()
+        self._chk(self.L.pd_mlp_set_norm(self.h, mu.ctypes.data_as(C.POINTER(C.c_float)),
+                                         sg.ctypes.data_as(C.POINTER(C.c_float)), float(y_scale)))
+
+    def norm(self):
+        mu = np.zeros(N.MLP_N_IN, dtype=np.float32)
+        sg = np.zeros(N.MLP_N_IN, dtype=np.float32)
+        ys = C.c_float()
+        self._chk(self.L.pd_mlp_get_norm(self.h, mu.ctypes.data_as(C.POINTER(C.c_float)),
+                                         sg.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ys)))
+        return mu, sg, ys.value
+
+    def fit_norm(self, X_raw: torch.Tensor, y_raw: torch.Tensor):
+        self._stream()
+        self._chk(self.L.pd_mlp_fit_norm(self.h, C.c_void_p(_ptr(X_raw)), C.c_void_p(_ptr(y_raw)), X_raw.shape[0]))
+
+    def pack(self, X_raw: torch.Tensor, y_raw: torch.Tensor = None):
+        n = X_raw.shape[0]
+        X = torch.empty((n, N.MLP_N_PAD), dtype=torch.bfloat16, device=X_raw.device)
+        t = torch.empty(n, dtype=torch.float32, device=X_raw.device) if y_raw is not None else None
+        self._stream()
+        self._chk(self.L.pd_mlp_pack(self.h, C.c_void_p(_ptr(X_raw)),
+                                     C.c_void_p(_ptr(y_raw)) if y_raw is not None else None, n,
+                                     C.c_void_p(_ptr(X)), C.c_void_p(_ptr(t)) if t is not None else None))
+        return X, t
+
+    def forward(self, X: torch.Tensor) -> torch.Tensor:
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        self._stream()
+        self._chk(self.L.pd_mlp_forward(self.h, C.c_void_p(_ptr(X)), X.shape[0], C.c_void_p(_ptr(y))))
+        return y
+
+    def gradient(self, X: torch.Tensor, t: torch.Tensor):
+        g = torch.empty(self.N_PARAM, dtype=torch.float32, device=X.device)
+        loss = C.c_float()
+        self._stream()
+        self._chk(self.L.pd_mlp_gradient(self.h, C.c_void_p(_ptr(X)), C.c_void_p(_ptr(t)), X.shape[0],
+                                         C.c_void_p(_ptr(g)), C.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, lr: float):
+        self._stream()
+        self._chk(self.L.pd_mlp_adam_step(self.h, float(lr)))
+
+    def train(self, X: torch.Tensor, t: torch.Tensor, batch: int, epochs: int, lr_max: float, seed: int = 0):
+        hist = np.zeros(max(epochs, 1), dtype=np.float32)
+        self._stream()
+        self._chk(self.L.pd_mlp_train(self.h, C.c_void_p(_ptr(X)), C.c_void_p(_ptr(t)), X.shape[0], int(batch),
+                                      int(epochs), float(lr_max), int(seed),
+                                      hist.ctypes.data_as(C.POINTER(C.c_float))))
+        return hist[:epochs]
+
+    def sync(self):
+        self._chk(self.L.pd_mlp_sync(self.h))

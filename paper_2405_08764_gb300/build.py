@@ -37,7 +37,7 @@ def _stale() -> bool:
     if not os.path.exists(OUT):
         return True
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) \
-        + [os.path.join(ROOT, "include", "pd.h"), __file__]
+        + glob.glob(os.path.join(ROOT, "include", "*.h")) + [__file__]
     t = os.path.getmtime(OUT)
     return any(os.path.getmtime(d) > t for d in deps)
 

@@ -1,5 +1,5 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads, and exports
-every function include/pd.h declares (no device calls)."""
+every function the headers in include/ declare (no device calls)."""
 import ctypes
 import os
 import re
@@ -10,9 +10,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "pd.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pd_[a-z_]+)\s*\(", src)))
+    import glob
+    names = set()
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(pd_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")

@@ -1,0 +1,156 @@
+"""The surrogate network's tensor-core kernels (include/pd_surrogate.h) against
+the FP64 CPU oracle: forward pass (ragged and multi-chunk row counts), the
+full backward pass (every parameter tensor), Adam, feature standardisation,
+and training on a synthetic regression."""
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def MLP():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_08764_gb300.api import MLP
+    return MLP
+
+
+def _theta(seed=3):
+    th = S.init_params(seed)
+    rng = np.random.default_rng(seed + 100)
+    p = S.unflatten(th)
+    for k in ("b1", "b2", "b3"):
+        p[k] = 0.1 * rng.normal(size=p[k].shape)
+    p["b4"] = np.array([0.05])
+    return S.flatten(p).astype(np.float32)
+
+
+def _inputs(n, seed=0):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, S.N_PAD), dtype=np.float32)
+    X[:, :S.N_IN] = rng.normal(size=(n, S.N_IN))
+    Xd = torch.tensor(X).to(torch.bfloat16).cuda()
+    return Xd, Xd.float().cpu().numpy().astype(np.float64)
+
+
+def _slices():
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in S.SHAPES])
+    return {name: slice(offs[k], offs[k + 1]) for k, (name, _) in enumerate(S.SHAPES)}
+
+
+def test_forward_matches_oracle_ragged_rows(MLP):
+    net = MLP(1024)
+    th = _theta()
+    net.set_params(th)
+    X, Xh = _inputs(1000)
+    y = net.forward(X).cpu().numpy()
+    want, _ = S.forward(th.astype(np.float64), Xh, round_bf16=True)
+    # same BF16 rounding points; FP32 accumulation order and rare rounding flips remain
+    assert np.abs(y - want).max() <= 1e-3 * np.abs(want).max(), np.abs(y - want).max()
+    exact, _ = S.forward(th.astype(np.float64), Xh)
+    assert np.abs(y - exact).max() <= 5e-2 * np.abs(exact).max()
+
+
+def test_forward_across_inference_chunks(MLP):
+    net = MLP(128)
+    th = _theta(5)
+    net.set_params(th)
+    n = 70001
+    X, Xh = _inputs(n, 1)
+    y = net.forward(X).cpu().numpy()
+    rows = np.unique(np.concatenate([np.arange(0, 300), np.arange(65400, 65700), np.arange(n - 300, n),
+                                     np.random.default_rng(2).integers(0, n, 500)]))
+    want, _ = S.forward(th.astype(np.float64), Xh[rows], round_bf16=True)
+    assert np.abs(y[rows] - want).max() <= 1e-3 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n", [128, 300])
+def test_gradient_matches_oracle(MLP, n):
+    net = MLP(512)
+    th = _theta(7)
+    net.set_params(th)
+    X, Xh = _inputs(n, 3)
+    t = np.random.default_rng(4).normal(size=n).astype(np.float32)
+    g, loss = net.gradient(X, torch.tensor(t).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    want = S.gradient(th.astype(np.float64), Xh, t.astype(np.float64), round_bf16=True)
+    exact = S.gradient(th.astype(np.float64), Xh, t.astype(np.float64))
+    for name, sl in _slices().items():
+        a, b, c = g[sl], want[sl], exact[sl]
+        if name == "W1":   # padding columns get no gradient
+            assert np.all(a.reshape(S.WIDTH, S.N_PAD)[:, S.N_IN:] == 0.0)
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= 3e-3, (name, rel)
+        assert np.linalg.norm(a - c) / np.linalg.norm(c) <= 5e-2, name
+    yo, _ = S.forward(th.astype(np.float64), Xh, round_bf16=True)
+    assert abs(loss - np.mean((yo - t) ** 2)) <= 1e-4 * np.mean((yo - t) ** 2)
+
+
+def test_adam_steps_match_oracle(MLP):
+    net = MLP(256)
+    th = _theta(9)
+    net.set_params(th)
+    X, Xh = _inputs(256, 5)
+    t = torch.tensor(np.random.default_rng(6).normal(size=256).astype(np.float32)).cuda()
+    ref = th.astype(np.float64)
+    m = np.zeros_like(ref)
+    v = np.zeros_like(ref)
+    lr = 1e-3
+    for step in range(1, 4):
+        g, _ = net.gradient(X, t)
+        g = g.cpu().numpy().astype(np.float64)
+        net.adam_step(lr)
+        ref, m, v = S.adam(ref, g, m, v, step, lr)
+        got = net.params().astype(np.float64)
+        assert np.abs(got - ref).max() <= 2e-6 + 1e-3 * lr, step
+    # the BF16 operand copies follow the master weights
+    y = net.forward(X).cpu().numpy()
+    want, _ = S.forward(net.params().astype(np.float64), Xh, round_bf16=True)
+    assert np.abs(y - want).max() <= 1e-3 * np.abs(want).max()
+
+
+def test_fit_norm_and_pack(MLP):
+    net = MLP(128)
+    rng = np.random.default_rng(8)
+    Xr = (rng.normal(size=(5000, S.N_IN)) * rng.uniform(0.1, 10, S.N_IN) + rng.uniform(-5, 5, S.N_IN)).astype(np.float32)
+    Xr[:, 7] = 2.5                      # a constant feature keeps sigma = 1
+    yr = rng.normal(size=5000).astype(np.float32) * 3
+    Xd, yd = torch.tensor(Xr).cuda(), torch.tensor(yr).cuda()
+    net.fit_norm(Xd, yd)
+    mu, sg, ys = net.norm()
+    x64 = Xr.astype(np.float64)
+    np.testing.assert_allclose(mu, x64.mean(0), rtol=1e-5, atol=1e-6)
+    sd = x64.std(0)
+    sd[7] = 1.0
+    np.testing.assert_allclose(sg, sd, rtol=1e-5)
+    np.testing.assert_allclose(ys, np.abs(yr.astype(np.float64)).mean(), rtol=1e-6)
+    Xp, tp = net.pack(Xd, yd)
+    want = (Xr - mu) / sg
+    got = Xp.float().cpu().numpy()
+    np.testing.assert_array_equal(got[:, :S.N_IN], S.bf16(want).astype(np.float32))
+    assert np.all(got[:, S.N_IN:] == 0)
+    np.testing.assert_array_equal(tp.cpu().numpy(), yr / np.float32(ys))
+
+
+def test_training_reduces_the_loss(MLP):
+    rng = np.random.default_rng(10)
+    n = 16384
+    Xr = rng.normal(size=(n, S.N_IN))
+    t = np.sin(Xr[:, 0]) + 0.5 * Xr[:, 1] * Xr[:, 2] - 0.3 * Xr[:, 3] ** 2 + 0.2 * Xr[:, 4]
+    X = np.zeros((n, S.N_PAD), dtype=np.float32)
+    X[:, :S.N_IN] = Xr
+    Xd = torch.tensor(X).to(torch.bfloat16).cuda()
+    td = torch.tensor(t.astype(np.float32)).cuda()
+    net = MLP(1024)
+    net.set_params(S.init_params(11).astype(np.float32))
+    hist = net.train(Xd, td, batch=512, epochs=25, lr_max=2e-3, seed=1)
+    net.sync()
+    assert np.all(np.isfinite(hist))
+    assert hist[-1] < 0.05 * np.var(t), hist
+    # the trained parameters, evaluated by the oracle, fit the data as well
+    yo, _ = S.forward(net.params().astype(np.float64), Xd.float().cpu().numpy().astype(np.float64), round_bf16=True)
+    assert np.mean((yo - t) ** 2) < 0.05 * np.var(t)
