@@ -249,6 +249,105 @@ def run_batch(args):
     return 0
 
 
+def run_surrogate(args):
+    """Annulus 512 radial x 2048 angular nodes, 9x9 micro, seeded smooth D:
+    the surrogate-accelerated scheme (network trained here on the GPU from
+    patch-solver data of 8 other seeded fields, 2.1e6 samples) against the
+    plain FP64 and FP32 schemes, 100 macro steps each, same grid and steps."""
+    import numpy as np
+    import torch
+
+    from paper_2405_08764_gb300 import workloads as W
+    from paper_2405_08764_gb300.api import MLP, Grid, Surrogate
+
+    torch.cuda.set_device(0)
+    n_macro = 100
+    p = W.c5_surrogate_field()
+    # training data from the patch solver: fields at step 0 and step 50, every 8th patch
+    t0 = time.perf_counter()
+    net = MLP(4096)
+    Xs, ys = [], []
+    for sd in range(1000, 1008):
+        q = W.c5_surrogate_field(seed=sd)
+        g = Grid(q, prec="fp32")
+        s = Surrogate(g, net)
+        U = g.init_field()
+        dtm = g.info()["dt_macro_suggested"]
+        for k in range(2):
+            f = s.features(U, standardised=False, raw=True)
+            y = s.targets(U, k * 50 * dtm, f["Rs"])
+            Xs.append(f["X_raw"][k::8].contiguous())
+            ys.append(y[k::8].contiguous())
+            g.step(U, k * 50 * dtm, dtm, 50)
+        del s, g
+    Xr, yr = torch.cat(Xs), torch.cat(ys)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    net.fit_norm(Xr, yr)
+    X, tt = net.pack(Xr, yr)
+    net.init(21)
+    t0 = time.perf_counter()
+    hist = net.train(X, tt, batch=args.batch, epochs=args.epochs, lr_max=2e-3, seed=2)
+    net.sync()
+    train_s = time.perf_counter() - t0
+    n_train = int(X.shape[0])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(torch.cuda.current_stream())
+        fn()
+        b.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    res = {}
+    fields = {}
+    for name, prec in (("plain_fp64", "fp64"), ("plain_fp32", "fp32")):
+        g = Grid(p, prec=prec)
+        dtm = g.info()["dt_macro_suggested"]
+        U = g.init_field()
+        g.step(U.clone(), 0.0, dtm, 2)          # warm-up (graph capture for 2 steps)
+        res[name] = timed(lambda: g.step(U, 0.0, dtm, n_macro))
+        g.sync()
+        fields[name] = U
+    g = Grid(p, prec="fp32")
+    s = Surrogate(g, net)
+    dtm = g.info()["dt_macro_suggested"]
+    W_ = g.init_field()
+    s.step(W_, 0.0, dtm, 2)                      # warm-up
+    U = g.init_field()
+    st0, fb0 = s.counts()
+    sampler = ClockSampler(0)
+    sampler.start()
+    res["surrogate"] = timed(lambda: s.step(U, 0.0, dtm, n_macro, eps=1e-3))
+    clocks = sampler.stop()
+    g.sync()
+    st1, fb1 = s.counts()
+    fields["surrogate"] = U
+    ref = fields["plain_fp64"]
+    err = {k: (torch.linalg.norm(v - ref) / torch.linalg.norm(ref)).item() for k, v in fields.items() if k != "plain_fp64"}
+    served = 1.0 - (fb1 - fb0) / max(1, st1 - st0)
+    value = n_macro / res["surrogate"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "macro steps/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * res["surrogate"] / n_macro, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+        "config": {"workload": "annulus 512x2048 macro nodes, 9x9 micro, K=20, seeded smooth D, 100 macro steps; "
+                               "surrogate 35-256-256-256-1 trained on %d patch-solver samples of 8 other fields" % n_train,
+                   "train_epochs": args.epochs, "train_batch": args.batch, "train_s": train_s, "data_s": data_s,
+                   "loss_first_last": [float(hist[0]), float(hist[-1])], "check_eps": 1e-3},
+        "macro_steps_per_s": {k: n_macro / v for k, v in res.items()},
+        "speedup_vs_plain_fp64": res["plain_fp64"] / res["surrogate"],
+        "speedup_vs_plain_fp32": res["plain_fp32"] / res["surrogate"],
+        "l2_rel_vs_plain_fp64": err,
+        "served_by_network": served,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -395,8 +494,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
-                    help="c2: the benchmark workload (default); c4: the 4096-instance batch")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
+                    help="c2: the benchmark workload (default); c4: the 4096-instance batch; "
+                         "c5: the surrogate against the plain scheme on the 512x2048 annulus")
+    ap.add_argument("--epochs", type=int, default=40, help="c5: training epochs")
+    ap.add_argument("--batch", type=int, default=4096, help="c5: training minibatch")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
@@ -406,6 +508,8 @@ def main():
     __graft_entry__.build()
     if args.workload == "c4":
         return run_batch(args)
+    if args.workload == "c5":
+        return run_surrogate(args)
     return run_gpu(args)
 
 

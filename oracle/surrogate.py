@@ -14,8 +14,10 @@ the readings below define one so that it can be checked:
     (an invertible map of the 25 values), feature 5*q_ord + p_ord.  With s the
     largest magnitude of the 24 non-constant terms, term k >= 1 becomes D_k/s
     and the constant term U00/(|U00| + s);
-  - 4 metric terms at the patch centre, each over the macro explicit rate R:
-    2 alpha/(dxi^2 R), 2 gamma/(deta^2 R), nu/(dxi R), omega/(deta R), with
+  - 4 metric terms at the patch centre, each over the macro explicit rate R
+    and times the stencil feature of the derivative it multiplies:
+    2 alpha/(dxi^2 R) x[2], 2 gamma/(deta^2 R) x[10], nu/(dxi R) x[1],
+    omega/(deta R) x[5], with
     R = 2 alpha/dxi^2 + 2 gamma/deta^2 + |beta|/(dxi deta) + |nu|/dxi + |omega|/deta + |phi|
     (the operator of Section 2, eq. (Computational_Problem));
   - 6 coefficient samples: half the trace of the diffusion tensor at the patch
@@ -31,7 +33,9 @@ the readings below define one so that it can be checked:
   g(x) = x/2 (1 + tanh(sqrt(2/pi)(x + 0.044715 x^3))) (Hendrycks & Gimpel,
   2016), inputs padded to 64 with zeros.  Flat parameter layout (FP32 on the
   device, FP64 here): W1[256][64], b1[256], W2[256][256], b2[256],
-  W3[256][256], b3[256], w4[256], b4.
+  W3[256][256], b3[256], w4[256], b4.  On the device each standardised
+  input x enters the first BF16 product as two terms, hi = bf16(x) and
+  lo = bf16(x - hi) (x in FP32), both multiplied by bf16(W1).
 
 Parity: the MLP backward is pinned by central finite differences and the GELU
 by its odd-part identity; the features by exact discrete derivatives of
@@ -115,17 +119,30 @@ def bf16(a):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def split_input(X):
+    """hi + lo with hi = bf16(x) and lo = bf16(x - hi), x taken in FP32."""
+    x32 = np.asarray(X, dtype=np.float32).astype(np.float64)
+    hi = bf16(x32)
+    lo = bf16((x32 - hi).astype(np.float32))
+    return hi, lo
+
+
 def forward(theta, X, round_bf16: bool = False):
     """y = w4 . g(W3 g(W2 g(W1 x + b1) + b2) + b3) + b4 for every row of X
-    (X: [n, 64] or [n, 35]).  With round_bf16 the inputs, W1..W3, w4 and the
-    first two hidden activations are rounded to BF16 where the device rounds
-    them (the third activation stays FP32 on the device)."""
+    (X: [n, 64] or [n, 35]).  With round_bf16 the inputs enter as hi + lo
+    (split_input), and W1..W3, w4 and the first two hidden activations are
+    rounded to BF16 where the device rounds them (the third activation stays
+    FP32 on the device)."""
     p = unflatten(theta)
     X = np.asarray(X, dtype=np.float64)
     if X.shape[1] == N_IN:
         X = np.pad(X, ((0, 0), (0, N_PAD - N_IN)))
     r = bf16 if round_bf16 else (lambda a: a)
-    z1 = r(X) @ r(p["W1"]).T + p["b1"]
+    if round_bf16:
+        hi, lo = split_input(X)
+        z1 = (hi @ r(p["W1"]).T + lo @ r(p["W1"]).T) + p["b1"]
+    else:
+        z1 = X @ p["W1"].T + p["b1"]
     h1 = r(gelu(z1))
     z2 = h1 @ r(p["W2"]).T + p["b2"]
     h2 = r(gelu(z2))
@@ -146,7 +163,8 @@ def gradient(theta, X, t, round_bf16: bool = False):
     rule through the four layers.  With round_bf16 the forward pass rounds as
     in forward(), and the back-propagated dZ of each layer is rounded to BF16
     before it enters the weight and input gradients (the device stores dZ in
-    BF16 as a tensor-core operand); the bias gradients then sum the rounded dZ."""
+    BF16 as a tensor-core operand); the bias gradients then sum the rounded dZ,
+    and the first layer's weight gradient takes the high input part only."""
     p = unflatten(theta)
     r = bf16 if round_bf16 else (lambda a: a)
     y, c = forward(theta, X, round_bf16)
@@ -249,9 +267,17 @@ def static_features(o: Oracle):
 
 
 def features(o: Oracle, U, static=None):
-    """Raw (unstandardised) features [n_patch, 35], the scale s and the rate R."""
+    """Raw (unstandardised) features [n_patch, 35], the scale s and the rate R:
+    the stencil features, the metric terms times the stencil feature of the
+    derivative each multiplies (x[2] = xi-second, x[10] = eta-second,
+    x[1] = xi-first, x[5] = eta-first difference), the coefficient samples."""
     fs, R = static_features(o) if static is None else static
     x, s = stencil_features(stencils(o, U))
+    fs = fs.copy()
+    fs[:, 0] *= x[:, 2]
+    fs[:, 1] *= x[:, 10]
+    fs[:, 2] *= x[:, 1]
+    fs[:, 3] *= x[:, 5]
     return np.concatenate([x, fs], 1), s, R
 
 

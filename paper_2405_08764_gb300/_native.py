@@ -98,6 +98,7 @@ SIGNATURES = {
     "pd_mlp_set_stream": (C.c_int, [_VP, _VP]),
     "pd_mlp_set_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.c_int]),
     "pd_mlp_get_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.c_int]),
+    "pd_mlp_init": (C.c_int, [_VP, C.c_ulonglong]),
     "pd_mlp_set_norm": (C.c_int, [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float]),
     "pd_mlp_get_norm": (C.c_int, [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "pd_mlp_fit_norm": (C.c_int, [_VP, _VP, _VP, C.c_longlong]),
@@ -109,8 +110,16 @@ SIGNATURES = {
     "pd_mlp_adam_step": (C.c_int, [_VP, C.c_float]),
     "pd_mlp_sync": (C.c_int, [_VP]),
     "pd_mlp_last_error": (C.c_char_p, [_VP]),
+    "pd_surrogate_create": (C.c_int, [_GP, _VP, C.POINTER(_VP)]),
+    "pd_surrogate_destroy": (C.c_int, [_VP]),
+    "pd_surrogate_features": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "pd_surrogate_targets": (C.c_int, [_VP, _VP, C.c_double, _VP, _VP]),
+    "pd_surrogate_evaluate": (C.c_int, [_VP, _VP, C.c_double, _VP, _VP, _VP]),
+    "pd_surrogate_step": (C.c_int, [_VP, _VP, C.c_double, C.c_double, C.c_int, C.c_double]),
+    "pd_surrogate_counts": (C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "pd_surrogate_perturb": (C.c_int, [_VP, _VP, C.c_double, C.c_ulonglong, _VP]),
 }
-MLP_N_IN, MLP_N_PAD, MLP_WIDTH, MLP_N_PARAM = 35, 64, 256, 148481
+MLP_N_IN, MLP_N_PAD, MLP_IN_COLS, MLP_WIDTH, MLP_N_PARAM = 35, 64, 128, 256, 148481
 
 _lock = threading.Lock()
 _lib = None

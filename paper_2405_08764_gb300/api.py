@@ -240,7 +240,8 @@ class Grid:
 class MLP:
     """The surrogate network of include/pd_surrogate.h on the current CUDA
     device (35 -> 256 -> 256 -> 256 -> 1, BF16 tensor-core GEMMs).  Inputs
-    are BF16 tensors [n, 64]; parameters are a flat FP32 vector."""
+    are BF16 tensors [n, 128] (high parts, then low parts); parameters are a
+    flat FP32 vector."""
 
     N_PARAM = N.MLP_N_PARAM
 
@@ -270,6 +271,11 @@ class MLP:
         self._stream()
         self._chk(self.L.pd_mlp_set_params(self.h, th.ctypes.data_as(C.POINTER(C.c_float)), th.size))
 
+    def init(self, seed: int):
+        """fan-in uniform initialisation on the device"""
+        self._stream()
+        self._chk(self.L.pd_mlp_init(self.h, int(seed)))
+
     def params(self) -> np.ndarray:
         th = np.zeros(self.N_PARAM, dtype=np.float32)
         self._stream()
@@ -297,7 +303,7 @@ class MLP:
 
     def pack(self, X_raw: torch.Tensor, y_raw: torch.Tensor = None):
         n = X_raw.shape[0]
-        X = torch.empty((n, N.MLP_N_PAD), dtype=torch.bfloat16, device=X_raw.device)
+        X = torch.empty((n, N.MLP_IN_COLS), dtype=torch.bfloat16, device=X_raw.device)
         t = torch.empty(n, dtype=torch.float32, device=X_raw.device) if y_raw is not None else None
         self._stream()
         self._chk(self.L.pd_mlp_pack(self.h, C.c_void_p(_ptr(X_raw)),
@@ -333,3 +339,73 @@ class MLP:
 
     def sync(self):
         self._chk(self.L.pd_mlp_sync(self.h))
+
+
+class Surrogate:
+    """The surrogate on a one-instance Grid (include/pd_surrogate.h): features,
+    training targets from the patch solver, and macro steps with the residual
+    check and the burst fallback."""
+
+    def __init__(self, grid: Grid, net: MLP):
+        self.grid, self.net = grid, net
+        self.L = N.load()
+        grid._stream()
+        net._stream()
+        h = C.c_void_p()
+        N.check(self.L.pd_surrogate_create(grid.h, net.h, C.byref(h)), grid.h)
+        self.h = h
+        self.n_patch = grid.info(0)["n_patch"]
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.pd_surrogate_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def _pre(self):
+        self.grid._stream()
+        self.net._stream()
+
+    def _p(self, t):
+        return C.c_void_p(_ptr(t)) if t is not None else None
+
+    def features(self, U: torch.Tensor, standardised: bool = True, raw: bool = False):
+        n = self.n_patch
+        X = torch.empty((n, N.MLP_IN_COLS), dtype=torch.bfloat16, device=U.device) if standardised else None
+        scale = torch.empty(n, dtype=torch.float64, device=U.device) if standardised else None
+        Xr = torch.empty((n, N.MLP_N_IN), dtype=torch.float32, device=U.device) if raw else None
+        Rs = torch.empty(n, dtype=torch.float64, device=U.device) if raw else None
+        self._pre()
+        N.check(self.L.pd_surrogate_features(self.h, self._p(U), self._p(X), self._p(scale), self._p(Xr), self._p(Rs)),
+                self.grid.h)
+        return dict(X=X, scale=scale, X_raw=Xr, Rs=Rs)
+
+    def targets(self, U: torch.Tensor, t: float, Rs: torch.Tensor) -> torch.Tensor:
+        y = torch.empty(self.n_patch, dtype=torch.float32, device=U.device)
+        self._pre()
+        N.check(self.L.pd_surrogate_targets(self.h, self._p(U), float(t), self._p(Rs), self._p(y)), self.grid.h)
+        return y
+
+    def evaluate(self, U: torch.Tensor, t: float, F_hat=True, F1=True, F=True):
+        out = {k: (torch.empty(self.n_patch, dtype=torch.float64, device=U.device) if want else None)
+               for k, want in (("F_hat", F_hat), ("F1", F1), ("F", F))}
+        self._pre()
+        N.check(self.L.pd_surrogate_evaluate(self.h, self._p(U), float(t), self._p(out["F_hat"]), self._p(out["F1"]),
+                                             self._p(out["F"])), self.grid.h)
+        return out
+
+    def step(self, U: torch.Tensor, t0: float, dt_macro: float, n_macro: int, eps: float = 1e-3):
+        self._pre()
+        N.check(self.L.pd_surrogate_step(self.h, self._p(U), float(t0), float(dt_macro), int(n_macro), float(eps)),
+                self.grid.h)
+
+    def perturb(self, U: torch.Tensor, rel_sigma: float, seed: int, out: torch.Tensor = None) -> torch.Tensor:
+        """U plus seeded grid-scale noise of relative size rel_sigma on the interior nodes"""
+        V = torch.empty_like(U) if out is None else out
+        self._pre()
+        N.check(self.L.pd_surrogate_perturb(self.h, self._p(U), float(rel_sigma), int(seed), self._p(V)), self.grid.h)
+        return V
+
+    def counts(self):
+        a, b = C.c_longlong(), C.c_longlong()
+        N.check(self.L.pd_surrogate_counts(self.h, C.byref(a), C.byref(b)), self.grid.h)
+        return a.value, b.value

@@ -1227,6 +1227,36 @@ pd_status pd_load_checkpoint(pd_grid* g, double* U, double* t, long long* step, 
 
 }  // extern "C"
 
+namespace pd {
+
+pd_status grid_access(pd_grid* g, int inst, GridAccess& out)
+{
+    if (!g) return PD_EINVAL;
+    if (inst < 0 || inst >= (int)g->inst.size()) return fail(g, PD_EINVAL, "instance index out of range");
+    const Inst& s = g->inst[inst];
+    if (!s.coef_set) return fail(g, PD_ESTATE, "coefficients not set");
+    out.I = s.I;
+    out.coef = s.coef;
+    out.prec = s.d.prec;
+    out.n_inst = (int)g->inst.size();
+    out.device = g->device;
+    out.stream = g->stream;
+    out.dtm_sugg = s.dtm_sugg;
+    return PD_OK;
+}
+
+void grid_message(pd_grid* g, const char* msg)
+{
+    if (g) g->last = msg;
+}
+
+void grid_count_launches(pd_grid* g, long long n)
+{
+    if (g) g->launches += n;
+}
+
+}  // namespace pd
+
 // ---------------------------------------------------------------------------
 // pd_step_noalloc: the fused per-step path of pd_step with both of its scratch
 // buffers (the second macro field and the per-step time table) carved out of

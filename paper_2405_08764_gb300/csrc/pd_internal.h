@@ -304,6 +304,32 @@ cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const
 cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm,
                            cudaStream_t st);
 bool fused_supported(const InstDev& I);
+// read access to one instance of a grid for the other parts of the library
+struct GridAccess {
+    InstDev I;                       // host copy; pointers are device pointers
+    pd_coeff_desc coef;
+    int prec = 0;
+    int n_inst = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    double dtm_sugg = 0.0;
+};
+}  // namespace pd
+struct pd_grid;
+namespace pd {
+// PD_ESTATE when the instance's coefficients are not set
+pd_status grid_access(pd_grid* g, int inst, GridAccess& out);
+void grid_message(pd_grid* g, const char* msg);
+void grid_count_launches(pd_grid* g, long long n);
+
+// restricted change of every patch (or of the flagged ones) after k_steps micro
+// steps from the lift of U; tab_row is a time-table row built for k_steps
+cudaError_t launch_patch_dU(const InstDev& I, int prec, const double* U, const double* tab_row, int k_steps,
+                            double* dU, const unsigned char* mask, cudaStream_t st);
+// per-patch surrogate features that do not depend on U (10 per patch) and the
+// macro explicit rate R at the patch centre
+cudaError_t launch_surrogate_static(const InstDev& I, const pd_coeff_desc& c, double tau, float* feat, double* R,
+                                    cudaStream_t st);
 bool batch_supported(const InstDev& I);
 
 // Persistent dataflow launch of n_steps macro steps (see pd_persist.cu).

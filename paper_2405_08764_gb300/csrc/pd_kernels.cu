@@ -25,7 +25,7 @@ namespace {
 
 constexpr unsigned FULL = kFull;
 
-enum { MODE_FUSED = 0, MODE_BURST = 1 };
+enum { MODE_FUSED = 0, MODE_BURST = 1, MODE_DU = 2 };
 
 // Burst record of one micro point (16 values, dt-scaled):
 //   0..5  stencil weights cE, cW, cN, cS, cX, cC with the mirror ghosts of the
@@ -70,14 +70,19 @@ __global__ void burst_record_kernel(const InstDev I, const real* __restrict__ re
 
 // One warp = P patches of one patch row.  MODE_FUSED: lift -> burst -> restrict
 // -> project for one macro step, writing U at T_next into Un.  MODE_BURST: load
-// (w, r) from the micro state, run k_steps, store w.
+// (w, r) from the micro state, run k_steps, store w.  MODE_DU: lift -> k_steps
+// micro steps -> restrict, writing the restricted change of patch p into
+// dU_out[p]; with a mask only flagged patches are written and warps without a
+// flagged patch return at once.
 template <int M, bool CROSS, bool TSRC, typename real, int MODE>
 __global__ void __launch_bounds__(128, (sizeof(real) == 4 ? 4 : 1))
 patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __restrict__ Un,
                   const double* __restrict__ tab, double upd_scale, double bias_scale, int k_steps,
-                  real* __restrict__ st_w, const real* __restrict__ st_r, int n_item_warps)
+                  real* __restrict__ st_w, const real* __restrict__ st_r, int n_item_warps,
+                  double* __restrict__ dU_out, const unsigned char* __restrict__ mask)
 {
     constexpr int P = 32 / M;
+    constexpr bool LIFT = (MODE != MODE_BURST);
     constexpr int NC = (9 + M - 1) / M;
     __shared__ double lw_s[9][9];
     __shared__ int slot_s[9][3];
@@ -87,13 +92,13 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     real* ds_s = reinterpret_cast<real*>(dyn_smem);   // TSRC: K entries
 
     const int K = (MODE == MODE_FUSED) ? I.K : k_steps;
-    if (MODE == MODE_FUSED) {
+    if (LIFT) {
         for (int t = threadIdx.x; t < 81; t += blockDim.x) lw_s[t / 9][t % 9] = I.lw[t / 9][t % 9];
         for (int t = threadIdx.x; t < 27; t += blockDim.x) { slot_s[t / 3][t % 3] = I.c2slot[t / 3][t % 3]; cw_s[t / 3][t % 3] = I.c2w[t / 3][t % 3]; }
     }
     if (TSRC)
         for (int t = threadIdx.x; t < K; t += blockDim.x) ds_s[t] = (real)tab[t];
-    if (MODE == MODE_FUSED && threadIdx.x < 3) tinfo[threadIdx.x] = tab[K + threadIdx.x];
+    if (LIFT && threadIdx.x < 3) tinfo[threadIdx.x] = tab[K + threadIdx.x];
     __syncthreads();
 
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -121,10 +126,15 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     const int icl = active ? ic : (I.ncols - 1);
     const int i = I.i0 + icl, j = 1 + jr;
     const int qbase = (q < P ? q : P - 1) * M;
+    const int pidx = jr * I.ncols + icl;
+    if (MODE == MODE_DU && mask) {
+        const bool need = active && mask[pidx];
+        if (!__any_sync(FULL, need)) return;
+    }
 
     real cv[9];
     double bias = 0.0, u00 = 0.0;
-    if (MODE == MODE_FUSED) {
+    if (LIFT) {
         double c20, c02;
         macro_coeffs<M, real, false>(I, Uc, i, j, a, qbase, lw_s, slot_s, cw_s, cv, c20, c02, u00);
         if (I.restrict_mode == PD_RESTRICT_MACRO) {
@@ -136,7 +146,7 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     // per-point stencil weights, forcing and source from the burst records
     real w[M], Rr[M];
     real cE[M], cW[M], cN[M], cS[M], cC[M], cX[M], Gs[M];
-    const real sT = (MODE == MODE_FUSED) ? (real)tinfo[0] : real(0);
+    const real sT = LIFT ? (real)tinfo[0] : real(0);
     const real dt = (real)I.dt;
     const real* brec = static_cast<const real*>(I.brec);
     const long long rowstride = (long long)I.ncols * M;
@@ -149,7 +159,7 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
         load_vec4<real>(p, e, ww, n, s);
         load_vec4<real>(p + 4, x, cc, g, B0);
         real r;
-        if (MODE == MODE_FUSED) {
+        if (LIFT) {
             load_vec4<real>(p + 8, B1, B2, B3, B4);
             r = sT * g;
             r = fma(B0, cv[0], r); r = fma(B1, cv[1], r); r = fma(B2, cv[2], r);
@@ -198,8 +208,12 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     if (active && a == 0) {
         double inc = fma((double)col, upd_scale, bias * bias_scale);
         if (!isfinite(inc)) atomicOr(I.err, ERR_NONFINITE);
-        long long node = (long long)j * I.nxp + i;
-        Un[node] = u00 + inc;
+        if (MODE == MODE_DU) {
+            if (!mask || mask[pidx]) dU_out[pidx] = inc;
+        } else {
+            long long node = (long long)j * I.nxp + i;
+            Un[node] = u00 + inc;
+        }
     }
 }
 
@@ -377,11 +391,13 @@ __global__ void lift_table_kernel(int tkind, double tc, double t, double* tab, d
 
 template <int M, typename real, int MODE>
 cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const double* tab, double dtm,
-                        int k_steps, real* st_w, const real* st_r, cudaStream_t st)
+                        int k_steps, real* st_w, const real* st_r, cudaStream_t st,
+                        double* dU_out = nullptr, const unsigned char* mask = nullptr)
 {
     // dt_macro / tau scales the restricted change; the trapezoid sum also carries 1 / n^2
-    double bias_scale = dtm * I.inv_tau;
-    double upd_scale = bias_scale * I.inv_nn;
+    // (MODE_DU writes the restricted change itself)
+    double bias_scale = (MODE == MODE_DU) ? 1.0 : dtm * I.inv_tau;
+    double upd_scale = (MODE == MODE_DU) ? I.inv_nn : bias_scale * I.inv_nn;
     constexpr int P = 32 / M;
     int wpr = (I.ncols + P - 1) / P;
     int n_item_warps = wpr * I.nrows;
@@ -392,7 +408,7 @@ cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const do
     bool cross = I.has_cross != 0, tsrc = I.has_tsrc != 0;
     int K = (MODE == MODE_FUSED) ? I.K : k_steps;
     size_t smem = tsrc ? sizeof(real) * (size_t)K : 0;
-#define PD_LAUNCH(CR, TS) patch_warp_kernel<M, CR, TS, real, MODE><<<nb, bs, smem, st>>>(I, Uc, Un, tab, upd_scale, bias_scale, k_steps, st_w, st_r, n_item_warps)
+#define PD_LAUNCH(CR, TS) patch_warp_kernel<M, CR, TS, real, MODE><<<nb, bs, smem, st>>>(I, Uc, Un, tab, upd_scale, bias_scale, k_steps, st_w, st_r, n_item_warps, dU_out, mask)
     if (cross && tsrc) PD_LAUNCH(true, true);
     else if (cross) PD_LAUNCH(true, false);
     else if (tsrc) PD_LAUNCH(false, true);
@@ -403,14 +419,15 @@ cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const do
 
 template <typename real, int MODE>
 cudaError_t dispatch_m(const InstDev& I, const double* Uc, double* Un, const double* tab, double dtm,
-                       int k_steps, real* st_w, const real* st_r, cudaStream_t st)
+                       int k_steps, real* st_w, const real* st_r, cudaStream_t st,
+                       double* dU_out = nullptr, const unsigned char* mask = nullptr)
 {
     switch (I.mx) {
-    case 3: return launch_warp<3, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
-    case 5: return launch_warp<5, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
-    case 7: return launch_warp<7, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
-    case 9: return launch_warp<9, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
-    case 11: return launch_warp<11, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st);
+    case 3: return launch_warp<3, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
+    case 5: return launch_warp<5, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
+    case 7: return launch_warp<7, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
+    case 9: return launch_warp<9, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
+    case 11: return launch_warp<11, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -436,6 +453,14 @@ bool batch_supported(const InstDev& I)
 bool fused_supported(const InstDev& I)
 {
     return I.mx == I.my && (I.mx == 3 || I.mx == 5 || I.mx == 7 || I.mx == 9 || I.mx == 11) && I.K <= kMaxK;
+}
+
+cudaError_t launch_patch_dU(const InstDev& I, int prec, const double* U, const double* tab_row, int k_steps,
+                            double* dU, const unsigned char* mask, cudaStream_t st)
+{
+    if (prec == PD_FP32)
+        return dispatch_m<float, MODE_DU>(I, U, nullptr, tab_row, 0.0, k_steps, nullptr, nullptr, st, dU, mask);
+    return dispatch_m<double, MODE_DU>(I, U, nullptr, tab_row, 0.0, k_steps, nullptr, nullptr, st, dU, mask);
 }
 
 cudaError_t launch_fused_step(const InstDev& I, const InstDev*, int prec, const double* Uc, double* Un,

@@ -24,6 +24,7 @@ using bf16 = __nv_bfloat16;
 constexpr int kWidth = PD_MLP_WIDTH;
 constexpr int kIn = PD_MLP_N_IN;
 constexpr int kPad = PD_MLP_N_PAD;
+constexpr int kInCols = PD_MLP_IN_COLS;      // network input row: 64 high parts, then 64 low parts
 constexpr int kStages = 4;
 constexpr int kBM = 128, kBK = 64;
 constexpr int kErrTimeout = 8;
@@ -261,8 +262,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // ---------------------------------------------------------------------------
 // elementwise training kernels
 
-// Minibatch rows r of [B][64] from sample (a (s0 + r) + b) mod n (or row r of
-// X when a == 0), with the transposed copy [64][ld] and the targets; rows at
+// Minibatch rows r of [B][128] from sample (a (s0 + r) + b) mod n (or row r of
+// X when a == 0), the transposed high parts [64][ld] and the targets; rows at
 // or past n_valid are zero.  Block: 64 rows, 256 threads.
 __global__ void __launch_bounds__(256) gather_kernel(const bf16* __restrict__ X, const float* __restrict__ T,
                                                      long long n, unsigned long long ma, unsigned long long mb,
@@ -271,21 +272,23 @@ __global__ void __launch_bounds__(256) gather_kernel(const bf16* __restrict__ X,
 {
     __shared__ bf16 tile[64][kPad + 2];
     const int r0 = blockIdx.x * 64;
-    for (int e = threadIdx.x; e < 64 * 8; e += blockDim.x) {
-        const int r = e >> 3, q = e & 7;
+    for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
+        const int r = e >> 4, q = e & 15;
         const int row = r0 + r;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (row < n_valid) {
             long long src = ma ? (long long)((ma * (unsigned long long)(s0 + row) + mb) % (unsigned long long)n) : (long long)row;
-            v = reinterpret_cast<const uint4*>(X + (size_t)src * kPad)[q];
+            v = reinterpret_cast<const uint4*>(X + (size_t)src * kInCols)[q];
             if (q == 0 && T) tb[row] = T[src];
         } else if (q == 0) {
             tb[row] = 0.0f;
         }
-        reinterpret_cast<uint4*>(Xb + (size_t)row * kPad)[q] = v;
-        const bf16* h = reinterpret_cast<const bf16*>(&v);
+        reinterpret_cast<uint4*>(Xb + (size_t)row * kInCols)[q] = v;
+        if (q < 8) {
+            const bf16* h = reinterpret_cast<const bf16*>(&v);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) tile[r][q * 8 + k] = h[k];
+            for (int k = 0; k < 8; ++k) tile[r][q * 8 + k] = h[k];
+        }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
@@ -414,7 +417,10 @@ __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ grad,
     }
     const bf16 h = __float2bfloat16_rn(th);
     if (i < OFF_B1) {
-        W1b[i] = h;
+        // the high and the low input parts meet the same first-layer weights
+        const int n = i / kPad, k = i - n * kPad;
+        W1b[n * kInCols + k] = h;
+        W1b[n * kInCols + kPad + k] = h;
     } else if (i >= OFF_W2 && i < OFF_B2) {
         const int k = i - OFF_W2;
         W2b[k] = h;
@@ -460,7 +466,8 @@ __global__ void norm_stats_kernel(const float* __restrict__ X, const float* __re
     if (threadIdx.x == 0) atomicAdd(&acc[kIn], s1[kIn]);
 }
 
-// (x - mu)/sigma rounded to BF16 into [n][64] (padding zero), y/y_scale.
+// v = (x - mu)/sigma in FP32 into the network input row [128]: hi = bf16(v)
+// at column k, lo = bf16(v - hi) at column 64 + k (padding zero); y/y_scale.
 __global__ void pack_kernel(const float* __restrict__ X, const float* __restrict__ y, long long n,
                             const float* __restrict__ norm, bf16* __restrict__ Xo, float* __restrict__ to)
 {
@@ -470,8 +477,30 @@ __global__ void pack_kernel(const float* __restrict__ X, const float* __restrict
     const int k = (int)(e - r * kPad);
     float v = 0.0f;
     if (k < kIn) v = (X[r * kIn + k] - norm[k]) / norm[kIn + k];
-    Xo[e] = __float2bfloat16_rn(v);
+    const bf16 hi = __float2bfloat16_rn(v);
+    Xo[r * kInCols + k] = hi;
+    Xo[r * kInCols + kPad + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
     if (k == 0 && y && to) to[r] = y[r] / norm[2 * kIn];
+}
+
+// Fan-in uniform initialisation: every weight and bias of a layer with fan-in
+// f is drawn from U(-1/sqrt f, 1/sqrt f) (f = 35 for the first layer, 256
+// after it); the padding columns of W1 stay zero.  The draw for parameter i is
+// splitmix64(seed + (i + 1) * golden) scaled to [0, 1).
+__global__ void init_kernel(float* __restrict__ theta, unsigned long long seed)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N_PARAM) return;
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    double bound;
+    if (i < OFF_B1) bound = (i % kPad) < kIn ? 1.0 / sqrt((double)kIn) : 0.0;
+    else if (i < OFF_W2) bound = 1.0 / sqrt((double)kIn);
+    else bound = 1.0 / sqrt((double)kWidth);
+    theta[i] = (float)((2.0 * u - 1.0) * bound);
 }
 
 // learning rate of step s (device-side, so a captured step graph reads it)
@@ -618,7 +647,7 @@ pd_status fwd_bwd(pd_mlp* m, int B, int n_valid)
     const float* th = m->theta;
     // forward: Z_l, H_l (row-major and transposed)
     {
-        GemmArgs a = base_args(m, B, kWidth, kPad);
+        GemmArgs a = base_args(m, B, kWidth, kInCols);
         a.ldo = kWidth; a.ldt = m->cap; a.bias = th + OFF_B1; a.out_z = m->Z1; a.out_bf16 = m->H1; a.out_bf16_t = m->H1t;
         MCUDA(m, (launch_gemm<256, EPI_GELU>(m->mp.Xb, m->mp.W1, a, 1, st)));
     }
@@ -699,15 +728,15 @@ pd_status pd_mlp_create(int max_batch, void* stream, pd_mlp** out)
     const size_t B = (size_t)max_batch, C = (size_t)m->chunk, W = kWidth;
 #define A_(p, n) if ((e = alloc(m, &m->p, (n))) != cudaSuccess) { pd_mlp_destroy(m); return PD_ENOMEM; }
     A_(theta, N_PARAM) A_(grad, N_PARAM) A_(m1, N_PARAM) A_(m2, N_PARAM) A_(w4b, W)
-    A_(W1b, W * kPad) A_(W2b, W * W) A_(W3b, W * W) A_(W2t, W * W) A_(W3t, W * W)
-    A_(norm, 2 * kIn + 1) A_(Xb, B * kPad) A_(Xbt, B * kPad) A_(H1, B * W) A_(H1t, B * W) A_(H2, B * W) A_(H2t, B * W)
+    A_(W1b, W * kInCols) A_(W2b, W * W) A_(W3b, W * W) A_(W2t, W * W) A_(W3t, W * W)
+    A_(norm, 2 * kIn + 1) A_(Xb, B * kInCols) A_(Xbt, B * kPad) A_(H1, B * W) A_(H1t, B * W) A_(H2, B * W) A_(H2t, B * W)
     A_(dZ3, B * W) A_(dZ3t, B * W) A_(dZ2, B * W) A_(dZ2t, B * W) A_(dZ1, B * W) A_(dZ1t, B * W)
     A_(Z1, B * W) A_(Z2, B * W) A_(Z3, B * W) A_(tb, B) A_(loss, 1) A_(lr, 1) A_(I1, C * W) A_(I2, C * W)
     A_(stats, 2 * kIn + 1) A_(err, 1)
 #undef A_
     Maps& p = m->mp;
     const long long b = max_batch;
-    bool ok = make_map(&p.Xb, m->Xb, b, kPad, kPad, 128) && make_map(&p.W1, m->W1b, W, kPad, kPad, 256)
+    bool ok = make_map(&p.Xb, m->Xb, b, kInCols, kInCols, 128) && make_map(&p.W1, m->W1b, W, kInCols, kInCols, 256)
            && make_map(&p.H1, m->H1, b, W, W, 128) && make_map(&p.W2, m->W2b, W, W, W, 256)
            && make_map(&p.H2, m->H2, b, W, W, 128) && make_map(&p.W3, m->W3b, W, W, W, 256)
            && make_map(&p.dZ3t, m->dZ3t, W, max_batch, max_batch, 128) && make_map(&p.H2t, m->H2t, W, max_batch, max_batch, 256)
@@ -756,6 +785,18 @@ pd_status pd_mlp_set_params(pd_mlp* m, const float* theta, int n)
     if (rc) return rc;
     MCUDA(m, cudaStreamSynchronize(m->stream));
     return PD_OK;
+}
+
+pd_status pd_mlp_init(pd_mlp* m, unsigned long long seed)
+{
+    if (!m) return PD_EINVAL;
+    init_kernel<<<(N_PARAM + 255) / 256, 256, 0, m->stream>>>(m->theta, seed);
+    MCUDA(m, cudaGetLastError());
+    MCUDA(m, cudaMemsetAsync(m->m1, 0, sizeof(float) * N_PARAM, m->stream));
+    MCUDA(m, cudaMemsetAsync(m->m2, 0, sizeof(float) * N_PARAM, m->stream));
+    MCUDA(m, cudaMemsetAsync(m->grad, 0, sizeof(float) * N_PARAM, m->stream));
+    m->step = 0;
+    return refresh_copies(m);
 }
 
 pd_status pd_mlp_get_params(pd_mlp* m, float* theta, int n)
@@ -831,11 +872,11 @@ pd_status pd_mlp_forward(pd_mlp* m, const uint16_t* X, long long n, float* y)
     if (!X || !y || n < 0) return mfail(m, PD_EINVAL, "null argument");
     if (n == 0) return PD_OK;
     CUtensorMap mx;
-    if (!make_map(&mx, X, n, kPad, kPad, 128)) return mfail(m, PD_EINVAL, "input must be 16-byte aligned [n][64] BF16");
+    if (!make_map(&mx, X, n, kInCols, kInCols, 128)) return mfail(m, PD_EINVAL, "input must be 16-byte aligned [n][128] BF16");
     for (long long c0 = 0; c0 < n; c0 += m->chunk) {
         const int M = (int)std::min<long long>(m->chunk, n - c0);
         {
-            GemmArgs a = base_args(m, M, kWidth, kPad);
+            GemmArgs a = base_args(m, M, kWidth, kInCols);
             a.a_row0 = (int)c0; a.ldo = kWidth; a.bias = m->theta + OFF_B1; a.out_bf16 = m->I1;
             MCUDA(m, (launch_gemm<256, EPI_GELU>(mx, m->mp.W1, a, 1, m->stream)));
         }

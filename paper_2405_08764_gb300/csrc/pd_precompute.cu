@@ -461,7 +461,50 @@ __global__ void batch_time_table_kernel(const InstDev* __restrict__ insts, int n
     (void)n_macro;
 }
 
+// Surrogate features of patch p that do not change with U: the four metric
+// terms over the macro explicit rate R at the centre, half the trace of the
+// diffusion tensor at the centre and its relative change at the edge
+// midpoints E, W, N, S, and tau R.
+__global__ void surrogate_static_kernel(const InstDev I, const CoefDev C, double tau, float* __restrict__ feat,
+                                        double* __restrict__ Rout)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= I.n_patch) return;
+    const int i = I.i0 + p % I.ncols, j = 1 + p / I.ncols;
+    const double xi = I.xi0 + i * I.Dx, eta = I.eta0 + j * I.Dy;
+    Jet m = eval_map(I, xi, eta);
+    PhysPoint P = eval_phys(C, m.x, m.y);
+    double c[6];
+    transformed(m, P, c);
+    const double R = 2.0 * c[0] / (I.Dx * I.Dx) + 2.0 * c[2] / (I.Dy * I.Dy) + fabs(c[1]) / (I.Dx * I.Dy)
+                   + fabs(c[3]) / I.Dx + fabs(c[4]) / I.Dy + fabs(c[5]);
+    auto dhalf = [&](double a, double b) {
+        Jet q = eval_map(I, a, b);
+        PhysPoint Q = eval_phys(C, q.x, q.y);
+        return 0.5 * (Q.K.a + Q.K.c);
+    };
+    const double dc = 0.5 * (P.K.a + P.K.c);
+    const double de[4] = { dhalf(xi + 0.5 * I.hx, eta), dhalf(xi - 0.5 * I.hx, eta),
+                           dhalf(xi, eta + 0.5 * I.hy), dhalf(xi, eta - 0.5 * I.hy) };
+    float* o = feat + (long long)p * 10;
+    o[0] = (float)(2.0 * c[0] / (I.Dx * I.Dx * R));
+    o[1] = (float)(2.0 * c[2] / (I.Dy * I.Dy * R));
+    o[2] = (float)(c[3] / (I.Dx * R));
+    o[3] = (float)(c[4] / (I.Dy * R));
+    o[4] = (float)dc;
+    for (int k = 0; k < 4; ++k) o[5 + k] = (float)((de[k] - dc) / dc);
+    o[9] = (float)(tau * R);
+    Rout[p] = R;
+}
+
 }  // namespace
+
+cudaError_t launch_surrogate_static(const InstDev& I, const pd_coeff_desc& c, double tau, float* feat, double* R,
+                                    cudaStream_t st)
+{
+    surrogate_static_kernel<<<(I.n_patch + 127) / 128, 128, 0, st>>>(I, to_dev(c), tau, feat, R);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch_time_tables(const InstDev* insts, int n_inst, const double* dtm, double t0, int n_macro,
                                      const long long* tab_off, double* tab, long long total, cudaStream_t st)

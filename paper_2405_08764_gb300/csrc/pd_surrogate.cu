@@ -1,0 +1,452 @@
+// The surrogate on a grid: per-patch features from the macro field, the
+// residual check against a one-micro-step burst, the masked fallback to the
+// full burst, and the macro update (C ABI of include/pd_surrogate.h).
+#include "pd_internal.h"
+#include "pd_surrogate.h"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <string>
+
+using namespace pd;
+
+namespace {
+
+constexpr int kIn = PD_MLP_N_IN;
+constexpr int kPad = PD_MLP_N_PAD;
+constexpr int kInCols = PD_MLP_IN_COLS;
+constexpr int kStatic = 10;
+
+__device__ __forceinline__ void diff_basis(const double u[5], double e[5])
+{
+    // offsets -2..2 -> value, first, second, third and fourth differences
+    e[0] = u[2];
+    e[1] = 0.5 * (u[3] - u[1]);
+    e[2] = u[3] - 2.0 * u[2] + u[1];
+    e[3] = 0.5 * (u[4] - 2.0 * u[3] + 2.0 * u[1] - u[0]);
+    e[4] = u[4] - 4.0 * u[3] + 6.0 * u[2] - 4.0 * u[1] + u[0];
+}
+
+// One patch per thread: the 5x5 stencil (xi wraps on periodic grids, clamps
+// otherwise; eta clamps), its difference basis normalised by s, the metric
+// terms times the matching differences, the coefficient samples; then the
+// network input row (high and low BF16 parts of the standardised features)
+// and the output scale and/or the raw features and R s.
+__global__ void features_kernel(const InstDev I, const double* __restrict__ U, const float* __restrict__ stat,
+                                const double* __restrict__ R, const float* __restrict__ norm,
+                                __nv_bfloat16* __restrict__ X, double* __restrict__ scale,
+                                float* __restrict__ Xraw, double* __restrict__ Rs)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= I.n_patch) return;
+    const int i = I.i0 + p % I.ncols, j = 1 + p / I.ncols;
+    double a[5][5];
+    for (int q = 0; q < 5; ++q) {
+        const int row = min(max(j + q - 2, 0), I.n_eta);
+        double u[5];
+        for (int o = 0; o < 5; ++o) {
+            int c = i + o - 2;
+            if (I.periodic) c = (c % I.nxp + I.nxp) % I.nxp;
+            else c = min(max(c, 0), I.n_xi);
+            u[o] = U[(long long)row * I.nxp + c];
+        }
+        diff_basis(u, a[q]);
+    }
+    double D[25];
+    for (int po = 0; po < 5; ++po) {
+        double u[5], e[5];
+        for (int q = 0; q < 5; ++q) u[q] = a[q][po];
+        diff_basis(u, e);
+        for (int qo = 0; qo < 5; ++qo) D[5 * qo + po] = e[qo];
+    }
+    double s = 0.0;
+    for (int k = 1; k < 25; ++k) s = fmax(s, fabs(D[k]));
+    float x[kIn];
+    const double den = fabs(D[0]) + s;
+    x[0] = den > 0.0 ? (float)(D[0] / den) : 0.0f;
+    for (int k = 1; k < 25; ++k) x[k] = s > 0.0 ? (float)(D[k] / s) : 0.0f;
+    const float* st = stat + (long long)p * kStatic;
+    x[25] = (float)((double)st[0] * (s > 0.0 ? D[2] / s : 0.0));
+    x[26] = (float)((double)st[1] * (s > 0.0 ? D[10] / s : 0.0));
+    x[27] = (float)((double)st[2] * (s > 0.0 ? D[1] / s : 0.0));
+    x[28] = (float)((double)st[3] * (s > 0.0 ? D[5] / s : 0.0));
+    for (int k = 4; k < kStatic; ++k) x[25 + k] = st[k];
+    const double rs = R[p] * s;
+    if (Xraw) {
+        for (int k = 0; k < kIn; ++k) Xraw[(long long)p * kIn + k] = x[k];
+    }
+    if (Rs) Rs[p] = rs;
+    if (X) {
+        __nv_bfloat162* hi = reinterpret_cast<__nv_bfloat162*>(X + (long long)p * kInCols);
+        __nv_bfloat162* lo = hi + kPad / 2;
+        for (int k = 0; k < kPad; k += 2) {
+            const float v0 = k < kIn ? (x[k] - norm[k]) / norm[kIn + k] : 0.0f;
+            const float v1 = k + 1 < kIn ? (x[k + 1] - norm[k + 1]) / norm[kIn + k + 1] : 0.0f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            hi[k / 2] = h;
+            lo[k / 2] = __floats2bfloat162_rn(v0 - __bfloat162float(h.x), v1 - __bfloat162float(h.y));
+        }
+    }
+    if (scale) scale[p] = rs * (double)norm[2 * kIn];
+}
+
+__global__ void targets_kernel(int n, const double* __restrict__ dU, const double* __restrict__ Rs, double tau,
+                               float* __restrict__ y)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double r = Rs[p];
+    y[p] = r > 0.0 ? (float)(dU[p] / (tau * r)) : 0.0f;
+}
+
+__global__ void scale_out_kernel(int n, const double* __restrict__ in, double f, double* __restrict__ out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) out[p] = in[p] * f;
+}
+
+__global__ void predict_kernel(int n, const float* __restrict__ yhat, const double* __restrict__ scale,
+                               double* __restrict__ out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) out[p] = (double)yhat[p] * scale[p];
+}
+
+// sum over patches of (dU1 / dt)^2
+__global__ void sumsq_kernel(int n, const double* __restrict__ dU1, double inv_dt, double* __restrict__ acc)
+{
+    double v = 0.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const double f = dU1[p] * inv_dt;
+        v += f * f;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(acc, t);
+    }
+}
+
+// The residual check: keep F_hat = yhat * scale when |F_hat - F1| <= eps (|F1| + rho),
+// rho = sqrt(sum F1^2 / n), writing its restricted change F_hat tau; flag the rest.
+__global__ void check_kernel(int n, const float* __restrict__ yhat, const double* __restrict__ scale,
+                             const double* __restrict__ dU1, const double* __restrict__ sumsq, double inv_dt,
+                             double tau, double eps, double* __restrict__ dUf, unsigned char* __restrict__ mask,
+                             unsigned long long* __restrict__ n_fb)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    bool fb = false;
+    if (p < n) {
+        const double rho = sqrt(*sumsq / (double)n);
+        const double F1 = dU1[p] * inv_dt;
+        const double Fh = (double)yhat[p] * scale[p];
+        const bool ok = eps >= 0.0 && isfinite(Fh) && fabs(Fh - F1) <= eps * (fabs(F1) + rho);
+        if (ok) dUf[p] = Fh * tau;
+        mask[p] = ok ? 0 : 1;
+        fb = !ok;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, fb);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_fb, (unsigned long long)__popc(b));
+}
+
+__global__ void maxabs_kernel(long long n, const double* __restrict__ U, unsigned long long* __restrict__ out)
+{
+    double v = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        v = fmax(v, fabs(U[k]));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double uniform01(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void perturb_kernel(const InstDev I, const double* __restrict__ U, const unsigned long long* __restrict__ mx,
+                               double rel_sigma, unsigned long long seed, double* __restrict__ V)
+{
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = (long long)I.nxp * I.nyp;
+    if (k >= n) return;
+    const int j = (int)(k / I.nxp), i = (int)(k - (long long)j * I.nxp);
+    const bool interior = j > 0 && j < I.n_eta && (I.periodic || (i > 0 && i < I.n_xi));
+    double v = U[k];
+    if (interior) {
+        const double u1 = uniform01(seed + 2 * (unsigned long long)k * 0x9E3779B97F4A7C15ull);
+        const double u2 = uniform01(seed + (2 * (unsigned long long)k + 1) * 0x9E3779B97F4A7C15ull);
+        const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        v += rel_sigma * __longlong_as_double((long long)*mx) * z;
+    }
+    V[k] = v;
+}
+
+}  // namespace
+
+struct pd_surrogate {
+    pd_grid* g = nullptr;
+    pd_mlp* m = nullptr;
+    GridAccess ga;
+    InstDev I1;                      // the instance with K = 1 (the check burst)
+    int n = 0;
+    float* stat = nullptr;
+    double* R = nullptr;
+    uint16_t* X = nullptr;
+    double *scale = nullptr, *dU1 = nullptr, *dUf = nullptr, *sumsq = nullptr;
+    float* yhat = nullptr;
+    float* norm = nullptr;
+    unsigned char* mask = nullptr;
+    unsigned long long* n_fb = nullptr;
+    unsigned long long* umax = nullptr;
+    double *tab1 = nullptr, *tabK = nullptr;
+    size_t tab_steps = 0;
+    long long patch_steps = 0;
+    std::string last;
+};
+
+namespace {
+
+pd_status sfail(pd_surrogate* s, pd_status rc, const std::string& msg)
+{
+    if (s) {
+        s->last = msg;
+        grid_message(s->g, msg.c_str());
+    }
+    return rc;
+}
+
+#define SCUDA(s, call)                                                                                      \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess) return sfail(s, PD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+pd_status upload_norm(pd_surrogate* s)
+{
+    float h[2 * kIn + 1];
+    pd_status rc = pd_mlp_get_norm(s->m, h, h + kIn, h + 2 * kIn);
+    if (rc) return sfail(s, rc, "network normalisation");
+    SCUDA(s, cudaMemcpyAsync(s->norm, h, sizeof(h), cudaMemcpyHostToDevice, s->ga.stream));
+    SCUDA(s, cudaStreamSynchronize(s->ga.stream));
+    return PD_OK;
+}
+
+pd_status ensure_tables(pd_surrogate* s, int n_steps)
+{
+    if ((size_t)n_steps <= s->tab_steps) return PD_OK;
+    SCUDA(s, cudaStreamSynchronize(s->ga.stream));
+    cudaFree(s->tab1);
+    cudaFree(s->tabK);
+    s->tab1 = s->tabK = nullptr;
+    SCUDA(s, cudaMalloc(&s->tab1, sizeof(double) * (size_t)n_steps * (1 + kTabExtra)));
+    SCUDA(s, cudaMalloc(&s->tabK, sizeof(double) * (size_t)n_steps * (s->ga.I.K + kTabExtra)));
+    s->tab_steps = (size_t)n_steps;
+    return PD_OK;
+}
+
+unsigned blocks(int n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_surrogate_create(pd_grid* g, pd_mlp* m, pd_surrogate** out)
+{
+    if (!g || !m || !out) return PD_EINVAL;
+    *out = nullptr;
+    pd_surrogate* s = new pd_surrogate();
+    s->g = g;
+    s->m = m;
+    pd_status rc = grid_access(g, 0, s->ga);
+    if (rc) { delete s; return rc; }
+    const InstDev& I = s->ga.I;
+    if (s->ga.n_inst != 1) { delete s; grid_message(g, "the surrogate takes a grid of one instance"); return PD_EINVAL; }
+    if (I.coef_mode != COEF_RECORDS || !fused_supported(I)) {
+        delete s;
+        grid_message(g, "the surrogate needs per-point coefficient records and m_xi == m_eta in {3,5,7,9,11}");
+        return PD_EINVAL;
+    }
+    s->I1 = I;
+    s->I1.K = 1;
+    s->n = I.n_patch;
+    const size_t n = (size_t)s->n;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    A((void**)&s->stat, n * kStatic * sizeof(float));
+    A((void**)&s->R, n * sizeof(double));
+    A((void**)&s->X, n * kInCols * sizeof(uint16_t));
+    A((void**)&s->scale, n * sizeof(double));
+    A((void**)&s->dU1, n * sizeof(double));
+    A((void**)&s->dUf, n * sizeof(double));
+    A((void**)&s->yhat, n * sizeof(float));
+    A((void**)&s->mask, n);
+    A((void**)&s->sumsq, sizeof(double));
+    A((void**)&s->norm, (2 * kIn + 1) * sizeof(float));
+    A((void**)&s->n_fb, sizeof(unsigned long long));
+    A((void**)&s->umax, sizeof(unsigned long long));
+    if (e != cudaSuccess) { pd_surrogate_destroy(s); grid_message(g, "surrogate buffers"); return PD_ENOMEM; }
+    cudaStream_t st = s->ga.stream;
+    e = cudaMemsetAsync(s->n_fb, 0, sizeof(unsigned long long), st);
+    const double tau = I.K * I.dt;
+    if (e == cudaSuccess) e = launch_surrogate_static(I, s->ga.coef, tau, s->stat, s->R, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        grid_message(g, cudaGetErrorString(e));
+        pd_surrogate_destroy(s);
+        return PD_ECUDA;
+    }
+    grid_count_launches(g, 1);
+    *out = s;
+    return PD_OK;
+}
+
+pd_status pd_surrogate_destroy(pd_surrogate* s)
+{
+    if (!s) return PD_EINVAL;
+    if (s->ga.stream) cudaStreamSynchronize(s->ga.stream);
+    void* ptrs[] = { s->stat, s->R, s->X, s->scale, s->dU1, s->dUf, s->yhat, s->mask, s->sumsq, s->norm,
+                     s->n_fb, s->umax, s->tab1, s->tabK };
+    for (void* p : ptrs) cudaFree(p);
+    delete s;
+    return PD_OK;
+}
+
+pd_status pd_surrogate_features(pd_surrogate* s, const double* U, uint16_t* X, double* scale, float* Xraw, double* Rs)
+{
+    if (!s) return PD_EINVAL;
+    if (!U) return sfail(s, PD_EINVAL, "null field");
+    if (X || scale) {
+        pd_status rc = upload_norm(s);
+        if (rc) return rc;
+    }
+    features_kernel<<<blocks(s->n, 128), 128, 0, s->ga.stream>>>(s->ga.I, U, s->stat, s->R, s->norm,
+                                                                 reinterpret_cast<__nv_bfloat16*>(X), scale, Xraw, Rs);
+    SCUDA(s, cudaGetLastError());
+    grid_count_launches(s->g, 1);
+    return PD_OK;
+}
+
+pd_status pd_surrogate_targets(pd_surrogate* s, const double* U, double t, const double* Rs, float* y)
+{
+    if (!s) return PD_EINVAL;
+    if (!U || !Rs || !y) return sfail(s, PD_EINVAL, "null argument");
+    pd_status rc = ensure_tables(s, 1);
+    if (rc) return rc;
+    const InstDev& I = s->ga.I;
+    cudaStream_t st = s->ga.stream;
+    SCUDA(s, launch_time_table(I, t, 1.0, 1, s->tabK, st));
+    SCUDA(s, launch_patch_dU(I, s->ga.prec, U, s->tabK, I.K, s->dUf, nullptr, st));
+    targets_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->dUf, Rs, I.K * I.dt, y);
+    SCUDA(s, cudaGetLastError());
+    grid_count_launches(s->g, 3);
+    return PD_OK;
+}
+
+pd_status pd_surrogate_evaluate(pd_surrogate* s, const double* U, double t, double* F_hat, double* F1, double* F)
+{
+    if (!s) return PD_EINVAL;
+    if (!U) return sfail(s, PD_EINVAL, "null field");
+    pd_status rc = ensure_tables(s, 1);
+    if (rc) return rc;
+    const InstDev& I = s->ga.I;
+    cudaStream_t st = s->ga.stream;
+    if (F_hat) {
+        rc = pd_surrogate_features(s, U, s->X, s->scale, nullptr, nullptr);
+        if (rc) return rc;
+        pd_mlp_set_stream(s->m, st);
+        rc = pd_mlp_forward(s->m, s->X, s->n, s->yhat);
+        if (rc) return sfail(s, rc, pd_mlp_last_error(s->m));
+        predict_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->yhat, s->scale, F_hat);
+        SCUDA(s, cudaGetLastError());
+    }
+    if (F1) {
+        SCUDA(s, launch_time_table(s->I1, t, 1.0, 1, s->tab1, st));
+        SCUDA(s, launch_patch_dU(s->I1, s->ga.prec, U, s->tab1, 1, s->dU1, nullptr, st));
+        scale_out_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->dU1, 1.0 / I.dt, F1);
+        SCUDA(s, cudaGetLastError());
+    }
+    if (F) {
+        SCUDA(s, launch_time_table(I, t, 1.0, 1, s->tabK, st));
+        SCUDA(s, launch_patch_dU(I, s->ga.prec, U, s->tabK, I.K, s->dUf, nullptr, st));
+        scale_out_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->dUf, 1.0 / (I.K * I.dt), F);
+        SCUDA(s, cudaGetLastError());
+    }
+    return PD_OK;
+}
+
+pd_status pd_surrogate_step(pd_surrogate* s, double* U, double t0, double dt_macro, int n_macro, double eps)
+{
+    if (!s) return PD_EINVAL;
+    if (!U || n_macro < 0) return sfail(s, PD_EINVAL, "null field or negative step count");
+    if (n_macro == 0) return PD_OK;
+    pd_status rc = upload_norm(s);
+    if (rc) return rc;
+    rc = ensure_tables(s, n_macro);
+    if (rc) return rc;
+    const InstDev& I = s->ga.I;
+    cudaStream_t st = s->ga.stream;
+    const double dtm = dt_macro > 0 ? dt_macro : s->ga.dtm_sugg;
+    const double tau = I.K * I.dt;
+    const int strideK = I.K + kTabExtra, stride1 = 1 + kTabExtra;
+    SCUDA(s, launch_time_table(s->I1, t0, dtm, n_macro, s->tab1, st));
+    SCUDA(s, launch_time_table(I, t0, dtm, n_macro, s->tabK, st));
+    pd_mlp_set_stream(s->m, st);
+    long long nl = 2;
+    for (int k = 0; k < n_macro; ++k) {
+        const double t = t0 + k * dtm;
+        features_kernel<<<blocks(s->n, 128), 128, 0, st>>>(I, U, s->stat, s->R, s->norm,
+                                                           reinterpret_cast<__nv_bfloat16*>(s->X), s->scale, nullptr, nullptr);
+        SCUDA(s, cudaGetLastError());
+        rc = pd_mlp_forward(s->m, s->X, s->n, s->yhat);
+        if (rc) return sfail(s, rc, pd_mlp_last_error(s->m));
+        SCUDA(s, launch_patch_dU(s->I1, s->ga.prec, U, s->tab1 + (size_t)k * stride1, 1, s->dU1, nullptr, st));
+        SCUDA(s, cudaMemsetAsync(s->sumsq, 0, sizeof(double), st));
+        sumsq_kernel<<<304, 256, 0, st>>>(s->n, s->dU1, 1.0 / I.dt, s->sumsq);
+        check_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->yhat, s->scale, s->dU1, s->sumsq, 1.0 / I.dt, tau, eps,
+                                                        s->dUf, s->mask, s->n_fb);
+        SCUDA(s, cudaGetLastError());
+        SCUDA(s, launch_patch_dU(I, s->ga.prec, U, s->tabK + (size_t)k * strideK, I.K, s->dUf, s->mask, st));
+        SCUDA(s, launch_project(I, U, s->dUf, t, dtm, st));
+        nl += 7 + 3 * ((s->n + 65535) / 65536);
+    }
+    grid_count_launches(s->g, nl);
+    s->patch_steps += (long long)s->n * n_macro;
+    return PD_OK;
+}
+
+pd_status pd_surrogate_perturb(pd_surrogate* s, const double* U, double rel_sigma, unsigned long long seed, double* V)
+{
+    if (!s) return PD_EINVAL;
+    if (!U || !V || !(rel_sigma >= 0.0)) return sfail(s, PD_EINVAL, "null field or negative sigma");
+    const InstDev& I = s->ga.I;
+    const long long n = (long long)I.nxp * I.nyp;
+    cudaStream_t st = s->ga.stream;
+    SCUDA(s, cudaMemsetAsync(s->umax, 0, sizeof(unsigned long long), st));
+    maxabs_kernel<<<304, 256, 0, st>>>(n, U, s->umax);
+    perturb_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(I, U, s->umax, rel_sigma, seed, V);
+    SCUDA(s, cudaGetLastError());
+    grid_count_launches(s->g, 2);
+    return PD_OK;
+}
+
+pd_status pd_surrogate_counts(pd_surrogate* s, long long* patch_steps, long long* fallbacks)
+{
+    if (!s) return PD_EINVAL;
+    unsigned long long h = 0;
+    SCUDA(s, cudaMemcpyAsync(&h, s->n_fb, sizeof(h), cudaMemcpyDeviceToHost, s->ga.stream));
+    SCUDA(s, cudaStreamSynchronize(s->ga.stream));
+    if (patch_steps) *patch_steps = s->patch_steps;
+    if (fallbacks) *fallbacks = (long long)h;
+    return PD_OK;
+}
+
+}  // extern "C"

@@ -29,12 +29,29 @@ def _theta(seed=3):
     return S.flatten(p).astype(np.float32)
 
 
+def _rows(X32):
+    """network input rows [n][128]: high BF16 parts, then low parts"""
+    x = torch.tensor(X32)
+    hi = x.to(torch.bfloat16)
+    lo = (x - hi.float()).to(torch.bfloat16)
+    return torch.cat([hi, lo], 1).cuda()
+
+
 def _inputs(n, seed=0):
     rng = np.random.default_rng(seed)
     X = np.zeros((n, S.N_PAD), dtype=np.float32)
     X[:, :S.N_IN] = rng.normal(size=(n, S.N_IN))
-    Xd = torch.tensor(X).to(torch.bfloat16).cuda()
-    return Xd, Xd.float().cpu().numpy().astype(np.float64)
+    return _rows(X), X.astype(np.float64)
+
+
+def _close(y, want):
+    """Device and oracle round at the same points but accumulate in another
+    order, so a hidden activation near a BF16 rounding boundary can round the
+    other way (2^-8 of that activation) and move single rows; the bulk agrees
+    to FP32 accumulation error."""
+    err = np.abs(y - want) / np.abs(want).max()
+    assert np.quantile(err, 0.99) <= 5e-4, np.quantile(err, 0.99)
+    assert err.max() <= 1e-2, err.max()
 
 
 def _slices():
@@ -49,8 +66,7 @@ def test_forward_matches_oracle_ragged_rows(MLP):
     X, Xh = _inputs(1000)
     y = net.forward(X).cpu().numpy()
     want, _ = S.forward(th.astype(np.float64), Xh, round_bf16=True)
-    # same BF16 rounding points; FP32 accumulation order and rare rounding flips remain
-    assert np.abs(y - want).max() <= 1e-3 * np.abs(want).max(), np.abs(y - want).max()
+    _close(y, want)
     exact, _ = S.forward(th.astype(np.float64), Xh)
     assert np.abs(y - exact).max() <= 5e-2 * np.abs(exact).max()
 
@@ -65,7 +81,7 @@ def test_forward_across_inference_chunks(MLP):
     rows = np.unique(np.concatenate([np.arange(0, 300), np.arange(65400, 65700), np.arange(n - 300, n),
                                      np.random.default_rng(2).integers(0, n, 500)]))
     want, _ = S.forward(th.astype(np.float64), Xh[rows], round_bf16=True)
-    assert np.abs(y[rows] - want).max() <= 1e-3 * np.abs(want).max()
+    _close(y[rows], want)
 
 
 @pytest.mark.parametrize("n", [128, 300])
@@ -110,7 +126,7 @@ def test_adam_steps_match_oracle(MLP):
     # the BF16 operand copies follow the master weights
     y = net.forward(X).cpu().numpy()
     want, _ = S.forward(net.params().astype(np.float64), Xh, round_bf16=True)
-    assert np.abs(y - want).max() <= 1e-3 * np.abs(want).max()
+    _close(y, want)
 
 
 def test_fit_norm_and_pack(MLP):
@@ -131,8 +147,10 @@ def test_fit_norm_and_pack(MLP):
     Xp, tp = net.pack(Xd, yd)
     want = (Xr - mu) / sg
     got = Xp.float().cpu().numpy()
-    np.testing.assert_array_equal(got[:, :S.N_IN], S.bf16(want).astype(np.float32))
-    assert np.all(got[:, S.N_IN:] == 0)
+    hi, lo = S.split_input(want)
+    np.testing.assert_array_equal(got[:, :S.N_IN], hi.astype(np.float32))
+    np.testing.assert_array_equal(got[:, S.N_PAD:S.N_PAD + S.N_IN], lo.astype(np.float32))
+    assert np.all(got[:, S.N_IN:S.N_PAD] == 0) and np.all(got[:, S.N_PAD + S.N_IN:] == 0)
     np.testing.assert_array_equal(tp.cpu().numpy(), yr / np.float32(ys))
 
 
@@ -143,7 +161,7 @@ def test_training_reduces_the_loss(MLP):
     t = np.sin(Xr[:, 0]) + 0.5 * Xr[:, 1] * Xr[:, 2] - 0.3 * Xr[:, 3] ** 2 + 0.2 * Xr[:, 4]
     X = np.zeros((n, S.N_PAD), dtype=np.float32)
     X[:, :S.N_IN] = Xr
-    Xd = torch.tensor(X).to(torch.bfloat16).cuda()
+    Xd = _rows(X)
     td = torch.tensor(t.astype(np.float32)).cuda()
     net = MLP(1024)
     net.set_params(S.init_params(11).astype(np.float32))
@@ -152,5 +170,30 @@ def test_training_reduces_the_loss(MLP):
     assert np.all(np.isfinite(hist))
     assert hist[-1] < 0.05 * np.var(t), hist
     # the trained parameters, evaluated by the oracle, fit the data as well
-    yo, _ = S.forward(net.params().astype(np.float64), Xd.float().cpu().numpy().astype(np.float64), round_bf16=True)
+    yo, _ = S.forward(net.params().astype(np.float64), X.astype(np.float64), round_bf16=True)
     assert np.mean((yo - t) ** 2) < 0.05 * np.var(t)
+
+
+def test_device_initialisation(MLP):
+    """fan-in uniform draws from the stated counter-based generator"""
+    net = MLP(128)
+    net.init(1234)
+    th = net.params().astype(np.float64)
+    mask = (1 << 64) - 1
+    def draw(i):
+        z = (1234 + (int(i) + 1) * 0x9E3779B97F4A7C15) & mask
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z ^= z >> 31
+        return (z >> 11) / 2.0 ** 53
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in S.SHAPES])
+    for i in list(range(0, 40)) + [int(offs[1]) + 3, int(offs[2]) + 77, int(offs[6]) + 5, int(offs[7])]:
+        if i < offs[1]:
+            b = 1 / np.sqrt(35) if i % 64 < 35 else 0.0
+        elif i < offs[2]:
+            b = 1 / np.sqrt(35)
+        else:
+            b = 1 / np.sqrt(256)
+        assert abs(th[i] - np.float32((2 * draw(i) - 1) * b)) <= 1e-7, i
+    W1 = S.unflatten(th)["W1"]
+    assert np.all(W1[:, 35:] == 0) and np.abs(W1).max() <= 1 / np.sqrt(35)

@@ -160,6 +160,28 @@ def test_static_features_identity_map_closed_form():
     np.testing.assert_allclose(fs, np.tile(want, (len(fs), 1)), rtol=1e-13, atol=1e-16)
 
 
+def test_metric_features_multiply_the_matching_differences():
+    p = W.c5_surrogate_field(n_r=6, n_theta=12, m=5)
+    o = Oracle(p)
+    U = o.init_field()
+    fs, R = S.static_features(o)
+    X, s, R2 = S.features(o, U)
+    x, s2 = S.stencil_features(S.stencils(o, U))
+    np.testing.assert_array_equal(R, R2)
+    np.testing.assert_array_equal(s, s2)
+    for col, k in ((25, 2), (26, 10), (27, 1), (28, 5)):
+        np.testing.assert_array_equal(X[:, col], fs[:, col - 25] * x[:, k])
+    np.testing.assert_array_equal(X[:, 29:], fs[:, 4:])
+
+
+def test_split_input_carries_sixteen_bits():
+    x = np.random.default_rng(3).normal(size=(200, S.N_PAD)) * 10.0 ** np.random.default_rng(4).uniform(-3, 3, (200, S.N_PAD))
+    hi, lo = S.split_input(x)
+    x32 = x.astype(np.float32).astype(np.float64)
+    assert np.all(S.bf16(hi) == hi) and np.all(S.bf16(lo) == lo)
+    assert np.all(np.abs(hi + lo - x32) <= 2.0 ** -16 * np.abs(x32))
+
+
 def test_static_features_annulus_metric_terms_sum_to_one():
     """beta = phi = 0 on the annulus with v = 0, f = 0, so the four metric
     terms carry the whole rate R."""
