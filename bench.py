@@ -263,9 +263,11 @@ def run_surrogate(args):
     torch.cuda.set_device(0)
     n_macro = 100
     p = W.c5_surrogate_field()
-    # training data from the patch solver: fields at step 0 and step 50, every 8th patch
+    # training data from the patch solver: fields at step 0 and step 50, each also
+    # with 4 grid-scale perturbations (relative size 1e-10..1e-5), every 40th patch
     t0 = time.perf_counter()
     net = MLP(4096)
+    rng = np.random.default_rng(8)
     Xs, ys = [], []
     for sd in range(1000, 1008):
         q = W.c5_surrogate_field(seed=sd)
@@ -274,10 +276,13 @@ def run_surrogate(args):
         U = g.init_field()
         dtm = g.info()["dt_macro_suggested"]
         for k in range(2):
-            f = s.features(U, standardised=False, raw=True)
-            y = s.targets(U, k * 50 * dtm, f["Rs"])
-            Xs.append(f["X_raw"][k::8].contiguous())
-            ys.append(y[k::8].contiguous())
+            for c in range(5):
+                V = U if c == 0 else s.perturb(U, 10.0 ** rng.uniform(-10, -5), int(rng.integers(1 << 62)))
+                f = s.features(V, standardised=False, raw=True)
+                y = s.targets(V, k * 50 * dtm, f["Rs"])
+                o = int(rng.integers(40))
+                Xs.append(f["X_raw"][o::40].contiguous())
+                ys.append(y[o::40].contiguous())
             g.step(U, k * 50 * dtm, dtm, 50)
         del s, g
     Xr, yr = torch.cat(Xs), torch.cat(ys)
@@ -335,6 +340,7 @@ def run_surrogate(args):
         "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
         "config": {"workload": "annulus 512x2048 macro nodes, 9x9 micro, K=20, seeded smooth D, 100 macro steps; "
                                "surrogate 35-256-256-256-1 trained on %d patch-solver samples of 8 other fields" % n_train,
+                   "training_data": "8 seeded fields x 2 times x (clean + 4 perturbed) x every 40th patch",
                    "train_epochs": args.epochs, "train_batch": args.batch, "train_s": train_s, "data_s": data_s,
                    "loss_first_last": [float(hist[0]), float(hist[-1])], "check_eps": 1e-3},
         "macro_steps_per_s": {k: n_macro / v for k, v in res.items()},
@@ -497,8 +503,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
                     help="c2: the benchmark workload (default); c4: the 4096-instance batch; "
                          "c5: the surrogate against the plain scheme on the 512x2048 annulus")
-    ap.add_argument("--epochs", type=int, default=40, help="c5: training epochs")
-    ap.add_argument("--batch", type=int, default=4096, help="c5: training minibatch")
+    ap.add_argument("--epochs", type=int, default=80, help="c5: training epochs")
+    ap.add_argument("--batch", type=int, default=2048, help="c5: training minibatch")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()

@@ -8,6 +8,8 @@
  *
  * Network: 35 -> 256 -> 256 -> 256 -> 1, GELU in its tanh form
  *   g(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))),
+ * (the first two hidden layers evaluate tanh with the hardware approximation,
+ * absolute error of order 2^-11, below their BF16 output rounding),
  * BF16 weights and activations into the tensor cores (tcgen05), FP32
  * accumulation, FP32 master weights and Adam state.  Inputs are padded to 64
  * columns with zeros; a network input row holds 128 BF16 values: the high
@@ -34,7 +36,10 @@
  *
  * Residual check: F1 = restricted change of a one-micro-step burst / dt; the
  * prediction is kept when |F - F1| <= eps (|F1| + rms(F1)), rms over the
- * instance's patches; other patches take the full K-step burst.
+ * instance's patches; other patches take the full K-step burst.  After one
+ * micro step from w = 0 the departure is the forcing, which is linear in the
+ * interpolant's nine coefficients, so F1 is evaluated from a per-patch basis
+ * of ten numbers built once from the burst records.
  *
  * All calls are asynchronous on the object's stream unless stated; errors
  * are pd_status codes, pd_mlp_last_error gives the message.
@@ -116,8 +121,9 @@ const char* pd_mlp_last_error(const pd_mlp* m);
 
 /* ------------------------------------------------------------------------
  * The surrogate on a grid.  Grids of one instance with per-point coefficient
- * records (the default for one instance) and m_xi == m_eta in {3,5,7,9,11}.
- * Work runs on the grid's stream; the network runs there too. */
+ * records (the default for one instance), m_xi == m_eta in {3,5,7,9,11} and
+ * the lifted restriction (the default).  Work runs on the grid's stream; the
+ * network runs there too. */
 typedef struct pd_surrogate pd_surrogate;
 
 /* Allocates the per-patch work buffers (about 190 bytes per patch) and

@@ -322,10 +322,13 @@ pd_status grid_access(pd_grid* g, int inst, GridAccess& out);
 void grid_message(pd_grid* g, const char* msg);
 void grid_count_launches(pd_grid* g, long long n);
 
-// restricted change of every patch (or of the flagged ones) after k_steps micro
-// steps from the lift of U; tab_row is a time-table row built for k_steps
+// restricted change of every patch (or of the *list_n patches of list) after
+// k_steps micro steps from the lift of U; tab_row is a time-table row built
+// for k_steps
 cudaError_t launch_patch_dU(const InstDev& I, int prec, const double* U, const double* tab_row, int k_steps,
-                            double* dU, const unsigned char* mask, cudaStream_t st);
+                            double* dU, const int* list, const int* list_n, cudaStream_t st);
+// per-patch basis T[p][10] of the one-micro-step restricted change over dt
+cudaError_t launch_one_step_basis(const InstDev& I, int prec, double* T, cudaStream_t st);
 // per-patch surrogate features that do not depend on U (10 per patch) and the
 // macro explicit rate R at the patch centre
 cudaError_t launch_surrogate_static(const InstDev& I, const pd_coeff_desc& c, double tau, float* feat, double* R,

@@ -72,14 +72,14 @@ __global__ void burst_record_kernel(const InstDev I, const real* __restrict__ re
 // -> project for one macro step, writing U at T_next into Un.  MODE_BURST: load
 // (w, r) from the micro state, run k_steps, store w.  MODE_DU: lift -> k_steps
 // micro steps -> restrict, writing the restricted change of patch p into
-// dU_out[p]; with a mask only flagged patches are written and warps without a
-// flagged patch return at once.
+// dU_out[p]; with a patch list, warp w takes list entries w P .. w P + P - 1
+// (*list_n entries in all) instead of P neighbouring patches of one row.
 template <int M, bool CROSS, bool TSRC, typename real, int MODE>
 __global__ void __launch_bounds__(128, (sizeof(real) == 4 ? 4 : 1))
 patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __restrict__ Un,
                   const double* __restrict__ tab, double upd_scale, double bias_scale, int k_steps,
                   real* __restrict__ st_w, const real* __restrict__ st_r, int n_item_warps,
-                  double* __restrict__ dU_out, const unsigned char* __restrict__ mask)
+                  double* __restrict__ dU_out, const int* __restrict__ list, const int* __restrict__ list_n)
 {
     constexpr int P = 32 / M;
     constexpr bool LIFT = (MODE != MODE_BURST);
@@ -116,21 +116,28 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
         return;
     }
 
-    const int wpr = (I.ncols + P - 1) / P;
-    const int jr = warp / wpr;
-    const int ic0 = (warp - jr * wpr) * P;
     const int q = lane / M;
     const int a = lane - q * M;
-    const int ic = ic0 + q;
-    const bool active = (q < P) && (ic < I.ncols);
-    const int icl = active ? ic : (I.ncols - 1);
+    int jr, icl;
+    bool active;
+    if (MODE == MODE_DU && list) {
+        const int n_list = *list_n;
+        if (warp * P >= n_list) return;            // whole warp
+        const int e = warp * P + q;
+        active = (q < P) && (e < n_list);
+        const int pid = list[active ? e : warp * P];
+        jr = pid / I.ncols;
+        icl = pid - jr * I.ncols;
+    } else {
+        const int wpr = (I.ncols + P - 1) / P;
+        jr = warp / wpr;
+        const int ic = (warp - jr * wpr) * P + q;
+        active = (q < P) && (ic < I.ncols);
+        icl = active ? ic : (I.ncols - 1);
+    }
     const int i = I.i0 + icl, j = 1 + jr;
     const int qbase = (q < P ? q : P - 1) * M;
     const int pidx = jr * I.ncols + icl;
-    if (MODE == MODE_DU && mask) {
-        const bool need = active && mask[pidx];
-        if (!__any_sync(FULL, need)) return;
-    }
 
     real cv[9];
     double bias = 0.0, u00 = 0.0;
@@ -209,7 +216,7 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
         double inc = fma((double)col, upd_scale, bias * bias_scale);
         if (!isfinite(inc)) atomicOr(I.err, ERR_NONFINITE);
         if (MODE == MODE_DU) {
-            if (!mask || mask[pidx]) dU_out[pidx] = inc;
+            dU_out[pidx] = inc;
         } else {
             long long node = (long long)j * I.nxp + i;
             Un[node] = u00 + inc;
@@ -392,7 +399,7 @@ __global__ void lift_table_kernel(int tkind, double tc, double t, double* tab, d
 template <int M, typename real, int MODE>
 cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const double* tab, double dtm,
                         int k_steps, real* st_w, const real* st_r, cudaStream_t st,
-                        double* dU_out = nullptr, const unsigned char* mask = nullptr)
+                        double* dU_out = nullptr, const int* list = nullptr, const int* list_n = nullptr)
 {
     // dt_macro / tau scales the restricted change; the trapezoid sum also carries 1 / n^2
     // (MODE_DU writes the restricted change itself)
@@ -408,7 +415,7 @@ cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const do
     bool cross = I.has_cross != 0, tsrc = I.has_tsrc != 0;
     int K = (MODE == MODE_FUSED) ? I.K : k_steps;
     size_t smem = tsrc ? sizeof(real) * (size_t)K : 0;
-#define PD_LAUNCH(CR, TS) patch_warp_kernel<M, CR, TS, real, MODE><<<nb, bs, smem, st>>>(I, Uc, Un, tab, upd_scale, bias_scale, k_steps, st_w, st_r, n_item_warps, dU_out, mask)
+#define PD_LAUNCH(CR, TS) patch_warp_kernel<M, CR, TS, real, MODE><<<nb, bs, smem, st>>>(I, Uc, Un, tab, upd_scale, bias_scale, k_steps, st_w, st_r, n_item_warps, dU_out, list, list_n)
     if (cross && tsrc) PD_LAUNCH(true, true);
     else if (cross) PD_LAUNCH(true, false);
     else if (tsrc) PD_LAUNCH(false, true);
@@ -420,14 +427,14 @@ cudaError_t launch_warp(const InstDev& I, const double* Uc, double* Un, const do
 template <typename real, int MODE>
 cudaError_t dispatch_m(const InstDev& I, const double* Uc, double* Un, const double* tab, double dtm,
                        int k_steps, real* st_w, const real* st_r, cudaStream_t st,
-                       double* dU_out = nullptr, const unsigned char* mask = nullptr)
+                       double* dU_out = nullptr, const int* list = nullptr, const int* list_n = nullptr)
 {
     switch (I.mx) {
-    case 3: return launch_warp<3, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
-    case 5: return launch_warp<5, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
-    case 7: return launch_warp<7, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
-    case 9: return launch_warp<9, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
-    case 11: return launch_warp<11, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, mask);
+    case 3: return launch_warp<3, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, list, list_n);
+    case 5: return launch_warp<5, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, list, list_n);
+    case 7: return launch_warp<7, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, list, list_n);
+    case 9: return launch_warp<9, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, list, list_n);
+    case 11: return launch_warp<11, real, MODE>(I, Uc, Un, tab, dtm, k_steps, st_w, st_r, st, dU_out, list, list_n);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -456,11 +463,52 @@ bool fused_supported(const InstDev& I)
 }
 
 cudaError_t launch_patch_dU(const InstDev& I, int prec, const double* U, const double* tab_row, int k_steps,
-                            double* dU, const unsigned char* mask, cudaStream_t st)
+                            double* dU, const int* list, const int* list_n, cudaStream_t st)
 {
     if (prec == PD_FP32)
-        return dispatch_m<float, MODE_DU>(I, U, nullptr, tab_row, 0.0, k_steps, nullptr, nullptr, st, dU, mask);
-    return dispatch_m<double, MODE_DU>(I, U, nullptr, tab_row, 0.0, k_steps, nullptr, nullptr, st, dU, mask);
+        return dispatch_m<float, MODE_DU>(I, U, nullptr, tab_row, 0.0, k_steps, nullptr, nullptr, st, dU, list, list_n);
+    return dispatch_m<double, MODE_DU>(I, U, nullptr, tab_row, 0.0, k_steps, nullptr, nullptr, st, dU, list, list_n);
+}
+
+// Per patch, the trapezoid-weighted sums over its micro points of the burst
+// record's forcing basis B_0..B_8 and of dt G, times 1/(n^2 dt): after one
+// micro step from w = 0 the departure is the forcing, so the restricted
+// change over dt is F1 = sum_k c_k S_k + s(T) S_9 exactly.  The interpolant
+// coefficients are c_k = sum_q lw[k][q] U_q over the 3x3 stencil, so the
+// stored basis is T_q = sum_k S_k lw[k][q] (q = 0..8) and T_9 = S_9:
+// F1 = sum_q T_q U_q + s(T) T_9.
+template <typename real>
+__global__ void one_step_basis_kernel(const InstDev I, const real* __restrict__ brec, double* __restrict__ T)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= I.n_patch) return;
+    const int jr = p / I.ncols, ic = p - jr * I.ncols;
+    const int M = I.mx;
+    double acc[10] = { 0, 0, 0, 0, 0, 0, 0, 0, 0, 0 };
+    for (int b = 0; b < M; ++b) {
+        const double wb = (b == 0 || b == M - 1) ? 0.5 : 1.0;
+        for (int a = 0; a < M; ++a) {
+            const double w = wb * ((a == 0 || a == M - 1) ? 0.5 : 1.0);
+            const real* r = brec + (((long long)(jr * M + b) * I.ncols + ic) * M + a) * 16;
+            for (int k = 0; k < 9; ++k) acc[k] += w * (double)r[7 + k];
+            acc[9] += w * (double)r[6];
+        }
+    }
+    const double f = I.inv_nn / I.dt;
+    for (int q = 0; q < 9; ++q) {
+        double t = 0.0;
+        for (int k = 0; k < 9; ++k) t = fma(acc[k], I.lw[k][q], t);
+        T[(long long)p * 10 + q] = t * f;
+    }
+    T[(long long)p * 10 + 9] = acc[9] * f;
+}
+
+cudaError_t launch_one_step_basis(const InstDev& I, int prec, double* T, cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((I.n_patch + 127) / 128);
+    if (prec == PD_FP32) one_step_basis_kernel<float><<<nb, 128, 0, st>>>(I, static_cast<const float*>(I.brec), T);
+    else one_step_basis_kernel<double><<<nb, 128, 0, st>>>(I, static_cast<const double*>(I.brec), T);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fused_step(const InstDev& I, const InstDev*, int prec, const double* Uc, double* Un,

@@ -25,7 +25,6 @@ constexpr int kWidth = PD_MLP_WIDTH;
 constexpr int kIn = PD_MLP_N_IN;
 constexpr int kPad = PD_MLP_N_PAD;
 constexpr int kInCols = PD_MLP_IN_COLS;      // network input row: 64 high parts, then 64 low parts
-constexpr int kStages = 4;
 constexpr int kBM = 128, kBK = 64;
 constexpr int kErrTimeout = 8;
 
@@ -62,9 +61,9 @@ struct GemmArgs {
     unsigned long long wait_ns;
 };
 
-__host__ __device__ constexpr size_t gemm_smem_bytes(int BN)
+__host__ __device__ constexpr size_t gemm_smem_bytes(int BN, int S)
 {
-    return 1024 + (size_t)kStages * (kBM * kBK * 2 + (size_t)BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
+    return 1024 + (size_t)S * (kBM * kBK * 2 + (size_t)BN * kBK * 2) + (2 * S + 1) * 8 + 16 + kBM * 4;
 }
 
 __device__ __forceinline__ float gelu_f(float x)
@@ -77,6 +76,29 @@ __device__ __forceinline__ float gelu_grad_f(float x)
 {
     const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
     const float t = tanhf(u);
+    return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * x * x);
+}
+
+// Hidden layers (their outputs are rounded to BF16) evaluate tanh with the
+// hardware approximation tanh.approx.f32 (absolute error of order 2^-11, below
+// the BF16 rounding step); the output layer keeps tanhf.
+__device__ __forceinline__ float tanh_fast(float u)
+{
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+    return t;
+}
+
+__device__ __forceinline__ float gelu_fast(float x)
+{
+    const float u = 0.7978845608028654f * fmaf(0.044715f * x, x * x, x);
+    return 0.5f * x * (1.0f + tanh_fast(u));
+}
+
+__device__ __forceinline__ float gelu_grad_fast(float x)
+{
+    const float u = 0.7978845608028654f * fmaf(0.044715f * x, x * x, x);
+    const float t = tanh_fast(u);
     return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * x * x);
 }
 
@@ -98,15 +120,38 @@ __device__ __forceinline__ void store_bf16x32(bf16* dst, const float (&h)[32])
     }
 }
 
-// One 128 x BN output tile per block: warp 0 stages A and B through a
-// kStages-deep TMA ring, warp 1 owns the TMEM accumulator and issues the MMAs
-// from one thread, warps 2..5 drain TMEM (lane quadrant = warp % 4) through
-// the epilogue.  Every wait is bounded; a wait that runs out sets the error
-// flag, lets the other roles finish and frees TMEM.
-template <int BN, int EPI>
-__global__ void __launch_bounds__(192, 1)
+__device__ __forceinline__ void store_bf16x16(bf16* dst, const float (&h)[16])
+{
+    uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(h[8 * q + 0], h[8 * q + 1]);
+        __nv_bfloat162 p1 = __floats2bfloat162_rn(h[8 * q + 2], h[8 * q + 3]);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(h[8 * q + 4], h[8 * q + 5]);
+        __nv_bfloat162 p3 = __floats2bfloat162_rn(h[8 * q + 6], h[8 * q + 7]);
+        uint4 v;
+        v.x = *reinterpret_cast<uint32_t*>(&p0);
+        v.y = *reinterpret_cast<uint32_t*>(&p1);
+        v.z = *reinterpret_cast<uint32_t*>(&p2);
+        v.w = *reinterpret_cast<uint32_t*>(&p3);
+        d[q] = v;
+    }
+}
+
+constexpr int kEpiWarps = 4;                  // one per TMEM lane quadrant
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
+
+// One 128 x BN output tile per block: warp 0 stages A and B through an
+// S-deep TMA ring, warp 1 owns the TMEM accumulator and issues the MMAs from
+// one thread, warps 2..5 drain TMEM through the epilogue (lane quadrant =
+// warp % 4).  With S = 2 two blocks fit on an SM, so one block's epilogue
+// overlaps the other's loads and MMAs.  Every wait is bounded; a wait that
+// runs out sets the error flag, lets the other roles finish and frees TMEM.
+template <int BN, int EPI, int S>
+__global__ void __launch_bounds__(kGemmThreads, (S <= 2 ? 2 : 1))
 gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a)
 {
+    constexpr int kStages = S;
     using namespace tc;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -116,6 +161,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * B_BYTES);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    float* ydot_s = reinterpret_cast<float*>(tslot + 4);       // EPI_DOT: per-row partial sums [128]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
@@ -133,6 +179,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         *abort_flag = 0;
         mbar_fence_init();
     }
+    if (EPI == EPI_DOT && threadIdx.x < kBM) ydot_s[threadIdx.x] = 0.0f;
     if (warp == 1) tmem_alloc(smem_u32(tslot), BN);
     tc_fence_before();
     __syncthreads();
@@ -184,7 +231,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     } else {
         const int quad = warp & 3;
-        const int row = m0 + quad * 32 + lane;
+        const int half = (warp - 2) >> 2;            // 0: one warp per quadrant covers every column
+        const int rl = quad * 32 + lane;
+        const int row = m0 + rl;
         int ok = 1;
         if (lane == 0) {
             ok = mbar_wait(accf, 0, a.wait_ns) ? 1 : 0;
@@ -195,18 +244,20 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const bool live = ok && !*abort_flag;
         const bool in = live && row < a.M;
         const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
+        constexpr int CW = BN / (kEpiWarps / 4);    // columns of this warp
         float ydot = 0.0f;
         if (live) {
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                float v[32];
-                tmem_ld32(tbase + c * 32, v);
+            for (int c = 0; c < CW / 16; ++c) {
+                const int col = half * CW + c * 16;
+                float v[16];
+                tmem_ld16(tbase + col, v);
                 if (!in) continue;
-                const int nb = n0 + c * 32;
+                const int nb = n0 + col;
                 if (EPI == EPI_F32) {
                     float* o = a.out_f32 + (size_t)row * a.ldo + nb;
 #pragma unroll
-                    for (int k = 0; k < 32; k += 4) {
+                    for (int k = 0; k < 16; k += 4) {
                         float4 q = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
                         if (a.bias) { q.x += a.bias[nb + k]; q.y += a.bias[nb + k + 1]; q.z += a.bias[nb + k + 2]; q.w += a.bias[nb + k + 3]; }
                         *reinterpret_cast<float4*>(o + k) = q;
@@ -214,41 +265,46 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 } else if (EPI == EPI_F32_ATOMIC) {
                     float* o = a.out_f32 + (size_t)row * a.ldo + nb;
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) atomicAdd(o + k, v[k]);
+                    for (int k = 0; k < 16; ++k) atomicAdd(o + k, v[k]);
                 } else if (EPI == EPI_GELU) {
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) v[k] += a.bias[nb + k];
+                    for (int k = 0; k < 16; ++k) v[k] += a.bias[nb + k];
                     if (a.out_z) {
                         float* o = a.out_z + (size_t)row * a.ldo + nb;
 #pragma unroll
-                        for (int k = 0; k < 32; k += 4) *reinterpret_cast<float4*>(o + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                        for (int k = 0; k < 16; k += 4) *reinterpret_cast<float4*>(o + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
                     }
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) v[k] = gelu_f(v[k]);
-                    if (a.out_bf16) store_bf16x32(a.out_bf16 + (size_t)row * a.ldo + nb, v);
+                    for (int k = 0; k < 16; ++k) v[k] = gelu_fast(v[k]);
+                    if (a.out_bf16) store_bf16x16(a.out_bf16 + (size_t)row * a.ldo + nb, v);
                     if (a.out_bf16_t) {
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) a.out_bf16_t[(size_t)(nb + k) * a.ldt + row] = __float2bfloat16_rn(v[k]);
+                        for (int k = 0; k < 16; ++k) a.out_bf16_t[(size_t)(nb + k) * a.ldt + row] = __float2bfloat16_rn(v[k]);
                     }
                 } else if (EPI == EPI_GELU_BWD) {
                     const float* z = a.aux + (size_t)row * a.ldo + nb;
 #pragma unroll
-                    for (int k = 0; k < 32; k += 4) {
+                    for (int k = 0; k < 16; k += 4) {
                         const float4 q = *reinterpret_cast<const float4*>(z + k);
-                        v[k] *= gelu_grad_f(q.x);
-                        v[k + 1] *= gelu_grad_f(q.y);
-                        v[k + 2] *= gelu_grad_f(q.z);
-                        v[k + 3] *= gelu_grad_f(q.w);
+                        v[k] *= gelu_grad_fast(q.x);
+                        v[k + 1] *= gelu_grad_fast(q.y);
+                        v[k + 2] *= gelu_grad_fast(q.z);
+                        v[k + 3] *= gelu_grad_fast(q.w);
                     }
-                    store_bf16x32(a.out_bf16 + (size_t)row * a.ldo + nb, v);
+                    store_bf16x16(a.out_bf16 + (size_t)row * a.ldo + nb, v);
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) a.out_bf16_t[(size_t)(nb + k) * a.ldt + row] = __float2bfloat16_rn(v[k]);
+                    for (int k = 0; k < 16; ++k) a.out_bf16_t[(size_t)(nb + k) * a.ldt + row] = __float2bfloat16_rn(v[k]);
                 } else {   // EPI_DOT
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) ydot = fmaf(gelu_f(v[k] + a.bias[nb + k]), a.w_dot[nb + k], ydot);
+                    for (int k = 0; k < 16; ++k) ydot = fmaf(gelu_f(v[k] + a.bias[nb + k]), a.w_dot[nb + k], ydot);
                 }
             }
-            if (EPI == EPI_DOT && in) a.out_dot[row] = ydot + *a.b_dot;
+            // column groups of a row meet in shared memory (one group: a plain store)
+            if (EPI == EPI_DOT && in) atomicAdd(&ydot_s[rl], ydot);
+        }
+        if (EPI == EPI_DOT) {
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+            if (half == 0 && in) a.out_dot[row] = ydot_s[rl] + *a.b_dot;
         }
     }
     tc_fence_before();
@@ -513,18 +569,20 @@ __global__ void lr_kernel(float* lr, long long s, long long total, float lr_max)
     *lr = v;
 }
 
-template <int BN, int EPI>
+// S = 2 for the short products (K <= 256: every forward and input-gradient
+// GEMM), S = 4 for the weight gradients whose K is the minibatch
+template <int BN, int EPI, int S = 2>
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& a, int splits, cudaStream_t st)
 {
     static bool attr = false;
-    const size_t smem = gemm_smem_bytes(BN);
+    const size_t smem = gemm_smem_bytes(BN, S);
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, EPI, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((a.M + kBM - 1) / kBM, a.N / BN, splits);
-    gemm_kernel<BN, EPI><<<grid, 192, smem, st>>>(ta, tb, a);
+    gemm_kernel<BN, EPI, S><<<grid, kGemmThreads, smem, st>>>(ta, tb, a);
     return cudaGetLastError();
 }
 
@@ -671,7 +729,7 @@ pd_status fwd_bwd(pd_mlp* m, int B, int n_valid)
     {   // dW3 = dZ3^T H2
         GemmArgs a = base_args(m, kWidth, kWidth, B);
         a.ldo = kWidth; a.out_f32 = m->grad + OFF_W3; a.chunks_per_split = per;
-        MCUDA(m, (launch_gemm<256, EPI_F32_ATOMIC>(m->mp.dZ3t, m->mp.H2t, a, splits, st)));
+        MCUDA(m, (launch_gemm<256, EPI_F32_ATOMIC, 4>(m->mp.dZ3t, m->mp.H2t, a, splits, st)));
     }
     {   // dZ2 = (dZ3 W3) g'(Z2)
         GemmArgs a = base_args(m, B, kWidth, kWidth);
@@ -681,7 +739,7 @@ pd_status fwd_bwd(pd_mlp* m, int B, int n_valid)
     {   // dW2 = dZ2^T H1
         GemmArgs a = base_args(m, kWidth, kWidth, B);
         a.ldo = kWidth; a.out_f32 = m->grad + OFF_W2; a.chunks_per_split = per;
-        MCUDA(m, (launch_gemm<256, EPI_F32_ATOMIC>(m->mp.dZ2t, m->mp.H1t, a, splits, st)));
+        MCUDA(m, (launch_gemm<256, EPI_F32_ATOMIC, 4>(m->mp.dZ2t, m->mp.H1t, a, splits, st)));
     }
     {   // dZ1 = (dZ2 W2) g'(Z1)
         GemmArgs a = base_args(m, B, kWidth, kWidth);
@@ -691,7 +749,7 @@ pd_status fwd_bwd(pd_mlp* m, int B, int n_valid)
     {   // dW1 = dZ1^T X
         GemmArgs a = base_args(m, kWidth, kPad, B);
         a.ldo = kPad; a.out_f32 = m->grad + OFF_W1; a.chunks_per_split = per;
-        MCUDA(m, (launch_gemm<64, EPI_F32_ATOMIC>(m->mp.dZ1t, m->mp.Xbt, a, splits, st)));
+        MCUDA(m, (launch_gemm<64, EPI_F32_ATOMIC, 4>(m->mp.dZ1t, m->mp.Xbt, a, splits, st)));
     }
     bias_grad_kernel<<<dim3(kWidth, 3), 256, 0, st>>>(m->dZ1t, m->dZ2t, m->dZ3t, B, m->cap, m->grad);
     MCUDA(m, cudaGetLastError());

