@@ -239,7 +239,7 @@ pd_status pd_set_coeff_storage(pd_grid* g, int mode);
 /* Batched execution (grids with several instances, or table storage): one
  * kernel per macro step over all instances, warps pulling patch groups from a
  * device work queue (costliest micro size first).  The autotuner times
- * n_trial_steps macro steps of each candidate (64/128/256 threads per block x
+ * n_trial_steps macro steps of each candidate (64/128 threads per block x
  * full/half patches per warp) on scratch fields and keeps the fastest; it runs
  * on the first batched pd_step unless disabled with pd_set_autotune(g, 0, ...),
  * which fixes the configuration instead. */

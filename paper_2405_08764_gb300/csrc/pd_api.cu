@@ -35,6 +35,8 @@ struct Inst {
     std::vector<int2> bnd_host;
     double* col_tab = nullptr;       // table coefficient mode
     double* row_tab = nullptr;
+    float* col_tab_f = nullptr;      // FP32 copies
+    float* row_tab_f = nullptr;
     int* bnd_off = nullptr;          // boundary nodes owned by each item warp (persistent kernel)
     int* bnd_idx = nullptr;
     int n_item = 0;
@@ -553,7 +555,7 @@ pd_status batch_autotune(pd_grid* g, int n_trial)
     int best_block = g->bt_block;
     bool best_half = g->bt_half;
     g->tune_log.clear();
-    const int blocks[3] = { 64, 128, 256 };
+    const int blocks[2] = { 64, 128 };
     for (int hv = 0; hv < 2; ++hv) {
         g->bt_half = hv != 0;
         g->batch_dirty = true;
@@ -561,7 +563,7 @@ pd_status batch_autotune(pd_grid* g, int n_trial)
         if (rc) break;
         bool tables = batch_needs_tables(g);
         if (tables) { rc = batch_time_tables(g, 0.0, n_trial, dtm); if (rc) break; }
-        for (int bi = 0; bi < 3; ++bi) {
+        for (int bi = 0; bi < 2; ++bi) {
             g->bt_block = blocks[bi];
             int nl = 0;
             rc = enqueue_batch(g, trial, 1, g->stream, nl, tables);   // warm-up
@@ -754,7 +756,7 @@ pd_status pd_destroy_grid(pd_grid* g)
     for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
     for (auto& pr : g->tev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto e : g->tfree) cudaEventDestroy(e);
-    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.col_tab); cudaFree(s.row_tab); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
+    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.col_tab); cudaFree(s.row_tab); cudaFree(s.col_tab_f); cudaFree(s.row_tab_f); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
     cudaFree(g->err); cudaFree(g->acc); cudaFree(g->U_scratch); cudaFree(g->tab);
     cudaFree(g->state); cudaFree(g->dU); cudaFree(g->flags);
     cudaFree(g->insts_dev); cudaFree(g->items_dev); cudaFree(g->dtm_dev); cudaFree(g->tab_off_dev); cudaFree(g->counters);
@@ -808,7 +810,10 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
         s.I.coef_mode = s.d.map == PD_MAP_POLAR ? COEF_POLAR : COEF_SEPARABLE;
         if (!s.col_tab) PD_CUDA(g, cudaMalloc(&s.col_tab, sizeof(double) * 2 * (size_t)s.I.ncols * s.I.mx));
         if (!s.row_tab) PD_CUDA(g, cudaMalloc(&s.row_tab, sizeof(double) * 4 * (size_t)s.I.nrows * s.I.my));
+        if (!s.col_tab_f) PD_CUDA(g, cudaMalloc(&s.col_tab_f, sizeof(float) * 2 * (size_t)s.I.ncols * s.I.mx));
+        if (!s.row_tab_f) PD_CUDA(g, cudaMalloc(&s.row_tab_f, sizeof(float) * 4 * (size_t)s.I.nrows * s.I.my));
         s.I.col_tab = s.col_tab; s.I.row_tab = s.row_tab;
+        s.I.col_tab_f = s.col_tab_f; s.I.row_tab_f = s.row_tab_f;
         s.I.K11 = c->d0 * c->M11; s.I.K12 = c->d0 * c->M12; s.I.K22 = c->d0 * c->M22;
         s.I.v1 = c->va[0]; s.I.v2 = c->vb[0]; s.I.f0 = c->f0;
         cudaFree(s.rec); cudaFree(s.brec);
@@ -829,7 +834,7 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     PD_CUDA(g, launch_precompute(s.I, *c, s.amp, s.rec, s.d.prec, g->acc, g->acc + 1, g->stream));
     g->launches += 3;
     if (use_tables) {
-        PD_CUDA(g, launch_tables(s.I, s.col_tab, s.row_tab, nullptr, nullptr, g->stream));
+        PD_CUDA(g, launch_tables(s.I, s.col_tab, s.row_tab, s.col_tab_f, s.row_tab_f, nullptr, nullptr, g->stream));
         g->launches += 1;
     }
     unsigned long long h[2];
@@ -1088,7 +1093,7 @@ pd_status pd_autotune(pd_grid* g, int n_trial_steps, int* block, int* half_patch
 pd_status pd_set_autotune(pd_grid* g, int enabled, int block, int half_patches)
 {
     if (!g) return PD_EINVAL;
-    if (block != 64 && block != 128 && block != 256) return fail(g, PD_EINVAL, "block must be 64, 128 or 256");
+    if (block != 64 && block != 128) return fail(g, PD_EINVAL, "block must be 64 or 128");
     g->autotune = enabled != 0;
     g->bt_block = block;
     g->bt_half = half_patches != 0;

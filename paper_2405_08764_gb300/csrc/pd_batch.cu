@@ -45,8 +45,9 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     const double* trow = (A.tab && (TSRC || I.sol != PD_SOL_NONE)) ? A.tab + A.tab_off[it.inst] + (long long)A.step * (I.K + kTabExtra) : nullptr;
     const real sT = (TSRC && trow) ? (real)trow[I.K] : real(0);
 
+    const RealConsts<real> kc = real_consts<real>(I);
     PatchGeo<real> g;
-    g.hx = (real)I.hx; g.hy = (real)I.hy; g.dx = (real)I.dx; g.dy = (real)I.dy;
+    g.hx = (real)I.hx; g.hy = (real)I.hy; g.dx = kc.dx; g.dy = kc.dy;
     g.nx = M - 1; g.ny = M - 1;
     const real dt = (real)I.dt;
     const real* rec = static_cast<const real*>(I.rec);
@@ -58,13 +59,13 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     for (int b = 0; b < M; ++b) {
         real co[6], G = real(0);
         if (I.coef_mode != COEF_RECORDS) {
-            table_coeffs<real>(I, icl, a, jr, b, co);
+            table_coeffs_k<real>(I, kc, icl, a, jr, b, co);
         } else {
             const real* pr = rec + (base + b * rowstride) * 8;
             for (int k = 0; k < 6; ++k) co[k] = pr[k];
             G = pr[6];
         }
-        PointW<real> pw = point_weights_fast<real>(I, co[0], co[1], co[2], co[3], co[4], co[5]);
+        PointW<real> pw = point_weights_k<real>(I, kc, co[0], co[1], co[2], co[3], co[4], co[5]);
         real r = burst_forcing<real>(c, g, a, b, co[0], co[1], co[2], co[3], co[4], co[5], G, sT, pw);
         real e = dt * pw.wE, ww = dt * pw.wW, n = dt * pw.wN, s = dt * pw.wS, x = dt * pw.wX;
         real cc = real(1) + dt * pw.wC;
@@ -117,8 +118,9 @@ __device__ __forceinline__ void boundary_item(const InstDev& I, const BatchItem&
     Un[(long long)ij.y * I.nxp + ij.x] = v;
 }
 
+// at most 128 threads per block and 170 registers per thread: three blocks per SM
 template <bool TSRC, typename real>
-__global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A)
+__global__ void __launch_bounds__(128, 3) batch_kernel(const BatchArgs A)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {

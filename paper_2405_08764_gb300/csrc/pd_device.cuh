@@ -68,28 +68,28 @@ __device__ __forceinline__ void burst_steps(real (&w)[M], const real (&cE)[M], c
 }
 
 // Monomial coefficients of the patch's interpolant from the FP64 macro field,
-// one coefficient per lane (lanes qbase + k, k < 9), in two FP64 phases:
-//   phase 1: lane s forms difference s of the 3x3 stencil (three loads, one
-//            add and one fma);
-//   phase 2: lane k combines up to three differences (two fma, one multiply).
-// Micro sizes below 9 use the 9-term dot product with the weights lw.
-// Returns this lane's FP64 coefficient (k = a) and broadcasts the FP32/FP64
-// copies cv[0..8].
+// in two FP64 phases:
+//   phase 1: slot s (0..8) is one difference of the 3x3 stencil (three loads,
+//            one add and one fma); lane a of a patch forms slots a, a + M, ...;
+//   phase 2: coefficient k combines up to three slots (two fma, one multiply),
+//            gathered by shuffles from the lanes that formed them.
+// Broadcasts the FP32/FP64 copies cv[0..8] to every lane of the patch.
 template <int M, typename real, bool L2LOAD>
 __device__ __forceinline__ void macro_coeffs(const InstDev& I, const double* __restrict__ Uc, int i, int j, int a,
                                              int qbase, const double (*lw)[9], const int (*slot)[3],
                                              const double (*cw)[3], real cv[9], double& c20, double& c02,
                                              double& u00)
 {
+    (void)lw;
     auto ld = [&](int di, int dj) -> double {
         const double* p = Uc + (long long)(j + dj) * I.nxp + wrap_col(I, i + di);
         return L2LOAD ? __ldcg(p) : __ldg(p);
     };
-    if constexpr (M >= 9) {
+    auto slot_value = [&](int k) -> double {
         int ai = 0, aj = 0, bi = 0, bj = 0, ci = 0, cj = 0;
         double wB = 0.0;
         bool neg = false, zeroC = false;
-        switch (a) {
+        switch (k) {
         case 0: ai = -1; aj = -1; bi = 0; bj = -1; ci = 1; cj = -1; wB = -2.0; break;
         case 1: ai = -1; aj = 0;  bi = 0; bj = 0;  ci = 1; cj = 0;  wB = -2.0; break;
         case 2: ai = -1; aj = 1;  bi = 0; bj = 1;  ci = 1; cj = 1;  wB = -2.0; break;
@@ -103,7 +103,10 @@ __device__ __forceinline__ void macro_coeffs(const InstDev& I, const double* __r
         double A = ld(ai, aj), B = ld(bi, bj), Cv = ld(ci, cj);
         if (neg) Cv = -Cv;
         if (zeroC) Cv = 0.0;
-        double x1 = fma(wB, B, A + Cv);
+        return fma(wB, B, A + Cv);
+    };
+    if constexpr (M >= 9) {
+        double x1 = slot_value(a < 9 ? a : 8);
         int k = a < 9 ? a : 8;
         double P = __shfl_sync(kFull, x1, (qbase + slot[k][0]) & 31);
         double Q = __shfl_sync(kFull, x1, (qbase + slot[k][1]) & 31);
@@ -117,29 +120,34 @@ __device__ __forceinline__ void macro_coeffs(const InstDev& I, const double* __r
         u00 = __shfl_sync(kFull, x1, (qbase + 8) & 31);
     } else {
         constexpr int NC = (9 + M - 1) / M;
-        double stv[9];
+        double x1[NC];
 #pragma unroll
-        for (int pp = -1; pp <= 1; ++pp)
+        for (int r = 0; r < NC; ++r) x1[r] = slot_value(min(a + r * M, 8));
+        // slot s lives in register s / M of lane qbase + s % M
+        auto gather = [&](int s) -> double {
+            const int ln = (qbase + s % M) & 31;
+            double v = __shfl_sync(kFull, x1[0], ln);
 #pragma unroll
-            for (int qq = -1; qq <= 1; ++qq) stv[(pp + 1) * 3 + (qq + 1)] = ld(pp, qq);
+            for (int rr = 1; rr < NC; ++rr) {
+                const double w = __shfl_sync(kFull, x1[rr], ln);
+                if (s / M == rr) v = w;
+            }
+            return v;
+        };
         double ck[NC];
         real ckr[NC];
 #pragma unroll
         for (int r = 0; r < NC; ++r) {
-            int k = a + r * M;
-            double acc = 0.0;
-            if (k < 9) {
-#pragma unroll
-                for (int jj = 0; jj < 9; ++jj) acc = fma(lw[k][jj], stv[jj], acc);
-            }
-            ck[r] = acc;
-            ckr[r] = (real)acc;
+            const int k = min(a + r * M, 8);
+            const double P = gather(slot[k][0]), Q = gather(slot[k][1]), R = gather(slot[k][2]);
+            ck[r] = fma(cw[k][1], R, fma(cw[k][0], Q, P)) * cw[k][2];
+            ckr[r] = (real)ck[r];
         }
 #pragma unroll
         for (int kk = 0; kk < 9; ++kk) cv[kk] = __shfl_sync(kFull, ckr[kk / M], (qbase + kk % M) & 31);
         c20 = __shfl_sync(kFull, ck[3 / M], (qbase + 3 % M) & 31);
         c02 = __shfl_sync(kFull, ck[5 / M], (qbase + 5 % M) & 31);
-        u00 = stv[4];
+        u00 = gather(8);
     }
 }
 

@@ -55,6 +55,8 @@ struct InstDev {
     int coef_mode;
     const double* col_tab;       // [ncols][mx][2]
     const double* row_tab;       // [nrows][my][4]
+    const float* col_tab_f;      // FP32 copies for the FP32 batched path
+    const float* row_tab_f;
     double K11, K12, K22, v1, v2, f0;
     // reciprocals of the nano steps (division-free stencil weights)
     double inv_dx, inv_dy, inv_dx2, inv_dy2, inv_4dxdy;
@@ -180,6 +182,85 @@ __device__ __forceinline__ PointW<real> point_weights(real al, real be, real ga,
         else              { w.wE = ax - nu / dx; w.wW = ax; w.wC += nu / dx; w.ox = real(0.5) * dx; }
         if (om > real(0)) { w.wS = gy + om / dy; w.wN = gy; w.wC -= om / dy; w.oy = real(-0.5) * dy; }
         else              { w.wN = gy - om / dy; w.wS = gy; w.wC += om / dy; w.oy = real(0.5) * dy; }
+    }
+    return w;
+}
+
+// The instance constants in the working precision, converted once per patch
+// group: a double -> float conversion issues on the FP64 pipe, which on this
+// part runs at a small fraction of the FP32 rate.
+template <typename real>
+struct RealConsts {
+    real K11, K12, K22, v1, v2, f0;
+    real idx, idy, idx2, idy2, i4dxdy, dx, dy;
+    const real* col;             // 1-D metric tables in the working precision
+    const real* row;
+};
+
+template <typename real>
+__device__ __forceinline__ RealConsts<real> real_consts(const InstDev& I)
+{
+    RealConsts<real> k;
+    k.K11 = (real)I.K11; k.K12 = (real)I.K12; k.K22 = (real)I.K22;
+    k.v1 = (real)I.v1; k.v2 = (real)I.v2; k.f0 = (real)I.f0;
+    k.idx = (real)I.inv_dx; k.idy = (real)I.inv_dy; k.idx2 = (real)I.inv_dx2; k.idy2 = (real)I.inv_dy2;
+    k.i4dxdy = (real)I.inv_4dxdy; k.dx = (real)I.dx; k.dy = (real)I.dy;
+    if constexpr (sizeof(real) == 4) { k.col = I.col_tab_f; k.row = I.row_tab_f; }
+    else { k.col = I.col_tab; k.row = I.row_tab; }
+    return k;
+}
+
+// table_coeffs with the constants and tables already in the working precision
+template <typename real>
+__device__ __forceinline__ void table_coeffs_k(const InstDev& I, const RealConsts<real>& k, int ic, int a, int jr, int b,
+                                               real c[6])
+{
+    const real* ct = k.col + ((size_t)ic * I.mx + a) * 2;
+    const real* rt = k.row + ((size_t)jr * I.my + b) * 4;
+    if (I.coef_mode == COEF_SEPARABLE) {
+        const real ia = ct[0], ia2 = ct[1], ib = rt[0], ib2 = rt[1];
+        c[0] = k.K11 * ia * ia;
+        c[1] = real(2) * k.K12 * ia * ib;
+        c[2] = k.K22 * ib * ib;
+        c[3] = k.v1 * ia + k.K11 * ia2;
+        c[4] = k.v2 * ib + k.K22 * ib2;
+    } else {
+        const real s = ct[0], co = ct[1];
+        const real iR = rt[0], iRp = rt[1], q = rt[2];
+        const real ss = s * s, cc = co * co, sc = s * co;
+        const real A = ss * k.K11 - real(2) * sc * k.K12 + cc * k.K22;
+        const real B = sc * (k.K22 - k.K11) + (cc - ss) * k.K12;
+        const real C = cc * k.K11 + real(2) * sc * k.K12 + ss * k.K22;
+        const real Bp = (cc - ss) * (k.K22 - k.K11) - real(4) * sc * k.K12;
+        c[0] = A * iR * iR;
+        c[1] = real(2) * B * iR * iRp;
+        c[2] = C * iRp * iRp;
+        c[3] = (-s * k.v1 + co * k.v2) * iR + real(2) * B * iR * iR;
+        c[4] = (co * k.v1 + s * k.v2) * iRp - (Bp + C * (real(1) - q)) * iR * iRp;
+    }
+    c[5] = k.f0;
+}
+
+// point_weights_fast with the constants already in the working precision
+template <typename real>
+__device__ __forceinline__ PointW<real> point_weights_k(const InstDev& I, const RealConsts<real>& k, real al, real be,
+                                                        real ga, real nu, real om, real ph)
+{
+    PointW<real> w;
+    real ax = al * k.idx2, gy = ga * k.idy2;
+    w.wX = be * k.i4dxdy;
+    w.wC = -real(2) * ax - real(2) * gy + ph;
+    if (I.conv == PD_CONV_CENTRAL) {
+        real hn = real(0.5) * nu * k.idx, ho = real(0.5) * om * k.idy;
+        w.wE = ax - hn; w.wW = ax + hn;
+        w.wN = gy - ho; w.wS = gy + ho;
+        w.ox = real(0); w.oy = real(0);
+    } else {
+        real nx = nu * k.idx, oy = om * k.idy;
+        if (nu > real(0)) { w.wW = ax + nx; w.wE = ax; w.wC -= nx; w.ox = real(-0.5) * k.dx; }
+        else              { w.wE = ax - nx; w.wW = ax; w.wC += nx; w.ox = real(0.5) * k.dx; }
+        if (om > real(0)) { w.wS = gy + oy; w.wN = gy; w.wC -= oy; w.oy = real(-0.5) * k.dy; }
+        else              { w.wN = gy - oy; w.wS = gy; w.wC += oy; w.oy = real(0.5) * k.dy; }
     }
     return w;
 }
@@ -349,7 +430,7 @@ struct PersistArgs {
     int silent_warp;       // test hook: this item warp never publishes (-1: none)
 };
 // 1-D metric tables (table coefficient mode) and batched execution
-cudaError_t launch_tables(const InstDev& I, double* col_tab, double* row_tab, unsigned long long* rate_max,
+cudaError_t launch_tables(const InstDev& I, double* col_tab, double* row_tab, float* col_tab_f, float* row_tab_f, unsigned long long* rate_max,
                           unsigned long long* macro_rate_max, cudaStream_t st);
 cudaError_t launch_table_get_coeffs(const InstDev& I, double* out, cudaStream_t st);
 struct BatchItem {

@@ -362,8 +362,8 @@ __global__ void init_field_kernel(const InstDev I, const CoefDev C, const InitPa
     U[k] = v;
 }
 
-// 1-D metric tables of the table coefficient mode (FP64)
-__global__ void table_build_kernel(const InstDev I, double* col_tab, double* row_tab)
+// 1-D metric tables of the table coefficient mode (FP64, plus FP32 copies)
+__global__ void table_build_kernel(const InstDev I, double* col_tab, double* row_tab, float* col_f, float* row_f)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int ncol = I.ncols * I.mx, nrow = I.nrows * I.my;
@@ -380,6 +380,7 @@ __global__ void table_build_kernel(const InstDev I, double* col_tab, double* row
             double ia = 1.0 / m.x_a;
             o[0] = ia; o[1] = m.x_aa * ia * ia * ia;
         }
+        if (col_f) { col_f[(size_t)t * 2] = (float)o[0]; col_f[(size_t)t * 2 + 1] = (float)o[1]; }
     } else if (t < ncol + nrow) {
         int u = t - ncol;
         int jr = u / I.my, b = u % I.my;
@@ -394,6 +395,8 @@ __global__ void table_build_kernel(const InstDev I, double* col_tab, double* row
             double ib = 1.0 / m.y_b;
             o[0] = ib; o[1] = m.y_bb * ib * ib * ib; o[2] = 0.0; o[3] = 0.0;
         }
+        if (row_f)
+            for (int k = 0; k < 4; ++k) row_f[(size_t)u * 4 + k] = (float)o[k];
     }
 }
 
@@ -532,12 +535,12 @@ cudaError_t launch_precompute(const InstDev& I, const pd_coeff_desc& c, const do
     return cudaGetLastError();
 }
 
-cudaError_t launch_tables(const InstDev& I, double* col_tab, double* row_tab, unsigned long long* rate_max,
-                          unsigned long long* macro_rate_max, cudaStream_t st)
+cudaError_t launch_tables(const InstDev& I, double* col_tab, double* row_tab, float* col_tab_f, float* row_tab_f,
+                          unsigned long long* rate_max, unsigned long long* macro_rate_max, cudaStream_t st)
 {
     (void)rate_max; (void)macro_rate_max;
     int n = I.ncols * I.mx + I.nrows * I.my;
-    table_build_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, col_tab, row_tab);
+    table_build_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, col_tab, row_tab, col_tab_f, row_tab_f);
     return cudaGetLastError();
 }
 
