@@ -49,9 +49,11 @@ def peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         d = json.load(open(path))
-        p.update(hbm_gbs=d.get("hbm_gbs"), sm_max_mhz=d.get("sm_max_mhz", 2070.0), source="measured")
+        p.update(hbm_gbs=d.get("hbm_gbs"), sm_max_mhz=d.get("sm_max_mhz", 2070.0), source="measured",
+                 bf16_tflops=d.get("bf16_tflops", 1900.0))
     else:
         p["hbm_gbs"] = 6800.0
+        p["bf16_tflops"] = 1900.0
     # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop per clock at the maximum SM clock
     p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
     return p
@@ -267,7 +269,8 @@ def run_surrogate(args):
 
     torch.cuda.set_device(0)
     n_macro = 100
-    p = W.c5_surrogate_field()
+    n_r, n_theta = (int(v) for v in args.c5_grid.split("x"))
+    p = W.c5_surrogate_field(n_r=n_r, n_theta=n_theta)
     # training data from the patch solver: fields at step 0 and step 50, each also
     # with 4 grid-scale perturbations (relative size 1e-10..1e-5), every 40th patch
     t0 = time.perf_counter()
@@ -275,7 +278,7 @@ def run_surrogate(args):
     rng = np.random.default_rng(8)
     Xs, ys = [], []
     for sd in range(1000, 1008):
-        q = W.c5_surrogate_field(seed=sd)
+        q = W.c5_surrogate_field(n_r=n_r, n_theta=n_theta, seed=sd)
         g = Grid(q, prec="fp32")
         s = Surrogate(g, net)
         U = g.init_field()
@@ -330,11 +333,22 @@ def run_surrogate(args):
     st0, fb0 = s.counts()
     sampler = ClockSampler(0)
     sampler.start()
+    torch.cuda.nvtx.range_push("surrogate_steps")
     res["surrogate"] = timed(lambda: s.step(U, 0.0, dtm, n_macro, eps=1e-3))
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     g.sync()
     st1, fb1 = s.counts()
     fields["surrogate"] = U
+    # the network forward alone over every patch (the dominant kernel of the step)
+    Xf = s.features(U)["X"]
+    yf = net.forward(Xf)
+    n_rows = int(Xf.shape[0])
+    reps = 5
+    t_fwd = timed(lambda: [net.forward(Xf, out=yf) for _ in range(reps)]) / reps
+    flop_row = 2.0 * (35 * 256 + 256 * 256 + 256 * 256 + 256)     # algorithmic: 35-256-256-256-1
+    achieved = flop_row * n_rows / t_fwd / 1e12
+    pk = peaks()
     ref = fields["plain_fp64"]
     err = {k: (torch.linalg.norm(v - ref) / torch.linalg.norm(ref)).item() for k, v in fields.items() if k != "plain_fp64"}
     served = 1.0 - (fb1 - fb0) / max(1, st1 - st0)
@@ -343,8 +357,9 @@ def run_surrogate(args):
         "metric": METRIC, "value": value, "unit": "macro steps/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": 1e3 * res["surrogate"] / n_macro, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
-        "config": {"workload": "annulus 512x2048 macro nodes, 9x9 micro, K=20, seeded smooth D, 100 macro steps; "
-                               "surrogate 35-256-256-256-1 trained on %d patch-solver samples of 8 other fields" % n_train,
+        "config": {"workload": "annulus %dx%d macro nodes, 9x9 micro, K=20, seeded smooth D, 100 macro steps; "
+                               "surrogate 35-256-256-256-1 trained on %d patch-solver samples of 8 other fields"
+                               % (n_r + 1, n_theta, n_train),
                    "training_data": "8 seeded fields x 2 times x (clean + 4 perturbed) x every 40th patch",
                    "train_epochs": args.epochs, "train_batch": args.batch, "train_s": train_s, "data_s": data_s,
                    "loss_first_last": [float(hist[0]), float(hist[-1])], "check_eps": 1e-3},
@@ -353,6 +368,11 @@ def run_surrogate(args):
         "speedup_vs_plain_fp32": res["plain_fp32"] / res["surrogate"],
         "l2_rel_vs_plain_fp64": err,
         "served_by_network": served,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / pk["bf16_tflops"], "traffic": None,
+                     "kernel": "gemm_kernel (network forward over %d patches, 3 tcgen05 BF16 GEMMs per 65536 rows)"
+                               % n_rows, "flop_per_row": flop_row, "ms": 1e3 * t_fwd,
+                     "peak_source": "measured cuBLAS bf16 burst"},
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -509,6 +529,7 @@ def main():
                     help="c2: the benchmark workload (default); c4: the 4096-instance batch; "
                          "c5: the surrogate against the plain scheme on the 512x2048 annulus")
     ap.add_argument("--epochs", type=int, default=80, help="c5: training epochs")
+    ap.add_argument("--c5-grid", default="511x2048", help="c5: radial intervals x angular nodes")
     ap.add_argument("--batch", type=int, default=2048, help="c5: training minibatch")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])

@@ -311,8 +311,8 @@ class MLP:
                                      C.c_void_p(_ptr(X)), C.c_void_p(_ptr(t)) if t is not None else None))
         return X, t
 
-    def forward(self, X: torch.Tensor) -> torch.Tensor:
-        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    def forward(self, X: torch.Tensor, out: torch.Tensor = None) -> torch.Tensor:
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device) if out is None else out
         self._stream()
         self._chk(self.L.pd_mlp_forward(self.h, C.c_void_p(_ptr(X)), X.shape[0], C.c_void_p(_ptr(y))))
         return y
