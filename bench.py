@@ -370,8 +370,9 @@ def run_surrogate(args):
         "served_by_network": served,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": achieved / pk["bf16_tflops"], "traffic": None,
-                     "kernel": "gemm_kernel (network forward over %d patches, 3 tcgen05 BF16 GEMMs per 65536 rows)"
-                               % n_rows, "flop_per_row": flop_row, "ms": 1e3 * t_fwd,
+                     "kernel": "mlp_fused_kernel (network forward over %d patches: three tcgen05 BF16 layers "
+                               "per 128-row tile on chip, one persistent block per SM)" % n_rows,
+                     "flop_per_row": flop_row, "ms": 1e3 * t_fwd,
                      "peak_source": "measured cuBLAS bf16 burst"},
         "clocks": clocks,
     }

@@ -569,6 +569,252 @@ __global__ void lr_kernel(float* lr, long long s, long long total, float lr_max)
     *lr = v;
 }
 
+// ---------------------------------------------------------------------------
+// Fused network forward: one persistent block per SM loops over 128-row tiles
+// and runs all three layers on chip.  The 64 KB activation buffer holds the
+// tile's input (TMA) and then each hidden layer's BF16 output, written by the
+// epilogue warps in the same 128-byte-swizzled K-major layout the TMA uses
+// (16-byte unit j of row r at unit j ^ (r & 7)), so it is the next MMA's A
+// operand directly.  Weight chunks [256 x 64] stream through a TMA ring.
+
+struct FusedArgs {
+    long long n;
+    int n_tiles;
+    const float* b1;
+    const float* b2;
+    const float* b3;
+    const float* w4;
+    const float* b4;
+    float* y;
+    int* err;
+    unsigned long long wait_ns;
+};
+
+constexpr int kFS = 4;                         // weight ring stages
+constexpr int kFEpi = 8;                       // epilogue warps: two per TMEM lane quadrant
+constexpr int kFThreads = 64 + 32 * kFEpi;
+constexpr uint32_t kActChunk = 128 * 64 * 2;   // [128 rows][64] BF16
+constexpr uint32_t kActBytes = 4 * kActChunk;
+constexpr uint32_t kWChunk = 256 * 64 * 2;     // [256 rows][64] BF16
+
+__host__ __device__ constexpr size_t fused_smem_bytes()
+{
+    return 1024 + kActBytes + (size_t)kFS * kWChunk + 16 * 8 + 16 + 128 * 4;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
+                 const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmW3, const FusedArgs a)
+{
+    using namespace tc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* act = smem;
+    uint8_t* ring = smem + kActBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kFS * kWChunk);
+    // bars: wfull[kFS], wempty[kFS], xfull, accfull, actready, accfree, actfree, done, ydotready
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    float* ydot = reinterpret_cast<float*>(tslot + 4);                 // [128]: second half partial sums
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t b0 = smem_u32(bars);
+    auto wfull = [&](int s) { return b0 + 8 * s; };
+    auto wempty = [&](int s) { return b0 + 8 * (kFS + s); };
+    const uint32_t xfull = b0 + 8 * (2 * kFS), accfull = xfull + 8, actready = xfull + 16, accfree = xfull + 24,
+                   actfree = xfull + 32, done = xfull + 40, ydotready = xfull + 48;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kFS; ++s) {
+            mbar_init(wfull(s), 1);
+            mbar_init(wempty(s), 1);
+        }
+        mbar_init(xfull, 1);
+        mbar_init(accfull, 1);
+        mbar_init(actready, kFEpi);
+        mbar_init(accfree, kFEpi);
+        mbar_init(actfree, 1);
+        mbar_init(done, 1);
+        mbar_init(ydotready, kFEpi / 2);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(smem_u32(tslot), 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    // a wait that gives up (or sees another role give up) ends this role's loop
+    auto wait = [&](uint32_t bar, uint32_t parity) -> bool {
+        if (*abort_flag) return false;
+        if (mbar_wait(bar, parity, a.wait_ns)) return true;
+        atomicOr(a.err, kErrTimeout);
+        *abort_flag = 1;
+        return false;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_map(&tmX);
+            tma_prefetch_map(&tmW1);
+            tma_prefetch_map(&tmW2);
+            tma_prefetch_map(&tmW3);
+            int wc = 0, ti = 0, xi = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x, ++ti) {
+                if (ti > 0 && !(ok = wait(actfree, (ti - 1) & 1))) break;
+                mbar_expect_tx(xfull, 2 * kActChunk);
+                tma_load_2d(smem_u32(act), &tmX, xfull, 0, tile * 128);
+                tma_load_2d(smem_u32(act + kActChunk), &tmX, xfull, 64, tile * 128);
+                ++xi;
+                for (int L = 0; ok && L < 3; ++L) {
+                    const CUtensorMap* mp = L == 0 ? &tmW1 : (L == 1 ? &tmW2 : &tmW3);
+                    const int nk = L == 0 ? 2 : 4;
+                    for (int kc = 0; kc < nk; ++kc, ++wc) {
+                        const int s = wc % kFS;
+                        if (wc >= kFS && !(ok = wait(wempty(s), ((wc / kFS) & 1) ^ 1))) break;
+                        mbar_expect_tx(wfull(s), kWChunk);
+                        tma_load_2d(smem_u32(ring + s * kWChunk), mp, wfull(s), kc * 64, 0);
+                    }
+                }
+            }
+            // the copies in flight land before the block can exit
+            for (int k = max(0, wc - kFS); k < wc; ++k)
+                if (!mbar_wait(wfull(k % kFS), (k / kFS) & 1, a.wait_ns)) atomicOr(a.err, kErrTimeout);
+            if (xi > 0 && !mbar_wait(xfull, (xi - 1) & 1, a.wait_ns)) atomicOr(a.err, kErrTimeout);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16_f32(128, 256);
+            int wc = 0, ti = 0;
+            bool ok = true, issued = false;
+            for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x, ++ti) {
+                if (ti > 0 && !(ok = wait(accfree, (ti - 1) & 1))) break;
+                if (!(ok = wait(xfull, ti & 1))) break;
+                for (int L = 0; ok && L < 3; ++L) {
+                    if (L > 0 && !(ok = wait(actready, (2 * ti + L - 1) & 1))) break;
+                    tc_fence_after();
+                    const int nk = L == 0 ? 2 : 4;
+                    for (int kc = 0; kc < nk; ++kc, ++wc) {
+                        const int s = wc % kFS;
+                        if (!(ok = wait(wfull(s), (wc / kFS) & 1))) break;
+                        tc_fence_after();
+                        const uint64_t ad = sdesc_sw128(smem_u32(act + kc * kActChunk));
+                        const uint64_t bd = sdesc_sw128(smem_u32(ring + s * kWChunk));
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk)
+                            mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(wempty(s));
+                        issued = true;
+                    }
+                    if (ok) mma_commit(accfull);
+                }
+                if (ok) mma_commit(actfree);
+            }
+            // every MMA issued has completed before TMEM is freed
+            if (issued) {
+                mma_commit(done);
+                if (!mbar_wait(done, 0, a.wait_ns)) atomicOr(a.err, kErrTimeout);
+            }
+        }
+    } else {
+        const int quad = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int r = quad * 32 + lane;
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
+        int ac = 0, ti = 0;
+        for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ti) {
+            bool ok = true;
+            for (int L = 0; L < 3; ++L) {
+                int w_ok = 1;
+                if (lane == 0) w_ok = wait(accfull, ac & 1) ? 1 : 0;
+                w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+                ++ac;
+                if (!w_ok) { ok = false; break; }
+                tc_fence_after();
+                if (L < 2) {
+                    const float* bias = L == 0 ? a.b1 : a.b2;
+#pragma unroll 1
+                    for (int c = 0; c < 8; ++c) {
+                        const int col = half * 128 + c * 16;
+                        float v[16];
+                        tmem_ld16(tbase + col, v);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) v[k] = gelu_fast(v[k] + bias[col + k]);
+                        uint4 q[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            __nv_bfloat162 p0 = __floats2bfloat162_rn(v[8 * h + 0], v[8 * h + 1]);
+                            __nv_bfloat162 p1 = __floats2bfloat162_rn(v[8 * h + 2], v[8 * h + 3]);
+                            __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * h + 4], v[8 * h + 5]);
+                            __nv_bfloat162 p3 = __floats2bfloat162_rn(v[8 * h + 6], v[8 * h + 7]);
+                            q[h].x = *reinterpret_cast<uint32_t*>(&p0);
+                            q[h].y = *reinterpret_cast<uint32_t*>(&p1);
+                            q[h].z = *reinterpret_cast<uint32_t*>(&p2);
+                            q[h].w = *reinterpret_cast<uint32_t*>(&p3);
+                        }
+                        const int kc = col >> 6, j = (col & 63) >> 3;
+                        uint8_t* rowp = act + kc * kActChunk + r * 128;
+                        *reinterpret_cast<uint4*>(rowp + (((j) ^ (r & 7)) << 4)) = q[0];
+                        *reinterpret_cast<uint4*>(rowp + (((j + 1) ^ (r & 7)) << 4)) = q[1];
+                    }
+                    fence_async_shared();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(actready);
+                } else {
+                    float part = 0.0f;
+#pragma unroll 1
+                    for (int c = 0; c < 8; ++c) {
+                        const int col = half * 128 + c * 16;
+                        float v[16];
+                        tmem_ld16(tbase + col, v);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) part = fmaf(gelu_f(v[k] + a.b3[col + k]), a.w4[col + k], part);
+                    }
+                    tc_fence_before();
+                    if (half == 1) {
+                        // the second column half hands its partial sums over (bounded wait on the other side)
+                        ydot[r] = part;
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(accfree);
+                            mbar_arrive(ydotready);
+                        }
+                    } else {
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(accfree);
+                        int y_ok = 1;
+                        if (lane == 0) y_ok = wait(ydotready, ti & 1) ? 1 : 0;
+                        y_ok = __shfl_sync(0xffffffffu, y_ok, 0);
+                        if (!y_ok) { ok = false; break; }
+                        const long long row = (long long)tile * 128 + r;
+                        if (row < a.n) a.y[row] = part + ydot[r] + *a.b4;
+                    }
+                }
+            }
+            if (!ok) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
 // S = 2 for the short products (K <= 256: every forward and input-gradient
 // GEMM), S = 4 for the weight gradients whose K is the minibatch
 template <int BN, int EPI, int S = 2>
@@ -929,29 +1175,32 @@ pd_status pd_mlp_forward(pd_mlp* m, const uint16_t* X, long long n, float* y)
     if (!m) return PD_EINVAL;
     if (!X || !y || n < 0) return mfail(m, PD_EINVAL, "null argument");
     if (n == 0) return PD_OK;
+    if ((n + 127) / 128 > (long long)INT32_MAX) return mfail(m, PD_EINVAL, "too many rows");
     CUtensorMap mx;
     if (!make_map(&mx, X, n, kInCols, kInCols, 128)) return mfail(m, PD_EINVAL, "input must be 16-byte aligned [n][128] BF16");
-    for (long long c0 = 0; c0 < n; c0 += m->chunk) {
-        const int M = (int)std::min<long long>(m->chunk, n - c0);
-        {
-            GemmArgs a = base_args(m, M, kWidth, kInCols);
-            a.a_row0 = (int)c0; a.ldo = kWidth; a.bias = m->theta + OFF_B1; a.out_bf16 = m->I1;
-            MCUDA(m, (launch_gemm<256, EPI_GELU>(mx, m->mp.W1, a, 1, m->stream)));
-        }
-        {
-            GemmArgs a = base_args(m, M, kWidth, kWidth);
-            a.ldo = kWidth; a.bias = m->theta + OFF_B2; a.out_bf16 = m->I2;
-            MCUDA(m, (launch_gemm<256, EPI_GELU>(m->mp.I1, m->mp.W2, a, 1, m->stream)));
-        }
-        {
-            GemmArgs a = base_args(m, M, kWidth, kWidth);
-            a.ldo = kWidth; a.bias = m->theta + OFF_B3; a.w_dot = m->w4b; a.b_dot = m->theta + OFF_B4; a.out_dot = y + c0;
-            MCUDA(m, (launch_gemm<256, EPI_DOT>(m->mp.I2, m->mp.W3, a, 1, m->stream)));
-        }
+    static bool attr = false;
+    if (!attr) {
+        MCUDA(m, cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes()));
+        attr = true;
     }
+    int sms = 0;
+    MCUDA(m, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    FusedArgs a;
+    a.n = n;
+    a.n_tiles = (int)((n + 127) / 128);
+    a.b1 = m->theta + OFF_B1;
+    a.b2 = m->theta + OFF_B2;
+    a.b3 = m->theta + OFF_B3;
+    a.w4 = m->w4b;
+    a.b4 = m->theta + OFF_B4;
+    a.y = y;
+    a.err = m->err;
+    a.wait_ns = m->wait_ns;
+    const int grid = std::min(a.n_tiles, std::max(1, sms));
+    mlp_fused_kernel<<<grid, kFThreads, fused_smem_bytes(), m->stream>>>(mx, m->mp.W1, m->mp.W2, m->mp.W3, a);
+    MCUDA(m, cudaGetLastError());
     return PD_OK;
 }
-
 
 pd_status pd_mlp_gradient(pd_mlp* m, const uint16_t* X, const float* t, int n, float* grad_out, float* loss_host)
 {
