@@ -380,6 +380,89 @@ def run_surrogate(args):
     return 0
 
 
+def run_passes(args):
+    """The separate C-ABI passes (pd_lift, pd_micro_burst, pd_restrict, pd_project)
+    timed one by one on the 512x2048-node annulus (84.6 M micro points), L2
+    flushed before every timed pass; HBM-bound passes against the measured
+    copy bandwidth, the burst against the FP32 ALU peak."""
+    import torch
+
+    from paper_2405_08764_gb300 import workloads as W
+    from paper_2405_08764_gb300.api import Grid
+
+    torch.cuda.set_device(0)
+    n_r, n_theta = (int(v) for v in args.c5_grid.split("x"))
+    p = W.c5_surrogate_field(n_r=n_r, n_theta=n_theta)
+    g = Grid(p, prec="fp32")
+    info = g.info()
+    P, m, K = info["n_patch"], info["m_xi"], info["k_micro"]
+    pts = P * m * m
+    es = 4                                   # FP32 grid
+    U = g.init_field()
+    dtm = info["dt_macro_suggested"]
+    st = g.new_state()
+    dU = torch.empty(P, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=5):
+        tot = 0.0
+        for r in range(reps + 1):
+            flush.fill_(float(r))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                tot += a.elapsed_time(b)
+        return tot / reps / 1e3
+
+    n_int = P                                # interior macro nodes = patches
+    bytes_ = {
+        # per micro point: the FP32 coefficient record (32 B) in, u0 (8 B) + r + w (2 x 4 B) out;
+        # per patch: 9 stencil reads (cached), edge data 4 (m + 2) x 8 B and the bias out
+        "lift": pts * (32 + 8 + 2 * es) + P * (4 * (m + 2) * 8 + 8),
+        # per micro point: w and r in (K steps in registers), w out; burst record (64 B) in
+        "burst": pts * (2 * es + es + 64),
+        # per micro point w in; per patch bias in, dU out
+        "restrict": pts * es + P * 16,
+        # per interior node U and dU in, U out
+        "project": n_int * 24,
+    }
+    calls = {
+        "lift": lambda: g.lift(U, 0.0, st),
+        "burst": lambda: g.micro_burst(st, 0.0, K),
+        "restrict": lambda: g.restrict(st, dU),
+        "project": lambda: g.project(U, dU, 0.0, 1e-12),
+    }
+    for fn in calls.values():
+        fn()
+    torch.cuda.synchronize()
+    pk = peaks()
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = {}
+    for name, fn in calls.items():
+        s = timed(fn)
+        gbs = bytes_[name] / s / 1e9
+        res[name] = {"ms": 1e3 * s, "bytes": bytes_[name], "GB_per_s": gbs, "frac_hbm": gbs / pk["hbm_gbs"]}
+    clocks = sampler.stop()
+    upd = pts * K
+    res["burst"]["point_updates_per_s"] = upd / (res["burst"]["ms"] / 1e3)
+    res["burst"]["frac_fp32"] = FLOP_PER_UPDATE * res["burst"]["point_updates_per_s"] / 1e12 / pk["fp32_tflops"]
+    line = {
+        "metric": "separate C-ABI passes: achieved HBM GB/s (lift, restrict, project), burst point-updates/s",
+        "value": res["lift"]["GB_per_s"], "unit": "GB/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "annulus %dx%d macro nodes, %dx%d micro, K=%d: %d micro points" % (n_r + 1, n_theta, m, m, K, pts),
+                   "l2": "flushed before every timed pass (512 MB write)", "reps": 5},
+        "passes": res, "hbm_peak_gbs": pk["hbm_gbs"], "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -526,9 +609,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "passes"],
                     help="c2: the benchmark workload (default); c4: the 4096-instance batch; "
-                         "c5: the surrogate against the plain scheme on the 512x2048 annulus")
+                         "c5: the surrogate against the plain scheme on the 512x2048 annulus; "
+                         "passes: the separate C-ABI passes on that annulus")
     ap.add_argument("--epochs", type=int, default=80, help="c5: training epochs")
     ap.add_argument("--c5-grid", default="511x2048", help="c5: radial intervals x angular nodes")
     ap.add_argument("--batch", type=int, default=2048, help="c5: training minibatch")
@@ -543,6 +627,8 @@ def main():
         return run_batch(args)
     if args.workload == "c5":
         return run_surrogate(args)
+    if args.workload == "passes":
+        return run_passes(args)
     return run_gpu(args)
 
 

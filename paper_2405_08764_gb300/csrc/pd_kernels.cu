@@ -239,58 +239,115 @@ __device__ __forceinline__ long long rec_index(const InstDev& I, int jr, int ic,
     return ((long long)(jr * I.my + b) * I.ncols + ic) * I.mx + a;
 }
 
+// lift of several patches per block (ppb <= 8): interpolant coefficients
+// (FP64, nine threads per patch), then per micro point the lifted value u0
+// (FP64), the forcing r and w = 0, the edge data and the bias.  The quadratic
+// lift is evaluated as u0(a, b) = A(a) + t_b B(a) + Q(b) with per-patch tables
+// A = C0 + c10 s + c20 s^2, B = c01 + c11 s, Q = c02 t^2 (one FP64 fma and one
+// add per point).
 template <typename real>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restrict__ tab, double* u0,
-            real* r_out, real* w_out, double* edge, double* bias_out, int edge_stride)
+            real* r_out, real* w_out, double* edge, double* bias_out, int edge_stride, int ppb)
 {
-    __shared__ double cs[9];
-    const int p = blockIdx.x;
-    int i, j, ic, jr;
-    patch_ij(I, p, i, j, ic, jr);
-    if (threadIdx.x < 9) {
+    __shared__ double cs[8][9];
+    __shared__ double tabA[8][32], tabB[8][32], tabQ[8][32], tabT[8][32];
+    __shared__ double ecoef[8][4][3];        // edge data as a quadratic along each edge
+    __shared__ real csr[8][9];               // coefficients in the working precision
+    const int p0 = blockIdx.x * ppb;
+    const int mm = I.mx * I.my;
+    for (int t = threadIdx.x; t < ppb * 9; t += blockDim.x) {
+        const int q = t / 9, k = t - q * 9;
+        const int p = p0 + q;
         double acc = 0.0;
-        for (int pp = -1; pp <= 1; ++pp)
-            for (int qq = -1; qq <= 1; ++qq)
-                acc = fma(I.lw[threadIdx.x][(pp + 1) * 3 + qq + 1], U[(long long)(j + qq) * I.nxp + wrap_col(I, i + pp)], acc);
-        cs[threadIdx.x] = acc;
+        if (p < I.n_patch) {
+            int i, j, ic, jr;
+            patch_ij(I, p, i, j, ic, jr);
+            for (int pp = -1; pp <= 1; ++pp)
+                for (int qq = -1; qq <= 1; ++qq)
+                    acc = fma(I.lw[k][(pp + 1) * 3 + qq + 1], U[(long long)(j + qq) * I.nxp + wrap_col(I, i + pp)], acc);
+        }
+        cs[q][k] = acc;
     }
     __syncthreads();
-    Poly<double> cd = { cs[0], cs[1], cs[2], cs[3], cs[4], cs[5], cs[6], cs[7], cs[8] };
-    Poly<real> cr = { (real)cs[0], (real)cs[1], (real)cs[2], (real)cs[3], (real)cs[4], (real)cs[5],
-                      (real)cs[6], (real)cs[7], (real)cs[8] };
     PatchGeo<double> gd = { I.hx, I.hy, I.dx, I.dy, I.mx - 1, I.my - 1 };
-    PatchGeo<real> gr = { (real)I.hx, (real)I.hy, (real)I.dx, (real)I.dy, I.mx - 1, I.my - 1 };
+    for (int t = threadIdx.x; t < ppb * 32; t += blockDim.x) {
+        const int q = t >> 5, k = t & 31;
+        const double* c = cs[q];
+        if (k < I.mx) {
+            const double sa = gd.s(k);
+            tabA[q][k] = c[0] + sa * (c[1] + sa * c[3]);
+            tabB[q][k] = c[2] + c[4] * sa;
+        }
+        if (k < I.my) {
+            const double tb = gd.t(k);
+            tabT[q][k] = tb;
+            tabQ[q][k] = c[5] * tb * tb;
+        }
+        if (k < 9) csr[q][k] = (real)c[k];
+        if (k < 4) {
+            // d/dxi of P on xi = -+hx/2 as a quadratic in t; d/deta on eta = -+hy/2 in s
+            if (k < 2) {
+                const double s0 = (k == 0 ? -0.5 : 0.5) * I.hx;
+                ecoef[q][k][0] = c[1] + 2.0 * c[3] * s0;
+                ecoef[q][k][1] = c[4] + 2.0 * c[6] * s0;
+                ecoef[q][k][2] = c[7] + 2.0 * c[8] * s0;
+            } else {
+                const double t0 = (k == 2 ? -0.5 : 0.5) * I.hy;
+                ecoef[q][k][0] = c[2] + 2.0 * c[5] * t0;
+                ecoef[q][k][1] = c[4] + 2.0 * c[7] * t0;
+                ecoef[q][k][2] = c[6] + 2.0 * c[8] * t0;
+            }
+        }
+    }
+    __syncthreads();
+    const RealConsts<real> kc = real_consts<real>(I);
+    PatchGeo<real> gr = { (real)I.hx, (real)I.hy, kc.dx, kc.dy, I.mx - 1, I.my - 1 };
     const real* rec = static_cast<const real*>(I.rec);
     const real sT = (real)tab[0];
-    const long long pg = (long long)I.p_off + p;
-    const int mm = I.mx * I.my;
-    const long long pp0 = I.pt_off + (long long)p * mm;
-    for (int t = threadIdx.x; t < mm; t += blockDim.x) {
-        int a = t % I.mx, b = t / I.mx;
+    for (int t = threadIdx.x; t < ppb * mm; t += blockDim.x) {
+        const int q = t / mm, tl = t - q * mm;
+        const int p = p0 + q;
+        if (p >= I.n_patch) continue;
+        int i, j, ic, jr;
+        patch_ij(I, p, i, j, ic, jr);
+        const real* cq = csr[q];
+        Poly<real> cr = { cq[0], cq[1], cq[2], cq[3], cq[4], cq[5], cq[6], cq[7], cq[8] };
+        const int b = tl / I.mx, a = tl - b * I.mx;
         real v[8];
-        point_coeffs<real>(I, jr, ic, a, b, v);
-        double s = gd.s(a), tt = gd.t(b);
-        u0[pp0 + t] = cd.C0 + s * (cd.c10 + s * cd.c20 + tt * cd.c11) + tt * (cd.c01 + tt * cd.c02);
-        PointW<real> pw = point_weights<real>(v[0], v[1], v[2], v[3], v[4], v[5], gr.dx, gr.dy, I.conv);
-        r_out[pp0 + t] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
-        w_out[pp0 + t] = real(0);
+        if (I.coef_mode != COEF_RECORDS) {
+            table_coeffs_k<real>(I, kc, ic, a, jr, b, v);
+            v[6] = real(0);
+        } else {
+            const real* rr = rec + ((((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a) * 8;
+            for (int k = 0; k < 8; ++k) v[k] = rr[k];
+        }
+        const long long o = I.pt_off + (long long)p * mm + tl;
+        u0[o] = fma(tabT[q][b], tabB[q][a], tabA[q][a] + tabQ[q][b]);
+        PointW<real> pw = point_weights_k<real>(I, kc, v[0], v[1], v[2], v[3], v[4], v[5]);
+        r_out[o] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
+        w_out[o] = real(0);
     }
     // edge data of eq. (edge) = d/dxi, d/deta of the interpolant P at the edges
-    for (int t = threadIdx.x; t < 4 * edge_stride; t += blockDim.x) {
-        int side = t / edge_stride, e = t % edge_stride;
+    for (int t = threadIdx.x; t < ppb * 4 * edge_stride; t += blockDim.x) {
+        const int q = t / (4 * edge_stride), tl = t - q * 4 * edge_stride;
+        const int p = p0 + q;
+        if (p >= I.n_patch) continue;
+        const int side = tl / edge_stride, e = tl % edge_stride;
+        const double* ec = ecoef[q][side];
         double val = 0.0;
-        if (side < 2 && e < I.my + 2) {
-            double s = (side == 0 ? -0.5 : 0.5) * I.hx, tt = gd.t(e - 1);
-            val = cd.c10 + 2.0 * cd.c20 * s + cd.c11 * tt + edge_gap_xi(cd, s, tt);
-        } else if (side >= 2 && e < I.mx + 2) {
-            double s = gd.s(e - 1), tt = (side == 2 ? -0.5 : 0.5) * I.hy;
-            val = cd.c01 + 2.0 * cd.c02 * tt + cd.c11 * s + edge_gap_eta(cd, s, tt);
+        if ((side < 2 && e < I.my + 2) || (side >= 2 && e < I.mx + 2)) {
+            const double x = side < 2 ? gd.t(e - 1) : gd.s(e - 1);
+            val = fma(fma(ec[2], x, ec[1]), x, ec[0]);
         }
         edge[I.e_off + ((long long)p * 4 + side) * edge_stride + e] = val;
     }
-    if (threadIdx.x == 0)
-        bias_out[pg] = (I.restrict_mode == PD_RESTRICT_MACRO) ? (I.dx * I.dx * cd.c20 + I.dy * I.dy * cd.c02) / 6.0 : 0.0;
+    for (int q = threadIdx.x; q < ppb; q += blockDim.x) {
+        const int p = p0 + q;
+        if (p >= I.n_patch) continue;
+        const double* c = cs[q];
+        bias_out[(long long)I.p_off + p] = (I.restrict_mode == PD_RESTRICT_MACRO) ? (I.dx * I.dx * c[3] + I.dy * I.dy * c[5]) / 6.0 : 0.0;
+    }
 }
 
 // generic burst: whole patch in shared memory, one thread per micro point
@@ -336,26 +393,54 @@ burst_kernel(const InstDev I, const double* __restrict__ tab, int k_steps, real*
     for (int t = threadIdx.x; t < mm; t += blockDim.x) w_io[pp0 + t] = cur[t];
 }
 
-// trapezoid restriction of the departure: one warp per patch
+// trapezoid restriction of the departure: ppb (<= 64) patches per block, their
+// contiguous w staged through shared memory with coalesced loads, four threads
+// per patch summing against a table of the trapezoid weights (accumulation in
+// the grid's precision, like the fused kernels' column sums), dU in FP64
+constexpr int kRestrictPatches = 64;
+constexpr size_t kRestrictStage = 96 * 1024;
+
 template <typename real>
-__global__ void restrict_kernel(const InstDev I, const real* __restrict__ w, const double* __restrict__ bias,
-                                double* __restrict__ dU)
+__global__ void __launch_bounds__(256)
+restrict_kernel(const InstDev I, const real* __restrict__ w, const double* __restrict__ bias, double* __restrict__ dU,
+                int ppb)
 {
-    int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (p >= I.n_patch) return;
+    extern __shared__ __align__(16) unsigned char rsm[];
     const int mm = I.mx * I.my;
-    const long long pg = (long long)I.p_off + p;
-    const long long pp0 = I.pt_off + (long long)p * mm;
-    double acc = 0.0;
-    for (int t = lane; t < mm; t += 32) {
-        int a = t % I.mx, b = t / I.mx;
-        double wt = ((a == 0 || a == I.mx - 1) ? 0.5 : 1.0) * ((b == 0 || b == I.my - 1) ? 0.5 : 1.0);
-        acc += wt * (double)w[pp0 + t];
+    real* tile = reinterpret_cast<real*>(rsm);                // [ppb * mm]
+    real* tw = tile + (size_t)ppb * mm;                       // [mm] weights
+    for (int t = threadIdx.x; t < mm; t += blockDim.x) {
+        const int b = t / I.mx, a = t - b * I.mx;
+        tw[t] = real(((a == 0 || a == I.mx - 1) ? 0.5 : 1.0) * ((b == 0 || b == I.my - 1) ? 0.5 : 1.0));
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-    if (lane == 0) {
-        double v = acc / ((double)(I.mx - 1) * (I.my - 1)) + bias[pg];
+    const int p0 = blockIdx.x * ppb;
+    const int np = min(ppb, I.n_patch - p0);
+    const real* src = w + I.pt_off + (long long)p0 * mm;
+    const int n = np * mm;
+    constexpr int V = 16 / sizeof(real);
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(tile) & 15) == 0) {
+        const int nv = n / V;
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* t4 = reinterpret_cast<uint4*>(tile);
+#pragma unroll 4
+        for (int e = threadIdx.x; e < nv; e += blockDim.x) t4[e] = s4[e];
+        for (int e = nv * V + threadIdx.x; e < n; e += blockDim.x) tile[e] = src[e];
+    } else {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < n; e += blockDim.x) tile[e] = src[e];
+    }
+    __syncthreads();
+    const int q = threadIdx.x >> 2, sub = threadIdx.x & 3;
+    real acc = real(0);
+    if (q < np) {
+        const real* x = tile + q * mm;
+        for (int t = sub; t < mm; t += 4) acc = fma(tw[t], x[t], acc);
+    }
+    acc += __shfl_xor_sync(FULL, acc, 1);
+    acc += __shfl_xor_sync(FULL, acc, 2);
+    if (q < np && sub == 0) {
+        const long long pg = (long long)I.p_off + p0 + q;
+        double v = (double)acc / ((double)(I.mx - 1) * (I.my - 1)) + bias[pg];
         if (!isfinite(v)) atomicOr(I.err, ERR_NONFINITE);
         dU[pg] = v;
     }
@@ -529,12 +614,14 @@ cudaError_t launch_lift(const InstDev& I, const InstDev*, int prec, const double
     double* u0 = reinterpret_cast<double*>(state + lay.off_u0);
     double* edge = reinterpret_cast<double*>(state + lay.off_edge);
     double* bias = reinterpret_cast<double*>(state + lay.off_bias);
+    const int ppb = std::max(1, std::min(8, 256 / (I.mx * I.my)));
+    const unsigned nb = (unsigned)((I.n_patch + ppb - 1) / ppb);
     if (prec == PD_FP32)
-        lift_kernel<float><<<I.n_patch, 128, 0, st>>>(I, U, hdr + 1, u0, reinterpret_cast<float*>(state + lay.off_r),
-                                                      reinterpret_cast<float*>(state + lay.off_w), edge, bias, lay.edge_stride);
+        lift_kernel<float><<<nb, 256, 0, st>>>(I, U, hdr + 1, u0, reinterpret_cast<float*>(state + lay.off_r),
+                                               reinterpret_cast<float*>(state + lay.off_w), edge, bias, lay.edge_stride, ppb);
     else
-        lift_kernel<double><<<I.n_patch, 128, 0, st>>>(I, U, hdr + 1, u0, reinterpret_cast<double*>(state + lay.off_r),
-                                                       reinterpret_cast<double*>(state + lay.off_w), edge, bias, lay.edge_stride);
+        lift_kernel<double><<<nb, 256, 0, st>>>(I, U, hdr + 1, u0, reinterpret_cast<double*>(state + lay.off_r),
+                                                reinterpret_cast<double*>(state + lay.off_w), edge, bias, lay.edge_stride, ppb);
     return cudaGetLastError();
 }
 
@@ -576,11 +663,22 @@ cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const
                             cudaStream_t st)
 {
     const double* bias = reinterpret_cast<const double*>(state + lay.off_bias);
-    unsigned nb = (unsigned)((I.n_patch * 32 + 127) / 128);
-    if (prec == PD_FP32)
-        restrict_kernel<float><<<nb, 128, 0, st>>>(I, reinterpret_cast<const float*>(state + lay.off_w), bias, dU);
-    else
-        restrict_kernel<double><<<nb, 128, 0, st>>>(I, reinterpret_cast<const double*>(state + lay.off_w), bias, dU);
+    const size_t es = prec == PD_FP32 ? sizeof(float) : sizeof(double);
+    const size_t per = es * (size_t)I.mx * I.my;
+    const int ppb = (int)std::max<size_t>(1, std::min<size_t>(kRestrictPatches, kRestrictStage / per - 1));
+    const unsigned nb = (unsigned)((I.n_patch + ppb - 1) / ppb);
+    const size_t smem = per * (size_t)(ppb + 1);
+    cudaError_t e;
+    if (prec == PD_FP32) {
+        e = cudaFuncSetAttribute(restrict_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            restrict_kernel<float><<<nb, 256, smem, st>>>(I, reinterpret_cast<const float*>(state + lay.off_w), bias, dU, ppb);
+    } else {
+        e = cudaFuncSetAttribute(restrict_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            restrict_kernel<double><<<nb, 256, smem, st>>>(I, reinterpret_cast<const double*>(state + lay.off_w), bias, dU, ppb);
+    }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
