@@ -67,6 +67,38 @@ __device__ __forceinline__ void burst_steps(real (&w)[M], const real (&cE)[M], c
     }
 }
 
+// Slot s (0..8) of the 3x3 stencil around node (i, j): one FP64 difference
+// (three loads, one add, one fma).  Slots 0..2: second xi-differences at eta
+// offsets -1, 0, 1; 3..5: first xi-differences; 6: first eta-difference at
+// xi = 0; 7: second eta-difference at xi = 0; 8: U(0, 0).  The interpolant's
+// coefficient k combines slots c2slot[k][0..2] with weights c2w[k].
+template <bool L2LOAD>
+__device__ __forceinline__ double stencil_slot(const InstDev& I, const double* __restrict__ Uc, int i, int j, int k)
+{
+    auto ld = [&](int di, int dj) -> double {
+        const double* p = Uc + (long long)(j + dj) * I.nxp + wrap_col(I, i + di);
+        return L2LOAD ? __ldcg(p) : __ldg(p);
+    };
+    int ai = 0, aj = 0, bi = 0, bj = 0, ci = 0, cj = 0;
+    double wB = 0.0;
+    bool neg = false, zeroC = false;
+    switch (k) {
+    case 0: ai = -1; aj = -1; bi = 0; bj = -1; ci = 1; cj = -1; wB = -2.0; break;
+    case 1: ai = -1; aj = 0;  bi = 0; bj = 0;  ci = 1; cj = 0;  wB = -2.0; break;
+    case 2: ai = -1; aj = 1;  bi = 0; bj = 1;  ci = 1; cj = 1;  wB = -2.0; break;
+    case 3: ai = 1;  aj = -1; ci = -1; cj = -1; neg = true; break;
+    case 4: ai = 1;  aj = 0;  ci = -1; cj = 0;  neg = true; break;
+    case 5: ai = 1;  aj = 1;  ci = -1; cj = 1;  neg = true; break;
+    case 6: ai = 0;  aj = 1;  ci = 0;  cj = -1; neg = true; break;
+    case 7: ai = 0;  aj = -1; bi = 0; bj = 0;  ci = 0; cj = 1;  wB = -2.0; break;
+    default: zeroC = true; break;   // slot 8: U(0,0)
+    }
+    double A = ld(ai, aj), B = ld(bi, bj), Cv = ld(ci, cj);
+    if (neg) Cv = -Cv;
+    if (zeroC) Cv = 0.0;
+    return fma(wB, B, A + Cv);
+}
+
 // Monomial coefficients of the patch's interpolant from the FP64 macro field,
 // in two FP64 phases:
 //   phase 1: slot s (0..8) is one difference of the 3x3 stencil (three loads,
@@ -81,30 +113,7 @@ __device__ __forceinline__ void macro_coeffs(const InstDev& I, const double* __r
                                              double& u00)
 {
     (void)lw;
-    auto ld = [&](int di, int dj) -> double {
-        const double* p = Uc + (long long)(j + dj) * I.nxp + wrap_col(I, i + di);
-        return L2LOAD ? __ldcg(p) : __ldg(p);
-    };
-    auto slot_value = [&](int k) -> double {
-        int ai = 0, aj = 0, bi = 0, bj = 0, ci = 0, cj = 0;
-        double wB = 0.0;
-        bool neg = false, zeroC = false;
-        switch (k) {
-        case 0: ai = -1; aj = -1; bi = 0; bj = -1; ci = 1; cj = -1; wB = -2.0; break;
-        case 1: ai = -1; aj = 0;  bi = 0; bj = 0;  ci = 1; cj = 0;  wB = -2.0; break;
-        case 2: ai = -1; aj = 1;  bi = 0; bj = 1;  ci = 1; cj = 1;  wB = -2.0; break;
-        case 3: ai = 1;  aj = -1; ci = -1; cj = -1; neg = true; break;
-        case 4: ai = 1;  aj = 0;  ci = -1; cj = 0;  neg = true; break;
-        case 5: ai = 1;  aj = 1;  ci = -1; cj = 1;  neg = true; break;
-        case 6: ai = 0;  aj = 1;  ci = 0;  cj = -1; neg = true; break;
-        case 7: ai = 0;  aj = -1; bi = 0; bj = 0;  ci = 0; cj = 1;  wB = -2.0; break;
-        default: zeroC = true; break;   // slot 8: U(0,0)
-        }
-        double A = ld(ai, aj), B = ld(bi, bj), Cv = ld(ci, cj);
-        if (neg) Cv = -Cv;
-        if (zeroC) Cv = 0.0;
-        return fma(wB, B, A + Cv);
-    };
+    auto slot_value = [&](int k) -> double { return stencil_slot<L2LOAD>(I, Uc, i, j, k); };
     if constexpr (M >= 9) {
         double x1 = slot_value(a < 9 ? a : 8);
         int k = a < 9 ? a : 8;

@@ -239,7 +239,8 @@ __device__ __forceinline__ long long rec_index(const InstDev& I, int jr, int ic,
     return ((long long)(jr * I.my + b) * I.ncols + ic) * I.mx + a;
 }
 
-// lift of several patches per block (ppb <= 8): interpolant coefficients
+// lift of several patches per block (ppb <= 32, so that every phase keeps the
+// block's threads busy): interpolant coefficients
 // (FP64, nine threads per patch), then per micro point the lifted value u0
 // (FP64), the forcing r and w = 0, the edge data and the bias.  The quadratic
 // lift is evaluated as u0(a, b) = A(a) + t_b B(a) + Q(b) with per-patch tables
@@ -250,38 +251,48 @@ __global__ void __launch_bounds__(256)
 lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restrict__ tab, double* u0,
             real* r_out, real* w_out, double* edge, double* bias_out, int edge_stride, int ppb)
 {
-    __shared__ double cs[8][9];
-    __shared__ double tabA[8][32], tabB[8][32], tabQ[8][32], tabT[8][32];
-    __shared__ double ecoef[8][4][3];        // edge data as a quadratic along each edge
-    __shared__ real csr[8][9];               // coefficients in the working precision
+    constexpr int PPB = 32;
+    __shared__ double sl[PPB][9];            // stencil slots
+    __shared__ double cs[PPB][9];
+    __shared__ double tabA[PPB][32], tabB[PPB][32], tabQ[PPB][32];
+    __shared__ double ecoef[PPB][4][3];      // edge data as a quadratic along each edge
+    __shared__ real csr[PPB][9];             // coefficients in the working precision
+    __shared__ double gs[34], gt[34];        // micro coordinates s_a, t_b for a, b = -1 .. m
     const int p0 = blockIdx.x * ppb;
     const int mm = I.mx * I.my;
+    PatchGeo<double> gd = { I.hx, I.hy, I.dx, I.dy, I.mx - 1, I.my - 1 };
+    for (int t = threadIdx.x; t < 34; t += blockDim.x) {
+        gs[t] = gd.s(t - 1);
+        gt[t] = gd.t(t - 1);
+    }
     for (int t = threadIdx.x; t < ppb * 9; t += blockDim.x) {
         const int q = t / 9, k = t - q * 9;
         const int p = p0 + q;
-        double acc = 0.0;
+        double v = 0.0;
         if (p < I.n_patch) {
             int i, j, ic, jr;
             patch_ij(I, p, i, j, ic, jr);
-            for (int pp = -1; pp <= 1; ++pp)
-                for (int qq = -1; qq <= 1; ++qq)
-                    acc = fma(I.lw[k][(pp + 1) * 3 + qq + 1], U[(long long)(j + qq) * I.nxp + wrap_col(I, i + pp)], acc);
+            v = stencil_slot<false>(I, U, i, j, k);
         }
-        cs[q][k] = acc;
+        sl[q][k] = v;
     }
     __syncthreads();
-    PatchGeo<double> gd = { I.hx, I.hy, I.dx, I.dy, I.mx - 1, I.my - 1 };
+    for (int t = threadIdx.x; t < ppb * 9; t += blockDim.x) {
+        const int q = t / 9, k = t - q * 9;
+        const double* x = sl[q];
+        cs[q][k] = fma(I.c2w[k][1], x[I.c2slot[k][2]], fma(I.c2w[k][0], x[I.c2slot[k][1]], x[I.c2slot[k][0]])) * I.c2w[k][2];
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < ppb * 32; t += blockDim.x) {
         const int q = t >> 5, k = t & 31;
         const double* c = cs[q];
         if (k < I.mx) {
-            const double sa = gd.s(k);
+            const double sa = gs[k + 1];
             tabA[q][k] = c[0] + sa * (c[1] + sa * c[3]);
             tabB[q][k] = c[2] + c[4] * sa;
         }
         if (k < I.my) {
-            const double tb = gd.t(k);
-            tabT[q][k] = tb;
+            const double tb = gt[k + 1];
             tabQ[q][k] = c[5] * tb * tb;
         }
         if (k < 9) csr[q][k] = (real)c[k];
@@ -323,7 +334,7 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
             for (int k = 0; k < 8; ++k) v[k] = rr[k];
         }
         const long long o = I.pt_off + (long long)p * mm + tl;
-        u0[o] = fma(tabT[q][b], tabB[q][a], tabA[q][a] + tabQ[q][b]);
+        u0[o] = fma(gt[b + 1], tabB[q][a], tabA[q][a] + tabQ[q][b]);
         PointW<real> pw = point_weights_k<real>(I, kc, v[0], v[1], v[2], v[3], v[4], v[5]);
         r_out[o] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
         w_out[o] = real(0);
@@ -337,7 +348,7 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
         const double* ec = ecoef[q][side];
         double val = 0.0;
         if ((side < 2 && e < I.my + 2) || (side >= 2 && e < I.mx + 2)) {
-            const double x = side < 2 ? gd.t(e - 1) : gd.s(e - 1);
+            const double x = side < 2 ? gt[e] : gs[e];
             val = fma(fma(ec[2], x, ec[1]), x, ec[0]);
         }
         edge[I.e_off + ((long long)p * 4 + side) * edge_stride + e] = val;
@@ -614,7 +625,7 @@ cudaError_t launch_lift(const InstDev& I, const InstDev*, int prec, const double
     double* u0 = reinterpret_cast<double*>(state + lay.off_u0);
     double* edge = reinterpret_cast<double*>(state + lay.off_edge);
     double* bias = reinterpret_cast<double*>(state + lay.off_bias);
-    const int ppb = std::max(1, std::min(8, 256 / (I.mx * I.my)));
+    const int ppb = std::max(1, std::min(32, 2592 / (I.mx * I.my)));
     const unsigned nb = (unsigned)((I.n_patch + ppb - 1) / ppb);
     if (prec == PD_FP32)
         lift_kernel<float><<<nb, 256, 0, st>>>(I, U, hdr + 1, u0, reinterpret_cast<float*>(state + lay.off_r),
