@@ -94,7 +94,8 @@ pd_status pd_mlp_fit_norm(pd_mlp* m, const float* X_raw_dev, const float* y_raw_
 pd_status pd_mlp_pack(pd_mlp* m, const float* X_raw_dev, const float* y_raw_dev, long long n,
                       uint16_t* X_dev, float* t_dev);
 
-/* Network output for n input rows X [n][128] (BF16) into y_dev[n] (FP32). */
+/* Network output for n input rows X [n][128] (BF16) into y_dev[n] (FP32);
+ * n = 0 does nothing (the pointers may then be NULL). */
 pd_status pd_mlp_forward(pd_mlp* m, const uint16_t* X_dev, long long n, float* y_dev);
 
 /* Gradient of the loss (1/n) sum (y - t)^2 over n <= max_batch rows with

@@ -1162,8 +1162,8 @@ pd_status pd_mlp_fit_norm(pd_mlp* m, const float* X, const float* y, long long n
 pd_status pd_mlp_pack(pd_mlp* m, const float* X, const float* y, long long n, uint16_t* Xo, float* to)
 {
     if (!m) return PD_EINVAL;
-    if (!X || !Xo || n < 0) return mfail(m, PD_EINVAL, "null argument");
     if (n == 0) return PD_OK;
+    if (!X || !Xo || n < 0) return mfail(m, PD_EINVAL, "null argument");
     const long long tot = n * kPad;
     pack_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, m->stream>>>(X, y, n, m->norm, reinterpret_cast<bf16*>(Xo), to);
     MCUDA(m, cudaGetLastError());
@@ -1173,8 +1173,8 @@ pd_status pd_mlp_pack(pd_mlp* m, const float* X, const float* y, long long n, ui
 pd_status pd_mlp_forward(pd_mlp* m, const uint16_t* X, long long n, float* y)
 {
     if (!m) return PD_EINVAL;
-    if (!X || !y || n < 0) return mfail(m, PD_EINVAL, "null argument");
     if (n == 0) return PD_OK;
+    if (!X || !y || n < 0) return mfail(m, PD_EINVAL, "null argument");
     if ((n + 127) / 128 > (long long)INT32_MAX) return mfail(m, PD_EINVAL, "too many rows");
     CUtensorMap mx;
     if (!make_map(&mx, X, n, kInCols, kInCols, 128)) return mfail(m, PD_EINVAL, "input must be 16-byte aligned [n][128] BF16");

@@ -159,3 +159,19 @@ def test_autotuner_picks_a_configuration_and_keeps_results(Grid):
     g.step(V, 0.0, 0.0, 4)
     g.sync()
     np.testing.assert_array_equal(U.cpu().numpy(), V.cpu().numpy())
+
+
+def test_batch_with_a_single_patch_instance(Grid, orc):
+    """A 2 x 2 macro grid has one patch: one partial patch group and a
+    boundary chunk of eight nodes in the same queue as larger instances."""
+    probs = [W.base(n_xi=2, n_eta=2, m_xi=7, m_eta=7, init="bump"), _c4_subset(3)[2], _c4_subset(3)[0]]
+    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-4)):
+        g = Grid(probs, prec=prec)
+        U = g.init_field()
+        g.step(U, 0.0, 0.0, 4)
+        g.sync()
+        got = _split(g, U)
+        want = _oracle_runs(orc, probs, 4)
+        for k, (a, b) in enumerate(zip(got, want)):
+            err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+            assert err <= tol, (prec, k, err)

@@ -200,3 +200,15 @@ def test_device_initialisation(MLP):
         assert abs(th[i] - np.float32((2 * draw(i) - 1) * b)) <= 1e-7, i
     W1 = S.unflatten(th)["W1"]
     assert np.all(W1[:, 35:] == 0) and np.abs(W1).max() <= 1 / np.sqrt(35)
+
+
+def test_forward_of_zero_and_one_rows(MLP):
+    net = MLP(128)
+    th = _theta(2)
+    net.set_params(th)
+    X, Xh = _inputs(1, 9)
+    y = net.forward(X).cpu().numpy()
+    want, _ = S.forward(th.astype(np.float64), Xh, round_bf16=True)
+    assert abs(y[0] - want[0]) <= 1e-2 * abs(want[0]) + 1e-3
+    empty = torch.empty((0, 128), dtype=torch.bfloat16, device="cuda")
+    assert net.forward(empty).numel() == 0

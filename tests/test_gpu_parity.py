@@ -323,3 +323,32 @@ def test_invalid_calls_are_rejected(env, orc):
     U = g.new_field()
     with pytest.raises(N.PDError):
         g.lift(U, 0.0, st[1:])   # misaligned state buffer
+
+
+def test_largest_micro_patch_and_longest_burst(env, orc):
+    """The size limits of the descriptors: m = 32 (generic shared-memory
+    burst) and K = 4096 micro steps per burst, FP64 and FP32."""
+    big_m = W.base(n_xi=4, n_eta=3, m_xi=32, m_eta=32, k_micro=20, M=(0.7, 0.1, 1.1), va=(0.5, 0, 0),
+                   vb=(-0.4, 0, 0), f0=0.3, init="bump", n_macro=2)
+    long_k = W.base(n_xi=4, n_eta=4, m_xi=3, m_eta=3, k_micro=4096, cfl_micro=0.01, M=(0.7, 0.1, 1.1),
+                    va=(0.5, 0, 0), vb=(-0.4, 0, 0), f0=0.3, init="bump", n_macro=2)
+    for p in (big_m, long_k):
+        for prec, tol in (("fp64", 1e-12), ("fp32", 1e-4)):
+            got, want, _ = _run_both(env, orc, p, prec)
+            assert np.linalg.norm(got - want) / np.linalg.norm(want) <= tol, (p["m_xi"], p["k_micro"], prec)
+
+
+def test_zero_steps_and_empty_bursts_leave_the_state_alone(env, orc):
+    p = CASES["c2s"]
+    g = env(p, prec="fp32")
+    U = g.init_field()
+    U0 = U.clone()
+    g.step(U, 0.0, 1e-5, 0)
+    g.sync()
+    assert torch.equal(U, U0)
+    st = g.new_state()
+    g.lift(U, 0.0, st)
+    before = st.clone()
+    g.micro_burst(st, 0.0, 0)
+    g.sync()
+    assert torch.equal(st, before)
