@@ -207,6 +207,22 @@ pd_status pd_project(pd_grid* g, double* U_dev, const double* dU_dev, double t, 
 pd_status pd_step(pd_grid* g, double* U_dev, double t0, double dt_macro, int n_macro);
 pd_status pd_set_graph_mode(pd_grid* g, int enabled);
 
+/* Outer (projective) integrator of pd_step.  PD_INT_EULER is the paper's
+ * forward Euler, eq. (Extrapolation).  The paper names second-order
+ * Runge-Kutta and Adams-Bashforth outer integrators as the higher-order
+ * alternatives (Section 1); with F(U, T) = (U^1 - U^0)/tau from eq.
+ * (Time_Derivative):
+ *   PD_INT_HEUN: U* = U_n + dt F(U_n, T_n) (boundary data at T_{n+1}),
+ *                U_{n+1} = U_n + dt/2 (F(U_n, T_n) + F(U*, T_{n+1}));
+ *   PD_INT_AB2:  U_{n+1} = U_n + dt (3/2 F(U_n, T_n) - 1/2 F(U_{n-1}, T_{n-1})),
+ *                each pd_step call starting with one Heun step.
+ * The second-order integrators run one-instance grids with per-point records
+ * and m_xi == m_eta in {3,5,7,9,11} (PD_EINVAL otherwise), without graph
+ * capture or the persistent path: two fused kernels and one combination per
+ * Heun step, one restricted-change kernel and one update per AB2 step. */
+typedef enum { PD_INT_EULER = 0, PD_INT_HEUN = 1, PD_INT_AB2 = 2 } pd_integrator;
+pd_status pd_set_integrator(pd_grid* g, int kind);
+
 /* The same macro steps as pd_step with one fused kernel per step, for callers
  * that may not allocate device memory during a step.  The paper has no
  * counterpart; it is a deployment variant.  Such callers are, e.g., a

@@ -11,6 +11,7 @@ LIB_PATH = os.environ.get("PD_LIB_PATH") or os.path.join(HERE, "libpd.so")
 
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ECUDA, PD_ESTATE, PD_EUNSTABLE, PD_ETIMEOUT, PD_ENUMERIC = range(8)
 PD_FP64, PD_FP32 = 0, 1
+INTEGRATORS = {"euler": 0, "heun": 1, "ab2": 2}
 
 MAPS = {"identity": 0, "sine": 1, "tanh": 2, "polar": 3}
 CONV = {"upwind": 0, "central": 1}
@@ -78,6 +79,7 @@ SIGNATURES = {
     "pd_step_noalloc": (C.c_int, [_GP, _VP, C.c_double, C.c_double, C.c_int]),
     "pd_set_graph_mode": (C.c_int, [_GP, C.c_int]),
     "pd_set_persistent": (C.c_int, [_GP, C.c_int]),
+    "pd_set_integrator": (C.c_int, [_GP, C.c_int]),
     "pd_set_coeff_storage": (C.c_int, [_GP, C.c_int]),
     "pd_autotune": (C.c_int, [_GP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pd_set_autotune": (C.c_int, [_GP, C.c_int, C.c_int, C.c_int]),

@@ -73,7 +73,7 @@ class Grid:
     restriction and projection) or "fp64"."""
 
     def __init__(self, probs, prec: str = "fp32", graphs: bool = True, persistent: bool | None = None,
-                 storage: str = "auto", autotune: bool = True):
+                 storage: str = "auto", autotune: bool = True, integrator: str = "euler"):
         """persistent: None follows the PD_PERSISTENT environment variable (default on;
         "0" selects one fused launch per macro step, e.g. for kernel profilers that
         cannot replay cooperative launches)."""
@@ -96,6 +96,7 @@ class Grid:
         self.h = h
         self.L.pd_set_graph_mode(self.h, 1 if graphs else 0)
         self.L.pd_set_persistent(self.h, 1 if persistent else 0)
+        N.check(self.L.pd_set_integrator(self.h, N.INTEGRATORS[integrator]), self.h)
         N.check(self.L.pd_set_coeff_storage(self.h, {"auto": 0, "records": 1, "tables": 2}[storage]), self.h)
         if not autotune:
             N.check(self.L.pd_set_autotune(self.h, 0, 128, 0), self.h)

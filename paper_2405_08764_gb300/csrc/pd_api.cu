@@ -89,6 +89,10 @@ struct pd_grid {
     int* flags = nullptr;            // per-item-warp step counters (persistent kernel)
     size_t flags_n = 0;
     bool persist = true;
+    int integrator = PD_INT_EULER;   // outer (projective) integrator of pd_step
+    double* S2 = nullptr;            // second scratch field (Heun)
+    double* dUa = nullptr;           // per-patch restricted changes (AB2 history)
+    double* dUb = nullptr;
     long long wait_ns = 250000000LL;
     int silent_warp = -1;
     // batched execution (many instances or table-mode coefficients)
@@ -364,6 +368,53 @@ pd_status enqueue_steps(pd_grid* g, double* U, int n_macro, const std::vector<do
         tab_off += (size_t)n_macro * stride;
     }
     return PD_OK;
+}
+
+// pd_step with a second-order outer integrator: one instance, fused kernels
+pd_status step_higher(pd_grid* g, double* U, double t0, double dtm, int n_macro)
+{
+    Inst& s = g->inst[0];
+    const InstDev& I = s.I;
+    pd_status rc = ensure_step_buffers(g, n_macro + 1);
+    if (rc) return rc;
+    const size_t nf = (size_t)g->n_macro_total;
+    if (!g->S2) PD_CUDA(g, cudaMalloc(&g->S2, sizeof(double) * nf));
+    if (!g->dUa) {
+        PD_CUDA(g, cudaMalloc(&g->dUa, sizeof(double) * (size_t)g->n_patch_total));
+        PD_CUDA(g, cudaMalloc(&g->dUb, sizeof(double) * (size_t)g->n_patch_total));
+    }
+    cudaStream_t st = g->stream;
+    const int stride = I.K + kTabExtra;
+    PD_CUDA(g, launch_time_table(I, t0, dtm, n_macro + 1, g->tab, st));
+    int nl = 1;
+    auto row = [&](int k) { return g->tab + (size_t)k * stride; };
+    auto heun = [&](int k) -> pd_status {
+        cudaError_t e = launch_fused_step(I, nullptr, s.d.prec, U, g->U_scratch, row(k), dtm, st, &nl);
+        if (e == cudaSuccess) e = launch_fused_step(I, nullptr, s.d.prec, g->U_scratch, g->S2, row(k + 1), dtm, st, &nl);
+        if (e == cudaSuccess) { e = launch_heun_combine(I, U, g->U_scratch, g->S2, st); ++nl; }
+        if (e != cudaSuccess) return cuda_fail(g, e, "Heun step");
+        return PD_OK;
+    };
+    if (g->integrator == PD_INT_HEUN) {
+        for (int k = 0; k < n_macro && !rc; ++k) rc = heun(k);
+    } else {
+        // AB2: the history starts with the restricted change at T_0, the first step is Heun's
+        double* cur = g->dUb;
+        double* prev = g->dUa;
+        cudaError_t e = launch_patch_dU(I, s.d.prec, U, row(0), I.K, prev, nullptr, nullptr, st);
+        ++nl;
+        if (e != cudaSuccess) return cuda_fail(g, e, "AB2 history");
+        rc = heun(0);
+        for (int k = 1; k < n_macro && !rc; ++k) {
+            e = launch_patch_dU(I, s.d.prec, U, row(k), I.K, cur, nullptr, nullptr, st);
+            if (e == cudaSuccess) e = launch_ab2(I, U, cur, prev, t0 + k * dtm, dtm, st);
+            nl += 2;
+            if (e != cudaSuccess) return cuda_fail(g, e, "AB2 step");
+            std::swap(cur, prev);
+        }
+    }
+    g->launches += nl;
+    return rc;
 }
 
 pd_status step_fallback(pd_grid* g, double* U, double t0, const std::vector<double>& dtm, int n_macro)
@@ -758,6 +809,7 @@ pd_status pd_destroy_grid(pd_grid* g)
     for (auto e : g->tfree) cudaEventDestroy(e);
     for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.col_tab); cudaFree(s.row_tab); cudaFree(s.col_tab_f); cudaFree(s.row_tab_f); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
     cudaFree(g->err); cudaFree(g->acc); cudaFree(g->U_scratch); cudaFree(g->tab);
+    cudaFree(g->S2); cudaFree(g->dUa); cudaFree(g->dUb);
     cudaFree(g->state); cudaFree(g->dU); cudaFree(g->flags);
     cudaFree(g->insts_dev); cudaFree(g->items_dev); cudaFree(g->dtm_dev); cudaFree(g->tab_off_dev); cudaFree(g->counters);
     if (g->cap) cudaStreamDestroy(g->cap);
@@ -1009,6 +1061,12 @@ pd_status pd_step(pd_grid* g, double* U, double t0, double dt_macro, int n_macro
     cudaSetDevice(g->device);
     std::vector<double> dtm(g->inst.size());
     for (size_t k = 0; k < g->inst.size(); ++k) dtm[k] = dt_macro > 0 ? dt_macro : g->inst[k].dtm_sugg;
+    if (g->integrator != PD_INT_EULER) {
+        if (g->inst.size() != 1 || use_batch(g) || !fused_supported(g->inst[0].I))
+            return fail(g, PD_EINVAL, "second-order integrators need a grid of one instance with per-point records "
+                                      "and m_xi == m_eta in {3,5,7,9,11}");
+        return step_higher(g, U, t0, dtm[0], n_macro);
+    }
     if (use_batch(g)) {
         if (all_batch_supported(g)) return step_batch(g, U, t0, dtm, n_macro);
         return step_fallback(g, U, t0, dtm, n_macro);
@@ -1099,6 +1157,14 @@ pd_status pd_set_autotune(pd_grid* g, int enabled, int block, int half_patches)
     g->bt_half = half_patches != 0;
     g->bt_tuned = false;
     g->batch_dirty = true;
+    return PD_OK;
+}
+
+pd_status pd_set_integrator(pd_grid* g, int kind)
+{
+    if (!g) return PD_EINVAL;
+    if (kind != PD_INT_EULER && kind != PD_INT_HEUN && kind != PD_INT_AB2) return fail(g, PD_EINVAL, "unknown integrator");
+    g->integrator = kind;
     return PD_OK;
 }
 

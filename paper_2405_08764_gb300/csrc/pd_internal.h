@@ -408,6 +408,10 @@ void grid_count_launches(pd_grid* g, long long n);
 // for k_steps
 cudaError_t launch_patch_dU(const InstDev& I, int prec, const double* U, const double* tab_row, int k_steps,
                             double* dU, const int* list, const int* list_n, cudaStream_t st);
+// second-order outer integrators: Heun's combination and the AB2 update
+cudaError_t launch_heun_combine(const InstDev& I, double* U, const double* S1, const double* S2, cudaStream_t st);
+cudaError_t launch_ab2(const InstDev& I, double* U, const double* dUn, const double* dUp, double t, double dtm,
+                       cudaStream_t st);
 // per-patch basis T[p][10] of the one-micro-step restricted change over dt
 cudaError_t launch_one_step_basis(const InstDev& I, int prec, double* T, cudaStream_t st);
 // per-patch surrogate features that do not depend on U (10 per patch) and the

@@ -693,6 +693,61 @@ cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const
     return cudaGetLastError();
 }
 
+// Heun's combination: U_{n+1} = (U_n + S2)/2 on the interior nodes, with
+// S1 = U_n + dt F(U_n, T_n) (boundary data at T_{n+1}) and S2 = S1 + dt F(S1, T_{n+1});
+// the boundary nodes take S1's data at T_{n+1}.
+__global__ void heun_combine_kernel(const InstDev I, double* __restrict__ U, const double* __restrict__ S1,
+                                    const double* __restrict__ S2)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < I.n_patch) {
+        int i, j, ic, jr;
+        patch_ij(I, k, i, j, ic, jr);
+        const long long node = (long long)j * I.nxp + i;
+        U[node] = 0.5 * (U[node] + S2[node]);
+    } else if (k < I.n_patch + I.n_bnd) {
+        const int2 ij = I.bnd_ij[k - I.n_patch];
+        const long long node = (long long)ij.y * I.nxp + ij.x;
+        U[node] = S1[node];
+    }
+}
+
+// Adams-Bashforth-2: U += dt (3/2 dU_n - 1/2 dU_{n-1}) / tau on the interior,
+// Dirichlet data at t + dt on the boundary.
+__global__ void ab2_kernel(const InstDev I, double* __restrict__ U, const double* __restrict__ dUn,
+                           const double* __restrict__ dUp, double t_next, double dtm)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < I.n_patch) {
+        int i, j, ic, jr;
+        patch_ij(I, k, i, j, ic, jr);
+        const long long node = (long long)j * I.nxp + i;
+        const double d = 1.5 * dUn[(long long)I.p_off + k] - 0.5 * dUp[(long long)I.p_off + k];
+        if (!isfinite(d)) atomicOr(I.err, ERR_NONFINITE);
+        U[node] = U[node] + dtm * (d / I.tau);
+    } else if (k < I.n_patch + I.n_bnd) {
+        const int q = k - I.n_patch;
+        const int2 ij = I.bnd_ij[q];
+        const double2 xy = I.bnd_xy[q];
+        U[(long long)ij.y * I.nxp + ij.x] = exact_solution(I.sol, xy.x, xy.y, t_next);
+    }
+}
+
+cudaError_t launch_heun_combine(const InstDev& I, double* U, const double* S1, const double* S2, cudaStream_t st)
+{
+    const int n = I.n_patch + I.n_bnd;
+    heun_combine_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, U, S1, S2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ab2(const InstDev& I, double* U, const double* dUn, const double* dUp, double t, double dtm,
+                       cudaStream_t st)
+{
+    const int n = I.n_patch + I.n_bnd;
+    ab2_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, U, dUn, dUp, t + dtm, dtm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm, cudaStream_t st)
 {
     int n = I.n_patch + I.n_bnd;
