@@ -26,6 +26,7 @@ TIME = {"const": 0, "exp": 1, "sin": 2}
 SOL = {"none": 0, "exp_xyt": 1, "sinprod_decay": 2}
 INIT = {"zero": 0, "exact": 1, "bessel": 2, "bump": 3, "annulus_poly": 4}
 FORM = {"split": 0, "literal": 1}
+MICRO = {"fe": 0, "adi": 1}
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +62,7 @@ class Problem(C.Structure):
         ("src", C.c_int), ("src_p", C.c_double * 3), ("src_amp", C.POINTER(C.c_double)),
         ("tkind", C.c_int), ("tc", C.c_double),
         ("sol", C.c_int),
+        ("micro", C.c_int), ("dt_micro_fixed", C.c_double),
     ]
 
 
@@ -94,6 +96,7 @@ def lib():
                 "orc_step": (None, [_P, _D, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int]),
                 "orc_full_domain_size": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
                 "orc_full_domain": (None, [_P, C.c_int, _D, C.c_double, C.c_double, C.c_int]),
+                "orc_micro_patch": (None, [_P, C.c_int, _D, _D, C.c_double, C.c_int, C.c_double, _D]),
                 "orc_patch_dU": (None, [_P, _D, C.c_double, C.c_double, C.c_int, C.c_int,
                                         C.POINTER(C.c_int), _D]),
                 "orc_bessel_root": (C.c_double, [C.c_int, C.c_double, C.c_double, C.c_int]),
@@ -153,6 +156,8 @@ class Oracle:
             s.src_amp = _dp(self._amp)
         s.tkind, s.tc = TIME[p["time"]], float(p["tc"])
         s.sol = SOL[p["sol"]]
+        s.micro = MICRO[p.get("micro", "fe")]
+        s.dt_micro_fixed = float(p.get("dt_micro") or 0.0)
         self.s = s
         self.L = L
         rc = L.orc_validate(C.byref(s))
@@ -255,6 +260,20 @@ class Oracle:
         self.L.orc_step(C.byref(self.s), _dp(U), float(t0), float(dt_macro), int(n_steps),
                         float(dtm), FORM[form])
         return U
+
+    def micro_patch(self, p, w0, r, T, K, dt):
+        """Split-form micro solve of patch p alone from the departure w0 with
+        forcing r (None = 0); returns the departure after K steps."""
+        w0 = np.ascontiguousarray(w0, dtype=np.float64).reshape(-1)
+        assert w0.size == self.mx * self.my
+        out = np.zeros(self.mx * self.my)
+        rp = None
+        if r is not None:
+            r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+            assert r.size == self.mx * self.my
+            rp = _dp(r)
+        self.L.orc_micro_patch(C.byref(self.s), int(p), _dp(w0), rp, float(T), int(K), float(dt), _dp(out))
+        return out.reshape(self.my, self.mx)
 
     def patch_dU(self, U, t, sel, dt_micro=None, form="split"):
         U = np.ascontiguousarray(U, dtype=np.float64)

@@ -45,6 +45,8 @@ int orc_validate(const orc_problem* P)
     if (!(P->h_ratio_eta > 0.0 && P->h_ratio_eta < 1.0)) return 3;
     if (P->k_micro < 1) return 4;
     if (!(P->xi1 > P->xi0) || !(P->eta1 > P->eta0)) return 5;
+    if (P->micro != ORC_MICRO_FE && P->micro != ORC_MICRO_ADI) return 6;
+    if (!(P->dt_micro_fixed >= 0.0) || !isfinite(P->dt_micro_fixed)) return 6;
     return 0;
 }
 
@@ -364,6 +366,7 @@ static double rate_bound(const orc_problem* P, const double* c, double hx, doubl
 
 double orc_dt_micro(const orc_problem* P)
 {
+    if (P->dt_micro_fixed > 0.0) return P->dt_micro_fixed;
     int np = orc_n_patch(P);
     double rmax = 0.0;
     double* c = (double*)malloc(sizeof(double) * 7 * P->m_xi * P->m_eta);
@@ -612,6 +615,194 @@ static double trapezoid(const patch_geo* g, const double* u)
     return s / ((double)nx * ny);
 }
 
+/* ------------------------------------------------------------------------- */
+/* ADI micro solver.  Section 4.1 runs the micro simulations with an alternating
+   direction implicit scheme and two nano steps per burst but does not print
+   the scheme.  Reading: Peaceman-Rachford splitting of the micro operator of
+   op_at into line parts
+     Lx u = alpha u_xixi - nu u_xi + phi u / 2   (along xi),
+     Ly u = gamma u_etaeta - omega u_eta + phi u / 2   (along eta),
+     Lc u = beta u_xieta   (mixed part, always explicit),
+   with the same differences and ghost points as the explicit scheme, and the
+   source g taken at the middle of the step:
+     (I - dt/2 Lx) u*      = u^k + dt/2 (Ly u^k + Lc u^k + g(t_k + dt/2)),
+     (I - dt/2 Ly) u^{k+1} = u*  + dt/2 (Lx u* + Lc u* + g(t_k + dt/2)).
+   Each line operator is affine (the ghost points carry the edge data); it is
+   assembled column by column from its values on unit vectors, and each line
+   system is solved by Gaussian elimination with partial pivoting. */
+
+/* part dir of the micro operator at (a, b): 0 = Lx, 1 = Ly, 2 = Lc */
+static double op_part(const orc_problem* P, const patch_geo* g, const double* c,
+                      const double* u, int a, int b, int dir)
+{
+    int mx = g->mx;
+    double uc = EXT(u, a, b, mx);
+    if (dir == 0) {
+        double uE = EXT(u, a + 1, b, mx), uW = EXT(u, a - 1, b, mx);
+        double uxx = (uE - 2.0 * uc + uW) / (g->dx * g->dx);
+        double ux;
+        if (P->conv == ORC_CONV_CENTRAL) ux = (uE - uW) / (2.0 * g->dx);
+        else ux = c[3] > 0.0 ? (uc - uW) / g->dx : (uE - uc) / g->dx;
+        return c[0] * uxx - c[3] * ux + 0.5 * c[5] * uc;
+    }
+    if (dir == 1) {
+        double uN = EXT(u, a, b + 1, mx), uS = EXT(u, a, b - 1, mx);
+        double uyy = (uN - 2.0 * uc + uS) / (g->dy * g->dy);
+        double uy;
+        if (P->conv == ORC_CONV_CENTRAL) uy = (uN - uS) / (2.0 * g->dy);
+        else uy = c[4] > 0.0 ? (uc - uS) / g->dy : (uN - uc) / g->dy;
+        return c[2] * uyy - c[4] * uy + 0.5 * c[5] * uc;
+    }
+    double uxy = (EXT(u, a + 1, b + 1, mx) - EXT(u, a + 1, b - 1, mx)
+                - EXT(u, a - 1, b + 1, mx) + EXT(u, a - 1, b - 1, mx)) / (4.0 * g->dx * g->dy);
+    return c[1] * uxy;
+}
+
+/* ghost points of one line only (row b for dir 0, column a for dir 1), as in
+   fill_ghosts */
+static void line_ghosts(const patch_geo* g, const patch_edge* e, double* u, int dir, int line, int zero_data)
+{
+    int nx = g->mx - 1, ny = g->my - 1;
+    if (dir == 0) {
+        double gl = zero_data ? 0.0 : e->gL[line + 1];
+        double gr = zero_data ? 0.0 : e->gR[line + 1];
+        EXT(u, -1, line, g->mx) = EXT(u, 1, line, g->mx) - 2.0 * g->dx * gl;
+        EXT(u, nx + 1, line, g->mx) = EXT(u, nx - 1, line, g->mx) + 2.0 * g->dx * gr;
+    } else {
+        double gb = zero_data ? 0.0 : e->gB[line + 1];
+        double gt = zero_data ? 0.0 : e->gT[line + 1];
+        EXT(u, line, -1, g->mx) = EXT(u, line, 1, g->mx) - 2.0 * g->dy * gb;
+        EXT(u, line, ny + 1, g->mx) = EXT(u, line, ny - 1, g->mx) + 2.0 * g->dy * gt;
+    }
+}
+
+/* dense Gaussian elimination with partial pivoting: A (n x n, row-major) is
+   overwritten, x holds the right-hand side on entry and the solution on exit */
+static void solve_dense(int n, double* A, double* x)
+{
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(A[r * n + k]) > fabs(A[piv * n + k])) piv = r;
+        if (piv != k) {
+            for (int c = 0; c < n; ++c) {
+                double t = A[k * n + c]; A[k * n + c] = A[piv * n + c]; A[piv * n + c] = t;
+            }
+            double t = x[k]; x[k] = x[piv]; x[piv] = t;
+        }
+        for (int r = k + 1; r < n; ++r) {
+            double f = A[r * n + k] / A[k * n + k];
+            for (int c = k; c < n; ++c) A[r * n + c] -= f * A[k * n + c];
+            x[r] -= f * x[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double s = x[k];
+        for (int c = k + 1; c < n; ++c) s -= A[k * n + c] * x[c];
+        x[k] = s / A[k * n + k];
+    }
+}
+
+/* (I - h L_dir) x = rhs + h L_dir(0) on one line; rhs and the result are the
+   line's values of the [my][mx] array rhs and of the ghosted array out */
+static void line_solve(const orc_problem* P, const patch_geo* g, const patch_edge* e, const double* coef,
+                       int zero_data, int dir, int line, double h, const double* rhs, double* out,
+                       double* t)
+{
+    int mx = g->mx, n = dir == 0 ? g->mx : g->my;
+    double A[ORC_MAXM * ORC_MAXM], x[ORC_MAXM];
+    /* the constant part: the operator on the zero line with the edge data */
+    for (int q = 0; q < n; ++q) {
+        if (dir == 0) EXT(t, q, line, mx) = 0.0; else EXT(t, line, q, mx) = 0.0;
+    }
+    line_ghosts(g, e, t, dir, line, zero_data);
+    for (int q = 0; q < n; ++q) {
+        int a = dir == 0 ? q : line, b = dir == 0 ? line : q;
+        x[q] = rhs[b * mx + a] + h * op_part(P, g, coef + 7 * (b * mx + a), t, a, b, dir);
+    }
+    /* the linear part, column k from the unit vector e_k with zero edge data */
+    for (int k = 0; k < n; ++k) {
+        for (int q = 0; q < n; ++q) {
+            double v = q == k ? 1.0 : 0.0;
+            if (dir == 0) EXT(t, q, line, mx) = v; else EXT(t, line, q, mx) = v;
+        }
+        line_ghosts(g, e, t, dir, line, 1);
+        for (int q = 0; q < n; ++q) {
+            int a = dir == 0 ? q : line, b = dir == 0 ? line : q;
+            A[q * n + k] = (q == k ? 1.0 : 0.0) - h * op_part(P, g, coef + 7 * (b * mx + a), t, a, b, dir);
+        }
+    }
+    solve_dense(n, A, x);
+    for (int q = 0; q < n; ++q) {
+        if (dir == 0) EXT(out, q, line, mx) = x[q]; else EXT(out, line, q, mx) = x[q];
+    }
+}
+
+/* One ADI step from t_k of size dt on the ghosted array u (in/out).  Split
+   form (r0 != NULL): departure with zero edge data and forcing
+   r0 + (s(t) - s(T)) G; literal form: full field with the edge data and
+   forcing s(t) G.  us, rhs and t are scratch arrays. */
+static void adi_step(const orc_problem* P, const patch_geo* g, const patch_edge* e, const double* coef,
+                     double amp, const double* r0, double sT, double tk, double dt,
+                     double* u, double* us, double* rhs, double* t)
+{
+    int mx = g->mx, my = g->my;
+    int zero_data = r0 != NULL;
+    double h = 0.5 * dt;
+    double sm = orc_time_factor(P, tk + h);
+    /* first half step: explicit in eta and the mixed part, implicit along xi */
+    fill_ghosts(g, e, u, zero_data);
+    for (int b = 0; b < my; ++b)
+        for (int a = 0; a < mx; ++a) {
+            const double* c = coef + 7 * (b * mx + a);
+            double f = r0 ? r0[b * mx + a] + (sm - sT) * amp * c[6] : sm * amp * c[6];
+            rhs[b * mx + a] = EXT(u, a, b, mx)
+                + h * (op_part(P, g, c, u, a, b, 1) + op_part(P, g, c, u, a, b, 2) + f);
+        }
+    for (int b = 0; b < my; ++b) line_solve(P, g, e, coef, zero_data, 0, b, h, rhs, us, t);
+    /* second half step: explicit in xi and the mixed part, implicit along eta */
+    fill_ghosts(g, e, us, zero_data);
+    for (int b = 0; b < my; ++b)
+        for (int a = 0; a < mx; ++a) {
+            const double* c = coef + 7 * (b * mx + a);
+            double f = r0 ? r0[b * mx + a] + (sm - sT) * amp * c[6] : sm * amp * c[6];
+            rhs[b * mx + a] = EXT(us, a, b, mx)
+                + h * (op_part(P, g, c, us, a, b, 0) + op_part(P, g, c, us, a, b, 2) + f);
+        }
+    for (int a = 0; a < mx; ++a) line_solve(P, g, e, coef, zero_data, 1, a, h, rhs, u, t);
+}
+
+/* The split-form micro solve (departure w = u - u0 in the ghosted array u,
+   mirror ghosts, forcing r0 = L_h(u0) + s(T) G): K steps of forward Euler or
+   of the ADI scheme.  un is scratch of the same size. */
+static void micro_split(const orc_problem* P, const patch_geo* g, const patch_edge* e, const double* coef,
+                        double amp, const double* r0, double T, int K, double dt, double* u, double* un)
+{
+    int mx = g->mx, my = g->my, nx = mx - 1, ny = my - 1;
+    double sT = orc_time_factor(P, T);
+    if (P->micro == ORC_MICRO_ADI) {
+        int ne = (mx + 2) * (my + 2);
+        double* rhs = (double*)calloc((size_t)mx * my, sizeof(double));
+        double* t = (double*)calloc((size_t)ne, sizeof(double));
+        for (int k = 0; k < K; ++k) adi_step(P, g, e, coef, amp, r0, sT, T + k * dt, dt, u, un, rhs, t);
+        free(rhs); free(t);
+        return;
+    }
+    for (int k = 0; k < K; ++k) {
+        double tk = T + k * dt;
+        double dsk = orc_time_factor(P, tk) - sT;
+        fill_ghosts(g, e, u, 1);
+        for (int b = 0; b <= ny; ++b)
+            for (int a = 0; a <= nx; ++a) {
+                const double* c = coef + 7 * (b * mx + a);
+                EXT(un, a, b, mx) = EXT(u, a, b, mx)
+                    + dt * (op_at(P, g, c, u, a, b) + r0[b * mx + a] + dsk * amp * c[6]);
+            }
+        for (int b = 0; b <= ny; ++b)
+            for (int a = 0; a <= nx; ++a) EXT(u, a, b, mx) = EXT(un, a, b, mx);
+    }
+}
+
 /* One patch through S1-S4 (gap-tooth steps (i)-(iv)).  Returns dU = U^1 - U^0;
    optionally writes the burst result (w or u) and the lift / forcing. */
 typedef struct {
@@ -638,7 +829,13 @@ static double run_patch(const orc_problem* P, const double* U, int p, const doub
     double amp = (P->src == ORC_SRC_GAUSS_PATCH && P->src_amp) ? P->src_amp[p] : 1.0;
     double sT = orc_time_factor(P, T);
 
-    if (form == ORC_FORM_LITERAL) {
+    if (form == ORC_FORM_LITERAL && P->micro == ORC_MICRO_ADI) {
+        memcpy(u, u0, sizeof(double) * ne);
+        double* rhs = (double*)calloc((size_t)mx * my, sizeof(double));
+        double* t = (double*)calloc((size_t)ne, sizeof(double));
+        for (int k = 0; k < K; ++k) adi_step(P, &g, &e, coef, amp, NULL, sT, T + k * dt, dt, u, un, rhs, t);
+        free(rhs); free(t);
+    } else if (form == ORC_FORM_LITERAL) {
         memcpy(u, u0, sizeof(double) * ne);
         for (int k = 0; k < K; ++k) {
             double tk = T + k * dt;
@@ -662,19 +859,7 @@ static double run_patch(const orc_problem* P, const double* U, int p, const doub
                 const double* c = coef + 7 * (b * mx + a);
                 r0[b * mx + a] = op_at(P, &g, c, u0, a, b) + sT * amp * c[6];
             }
-        for (int k = 0; k < K; ++k) {
-            double tk = T + k * dt;
-            double dsk = orc_time_factor(P, tk) - sT;
-            fill_ghosts(&g, &e, u, 1);
-            for (int b = 0; b <= ny; ++b)
-                for (int a = 0; a <= nx; ++a) {
-                    const double* c = coef + 7 * (b * mx + a);
-                    EXT(un, a, b, mx) = EXT(u, a, b, mx)
-                        + dt * (op_at(P, &g, c, u, a, b) + r0[b * mx + a] + dsk * amp * c[6]);
-                }
-            for (int b = 0; b <= ny; ++b)
-                for (int a = 0; a <= nx; ++a) EXT(u, a, b, mx) = EXT(un, a, b, mx);
-        }
+        micro_split(P, &g, &e, coef, amp, r0, T, K, dt, u, un);
     }
 
     /* Restriction (step (iv)) and the reference value U^0 (reading G4):
@@ -901,6 +1086,30 @@ void orc_full_domain(const orc_problem* P, int refine, double* u, double t0, dou
         memcpy(u, un, sizeof(double) * n);
     }
     free(c); free(un);
+}
+
+void orc_micro_patch(const orc_problem* P, int p, const double* w0, const double* r, double T,
+                     int K, double dt, double* out)
+{
+    patch_geo g = patch_of(P, p);
+    int mx = g.mx, my = g.my, ne = (mx + 2) * (my + 2);
+    double* c = (double*)malloc(sizeof(double) * 7 * mx * my);
+    double* u = (double*)calloc((size_t)ne, sizeof(double));
+    double* un = (double*)calloc((size_t)ne, sizeof(double));
+    double* r0 = (double*)calloc((size_t)mx * my, sizeof(double));
+    patch_edge e;
+    memset(&e, 0, sizeof(e));
+    patch_coeffs(P, &g, c);
+    for (int b = 0; b < my; ++b)
+        for (int a = 0; a < mx; ++a) {
+            EXT(u, a, b, mx) = w0[b * mx + a];
+            if (r) r0[b * mx + a] = r[b * mx + a];
+        }
+    double amp = (P->src == ORC_SRC_GAUSS_PATCH && P->src_amp) ? P->src_amp[p] : 1.0;
+    micro_split(P, &g, &e, c, amp, r0, T, K, dt, u, un);
+    for (int b = 0; b < my; ++b)
+        for (int a = 0; a < mx; ++a) out[b * mx + a] = EXT(u, a, b, mx);
+    free(c); free(u); free(un); free(r0);
 }
 
 /* dU for a selection of patches only (sampled checks at full size) */

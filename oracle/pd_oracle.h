@@ -28,6 +28,7 @@ enum { ORC_TIME_CONST = 0, ORC_TIME_EXP = 1, ORC_TIME_SIN = 2 };
 enum { ORC_SOL_NONE = 0, ORC_SOL_EXP_XYT = 1, ORC_SOL_SINPROD_DECAY = 2 };
 enum { ORC_INIT_ZERO = 0, ORC_INIT_EXACT = 1, ORC_INIT_BESSEL = 2, ORC_INIT_BUMP = 3, ORC_INIT_ANNULUS_POLY = 4 };
 enum { ORC_FORM_SPLIT = 0, ORC_FORM_LITERAL = 1 };
+enum { ORC_MICRO_FE = 0, ORC_MICRO_ADI = 1 };
 
 /* One problem instance: geometry, micro discretisation and CDR coefficients. */
 typedef struct {
@@ -57,6 +58,10 @@ typedef struct {
     int tkind; double tc;
     /* exact solution used for Dirichlet data and errors */
     int sol;
+    /* micro time stepper: forward Euler (Section 4.2) or the ADI scheme of
+       Section 4.1; a positive dt_micro_fixed replaces the cfl rule (G8) */
+    int micro;
+    double dt_micro_fixed;
 } orc_problem;
 
 /* sizes */
@@ -113,6 +118,13 @@ void orc_step(const orc_problem* P, double* U, double t0, double dt_macro, int n
 int orc_full_domain_size(const orc_problem* P, int refine, int* nxf, int* nyf);
 void orc_full_domain(const orc_problem* P, int refine, double* u, double t0, double dt,
                      int n_steps);
+
+/* The micro solver of patch p alone in the split form: from the departure
+   w0 [m_eta][m_xi] (mirror ghosts, zero edge data) with the forcing r
+   [m_eta][m_xi] (NULL = 0) plus the source change (s(t) - s(T)) G, K steps of
+   dt from time T by P->micro (forward Euler or ADI); out = departure after K. */
+void orc_micro_patch(const orc_problem* P, int p, const double* w0, const double* r, double T,
+                     int K, double dt, double* out);
 
 /* dU for a selection of patches only (sampled checks at full size) */
 void orc_patch_dU(const orc_problem* P, const double* U, double t, double dt, int form,

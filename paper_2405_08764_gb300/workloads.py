@@ -17,6 +17,7 @@ Problem dictionary keys (all plain Python values or numpy arrays):
   time in {"const", "exp", "sin"}, tc
   sol in {"none", "exp_xyt", "sinprod_decay"}
   init in {"zero", "exact", "bessel", "bump", "annulus_poly"}, init_p (list of floats)
+  micro in {"fe", "adi"} (micro time stepper), dt_micro (float or None = cfl rule)
   dt_macro (float or None = suggested), n_macro, t0
 """
 from __future__ import annotations
@@ -45,6 +46,7 @@ def base(**kw) -> dict:
         va=(0.0, 0.0, 0.0), vb=(0.0, 0.0, 0.0), f0=0.0,
         src="none", src_p=(0.0, 0.0, 0.0), src_amp=None,
         time="const", tc=0.0, sol="none", init="zero", init_p=[],
+        micro="fe", dt_micro=None,
         dt_macro=None, n_macro=1, t0=0.0,
     )
     p.update(kw)
@@ -178,6 +180,16 @@ def paper_cdr(variable_d: bool, lam: float = 0.1, n: int = 10, m: int = 11,
         d_aff=d_aff, va=va, vb=(0.0, 0.0, 10.0), f0=20.0,
         src="exp_linear", src_p=src_p, time="exp", tc=1.0, sol="exp_xyt", init="exact",
     )
+
+
+def paper_cdr_adi(variable_d: bool, lam: float, n: int, n_t: int, restrict: str = "macro") -> dict:
+    """Section 4.1 at the paper's own patch settings: h = 1e-3 in the
+    computational box, n = 10 nano intervals, bursts of tau = 1e-6 made of
+    n_t = 2 ADI nano steps, N_t macro steps of 1 / N_t over [0, 1]; the
+    restriction reference is the macro value (eq. Time_Derivative as printed)."""
+    p = paper_cdr(variable_d, lam=lam, n=n, m=11, h_ratio=1e-3 * n, k_micro=2)
+    p.update(micro="adi", dt_micro=5e-7, restrict=restrict, dt_macro=1.0 / n_t, n_macro=n_t)
+    return p
 
 
 def paper_annulus(n_theta: int = 16, n_r: int = 10, m: int = 9, h_ratio: float = 0.2) -> dict:

@@ -151,10 +151,34 @@ def test_paper_tables_2_and_4(orc, variable_d, table):
     """Section 4.1 rerun with forward-Euler bursts at the tables' macro settings:
     max % error within a factor 1.5 of the printed value, lambda = 0.1 best."""
     g = GOLD[table]
-    got = [_max_pct_error(orc, W.paper_cdr(variable_d, lam=lam), 2000) for lam in g["lambda"]]
-    for mine, paper in zip(got, g["max_percent_error"]):
-        assert paper / 1.5 < mine < paper * 1.5, (got, g["max_percent_error"])
+    want = g["columns"][0]["max_percent_error"][:3]
+    got = [_max_pct_error(orc, W.paper_cdr(variable_d, lam=lam), 2000) for lam in g["lambda"][:3]]
+    for mine, paper in zip(got, want):
+        assert paper / 1.5 < mine < paper * 1.5, (got, want)
     assert got[1] < got[0] and got[1] < got[2]
+
+
+def _printed_unit(v):
+    """one unit in the last of the three printed significant digits"""
+    return 10.0 ** (math.floor(math.log10(abs(v))) - 2)
+
+
+@pytest.mark.parametrize("variable_d,table,lams", [(False, "table2_constant_diffusivity", (0.0, 0.1, 0.3, 0.6)),
+                                                   (True, "table4_variable_diffusivity", (0.0, 0.2, 0.5))])
+def test_paper_tables_reproduced_with_adi_bursts(orc, variable_d, table, lams):
+    """Section 4.1 at the paper's own micro settings (ADI, n_t = 2, tau = 1e-6,
+    h = 1e-3, n = 10) and the printed restriction reference: the 10 x 10,
+    N_t = 2000 column of Tables 2 and 4 to within one unit of the last printed
+    digit.  The tables' maximum is taken over the macro nodes at t = 1 (the
+    maximum over earlier times as well differs in the third digit at
+    lambda = 0.1)."""
+    g = GOLD[table]
+    col = g["columns"][0]
+    for lam in lams:
+        want = col["max_percent_error"][g["lambda"].index(lam)]
+        p = W.paper_cdr_adi(variable_d, lam, col["n"], col["n_t"])
+        got = _max_pct_error(orc, p, col["n_t"], chunks=1)
+        assert abs(got - want) <= _printed_unit(want), (lam, got, want)
 
 
 def test_paper_table7_annulus(orc):

@@ -9,7 +9,8 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PINS = ["tests/test_oracle_coeffs.py", "tests/test_oracle_scheme.py", "tests/test_oracle_bruteforce.py"]
+PINS = ["tests/test_oracle_coeffs.py", "tests/test_oracle_scheme.py", "tests/test_oracle_bruteforce.py",
+        "tests/test_oracle_adi.py"]
 
 MUTATIONS = {
     "cross_term_sign": ("- EXT(u, a + 1, b - 1, mx)\n                - EXT(u, a - 1, b + 1, mx)",
@@ -29,6 +30,18 @@ MUTATIONS = {
     "transposed_metric": ("double a[2] = { yb, -xb }, b[2] = { -ya, xa };",
                           "double a[2] = { yb, -xb }, b[2] = { -xa, ya };"),
     "periodic_wrap": ("return ((i % n) + n) % n;", "return i < 0 ? 0 : (i >= n ? n - 1 : i);"),
+    "adi_mixed_dropped": ("+ h * (op_part(P, g, c, u, a, b, 1) + op_part(P, g, c, u, a, b, 2) + f);",
+                          "+ h * (op_part(P, g, c, u, a, b, 1) + f);"),
+    "adi_full_half_step": ("double h = 0.5 * dt;\n    double sm", "double h = dt;\n    double sm"),
+    "adi_source_time": ("double sm = orc_time_factor(P, tk + h);", "double sm = orc_time_factor(P, tk);"),
+    "adi_reaction_split": ("return c[0] * uxx - c[3] * ux + 0.5 * c[5] * uc;",
+                           "return c[0] * uxx - c[3] * ux + c[5] * uc;"),
+    "adi_eta_upwind": ("else uy = c[4] > 0.0 ? (uc - uS) / g->dy : (uN - uc) / g->dy;",
+                       "else uy = c[4] < 0.0 ? (uc - uS) / g->dy : (uN - uc) / g->dy;"),
+    "adi_line_ghost_sign": ("EXT(u, -1, line, g->mx) = EXT(u, 1, line, g->mx) - 2.0 * g->dx * gl;",
+                            "EXT(u, -1, line, g->mx) = EXT(u, 1, line, g->mx) + 2.0 * g->dx * gl;"),
+    "adi_explicit_direction": ("+ h * (op_part(P, g, c, u, a, b, 1) + op_part(P, g, c, u, a, b, 2) + f);",
+                               "+ h * (op_part(P, g, c, u, a, b, 0) + op_part(P, g, c, u, a, b, 2) + f);"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }
