@@ -58,6 +58,15 @@ typedef enum { PD_MAP_IDENTITY = 0, PD_MAP_SINE = 1, PD_MAP_TANH = 2, PD_MAP_POL
 typedef enum { PD_FP64 = 0, PD_FP32 = 1 } pd_precision;
 typedef enum { PD_CONV_UPWIND = 0, PD_CONV_CENTRAL = 1 } pd_conv;
 typedef enum { PD_RESTRICT_LIFTED = 0, PD_RESTRICT_MACRO = 1 } pd_restrict_mode;
+/* Micro time stepper inside the patches: forward Euler (Section 4.2), or the
+ * alternating direction implicit scheme of Section 4.1, read as the
+ * Peaceman-Rachford splitting: with h = dt/2, Lx the xi part (alpha u_xixi -
+ * nu u_xi + phi u/2), Ly the eta part and Lc = beta u_xieta (explicit),
+ *   (I - h Lx) u* = u + h (Ly u + Lc u + g(t + h)),
+ *   (I - h Ly) u' = u* + h (Lx u* + Lc u* + g(t + h)),
+ * each line system tridiagonal with the ghost-point Neumann data.  Second
+ * order in dt when beta = 0, first order otherwise. */
+typedef enum { PD_MICRO_FE = 0, PD_MICRO_ADI = 1 } pd_micro_solver;
 typedef enum { PD_SRC_NONE = 0, PD_SRC_MMS_SINPROD = 1, PD_SRC_EXP_LINEAR = 2,
                PD_SRC_GAUSS_PATCH = 3 } pd_source;
 typedef enum { PD_TIME_CONST = 0, PD_TIME_EXP = 1, PD_TIME_SIN = 2 } pd_time_kind;
@@ -86,6 +95,12 @@ typedef struct {
     int prec;                     /* pd_precision of the micro burst */
     int conv_scheme;              /* pd_conv for the first derivatives */
     int restrict_mode;            /* pd_restrict_mode (reference value U^0 of eq. Time_Derivative) */
+    int micro_solver;             /* pd_micro_solver; ADI needs one instance with per-point
+                                     coefficients and m_xi == m_eta in {3,5,7,9,11} and runs
+                                     in pd_step (fused path, any outer integrator) */
+    double dt_micro;              /* > 0: fixed micro step (Section 4.1: tau / n_t), replacing
+                                     cfl_micro; forward Euler still needs dt within its
+                                     explicit bound (else PD_EUNSTABLE at pd_set_coeffs) */
 } pd_grid_desc;
 
 /* Coefficients of eq. (1), u_t = div(K grad u - v u) + f u + g, with
@@ -123,7 +138,7 @@ typedef struct {
     long long patch_offset;       /* offset (in patches) of this instance in dU_dev and the bias section */
     long long point_offset;       /* offset (in micro points) of this instance in the u0, r, w sections */
     long long edge_offset;        /* offset (in entries) of this instance in the edge section */
-    double dt_micro;              /* micro forward-Euler step (reading G8) */
+    double dt_micro;              /* micro step (cfl rule G8, or the descriptor's fixed step) */
     double tau;                   /* burst length K * dt_micro */
     double dt_macro_suggested;    /* half the macro explicit bound (reading G9) */
     size_t state_bytes;           /* whole micro-state buffer (all instances) */

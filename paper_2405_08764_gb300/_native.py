@@ -16,6 +16,7 @@ INTEGRATORS = {"euler": 0, "heun": 1, "ab2": 2}
 MAPS = {"identity": 0, "sine": 1, "tanh": 2, "polar": 3}
 CONV = {"upwind": 0, "central": 1}
 RESTRICT = {"lifted": 0, "macro": 1}
+MICRO = {"fe": 0, "adi": 1}
 SRC = {"none": 0, "mms_sinprod": 1, "exp_linear": 2, "gauss_patch": 3}
 TIME = {"const": 0, "exp": 1, "sin": 2}
 SOL = {"none": 0, "exp_xyt": 1, "sinprod_decay": 2}
@@ -31,6 +32,7 @@ class GridDesc(C.Structure):
         ("h_ratio_xi", C.c_double), ("h_ratio_eta", C.c_double),
         ("k_micro", C.c_int), ("cfl_micro", C.c_double),
         ("prec", C.c_int), ("conv_scheme", C.c_int), ("restrict_mode", C.c_int),
+        ("micro_solver", C.c_int), ("dt_micro", C.c_double),
     ]
 
 

@@ -31,6 +31,8 @@ def grid_desc(p: dict, prec: str) -> N.GridDesc:
     d.prec = N.PD_FP32 if prec == "fp32" else N.PD_FP64
     d.conv_scheme = N.CONV[p["conv"]]
     d.restrict_mode = N.RESTRICT[p["restrict"]]
+    d.micro_solver = N.MICRO[p.get("micro", "fe")]
+    d.dt_micro = float(p.get("dt_micro") or 0.0)
     return d
 
 

@@ -26,6 +26,8 @@ struct Inst {
     InstDev I;                       // host copy (pointers are device pointers)
     void* rec = nullptr;             // coefficient records
     void* brec = nullptr;            // burst records (weights, source, forcing basis)
+    void* arec_c = nullptr;          // ADI line records (eta lines, xi lines)
+    void* arec_r = nullptr;
     int2* bnd_ij = nullptr;
     double2* bnd_xy = nullptr;
     double* amp = nullptr;
@@ -141,7 +143,12 @@ bool valid_desc(const pd_grid_desc& d, std::string& why)
         why = "patch ratio h / Delta must lie in (0, 1)"; return false;
     }
     if (d.k_micro < 1 || d.k_micro > kMaxK) { why = "k_micro must be in [1, 4096]"; return false; }
-    if (!(d.cfl_micro > 0 && d.cfl_micro <= 1)) { why = "cfl_micro must be in (0, 1]"; return false; }
+    if (d.micro_solver != PD_MICRO_FE && d.micro_solver != PD_MICRO_ADI) { why = "unknown micro solver"; return false; }
+    if (!(d.dt_micro >= 0) || !std::isfinite(d.dt_micro)) { why = "dt_micro must be >= 0 and finite"; return false; }
+    if (d.dt_micro == 0 && !(d.cfl_micro > 0 && d.cfl_micro <= 1)) { why = "cfl_micro must be in (0, 1]"; return false; }
+    if (d.micro_solver == PD_MICRO_ADI && !(d.m_xi == d.m_eta && (d.m_xi == 3 || d.m_xi == 5 || d.m_xi == 7 || d.m_xi == 9 || d.m_xi == 11))) {
+        why = "the ADI micro solver needs m_xi == m_eta in {3,5,7,9,11}"; return false;
+    }
     if (!(d.xi1 > d.xi0) || !(d.eta1 > d.eta0)) { why = "empty computational box"; return false; }
     if (d.map < 0 || d.map > 3) { why = "unknown map"; return false; }
     if (d.prec != PD_FP32 && d.prec != PD_FP64) { why = "unknown precision"; return false; }
@@ -207,6 +214,7 @@ void fill_inst(Inst& s, long long u_off, long long p_off, long long pt_off, long
     I.i0 = I.periodic ? 0 : 1;
     I.mx = d.m_xi; I.my = d.m_eta; I.K = d.k_micro;
     I.conv = d.conv_scheme; I.restrict_mode = d.restrict_mode; I.map = d.map;
+    I.micro = d.micro_solver;
     I.n_patch = I.ncols * I.nrows;
     I.xi0 = d.xi0; I.xi1 = d.xi1; I.eta0 = d.eta0; I.eta1 = d.eta1;
     I.Dx = (d.xi1 - d.xi0) / d.n_xi;
@@ -329,7 +337,7 @@ pd_status enqueue_steps(pd_grid* g, double* U, int n_macro, const std::vector<do
         const InstDev& I = s.I;
         double* bufs[2] = { U + I.u_off, g->U_scratch + I.u_off };
         int stride = I.K + kTabExtra;
-        if (g->persist && persist_fits(I, s.d.prec)) {
+        if (g->persist && I.micro == PD_MICRO_FE && persist_fits(I, s.d.prec)) {
             int chunk = persist_max_steps(I, s.d.prec);
             for (int s0 = 0; s0 < n_macro; s0 += chunk) {
                 PersistArgs pa;
@@ -744,6 +752,10 @@ pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_strea
             delete g;
             return PD_EINVAL;
         }
+        if (n_inst > 1 && descs[k].micro_solver != PD_MICRO_FE) {   // ADI runs on one-instance grids
+            delete g;
+            return PD_EINVAL;
+        }
         g->inst[k].d = descs[k];
         fill_inst(g->inst[k], u_off, p_off, pt_off, e_off);
         u_off += (long long)g->inst[k].I.nxp * g->inst[k].I.nyp;
@@ -807,7 +819,7 @@ pd_status pd_destroy_grid(pd_grid* g)
     for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
     for (auto& pr : g->tev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto e : g->tfree) cudaEventDestroy(e);
-    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.col_tab); cudaFree(s.row_tab); cudaFree(s.col_tab_f); cudaFree(s.row_tab_f); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
+    for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.arec_c); cudaFree(s.arec_r); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.col_tab); cudaFree(s.row_tab); cudaFree(s.col_tab_f); cudaFree(s.row_tab_f); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
     cudaFree(g->err); cudaFree(g->acc); cudaFree(g->U_scratch); cudaFree(g->tab);
     cudaFree(g->S2); cudaFree(g->dUa); cudaFree(g->dUb);
     cudaFree(g->state); cudaFree(g->dU); cudaFree(g->flags);
@@ -855,7 +867,8 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     // per-point records
     bool tabular = c->dx == 0 && c->dy == 0 && c->ds == 0 && c->n_four == 0 && c->va[1] == 0 && c->va[2] == 0
                 && c->vb[1] == 0 && c->vb[2] == 0 && c->src == PD_SRC_NONE;
-    bool use_tables = tabular && (g->storage == 2 || (g->storage == 0 && g->inst.size() > 1));
+    bool use_tables = tabular && s.d.micro_solver == PD_MICRO_FE
+                   && (g->storage == 2 || (g->storage == 0 && g->inst.size() > 1));
     size_t es = s.d.prec == PD_FP32 ? 4 : 8;
     size_t npts = (size_t)s.I.n_patch * s.I.mx * s.I.my;
     if (use_tables) {
@@ -868,8 +881,8 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
         s.I.col_tab_f = s.col_tab_f; s.I.row_tab_f = s.row_tab_f;
         s.I.K11 = c->d0 * c->M11; s.I.K12 = c->d0 * c->M12; s.I.K22 = c->d0 * c->M22;
         s.I.v1 = c->va[0]; s.I.v2 = c->vb[0]; s.I.f0 = c->f0;
-        cudaFree(s.rec); cudaFree(s.brec);
-        s.rec = s.brec = nullptr;
+        cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.arec_c); cudaFree(s.arec_r);
+        s.rec = s.brec = s.arec_c = s.arec_r = nullptr;
     } else {
         s.I.coef_mode = COEF_RECORDS;
         if (!s.rec) {
@@ -877,8 +890,13 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
             if (ea == cudaSuccess) ea = cudaMalloc(&s.brec, npts * 16 * es);
             if (ea != cudaSuccess) return fail(g, ea == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA, "coefficient records");
         }
+        if (s.d.micro_solver == PD_MICRO_ADI && !s.arec_c) {
+            cudaError_t ea = cudaMalloc(&s.arec_c, npts * 8 * es);
+            if (ea == cudaSuccess) ea = cudaMalloc(&s.arec_r, npts * 8 * es);
+            if (ea != cudaSuccess) return fail(g, ea == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA, "ADI records");
+        }
     }
-    s.I.rec = s.rec; s.I.brec = s.brec;
+    s.I.rec = s.rec; s.I.brec = s.brec; s.I.arec_c = s.arec_c; s.I.arec_r = s.arec_r;
     g->batch_dirty = true;
     s.I.has_tsrc = (c->src != PD_SRC_NONE && c->tkind != PD_TIME_CONST) ? 1 : 0;
     PD_CUDA(g, cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long) * 4, g->stream));
@@ -899,7 +917,14 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     std::memcpy(&rate, &h[0], sizeof(double));
     std::memcpy(&mrate, &h[1], sizeof(double));
     if (!(rate > 0)) return fail(g, PD_EINVAL, "zero operator: no micro step bound");
-    s.dt = s.d.cfl_micro / rate;
+    if (s.d.dt_micro > 0) {
+        // fixed micro step; forward Euler must stay within its explicit bound
+        if (s.d.micro_solver == PD_MICRO_FE && s.d.dt_micro * rate > 1.0)
+            return fail(g, PD_EUNSTABLE, "dt_micro above the explicit forward-Euler bound");
+        s.dt = s.d.dt_micro;
+    } else {
+        s.dt = s.d.cfl_micro / rate;
+    }
     s.tau = s.d.k_micro * s.dt;
     s.dtm_sugg = mrate > 0 ? 0.5 / mrate : s.tau;
     s.I.dt = s.dt; s.I.tau = s.tau;
@@ -908,6 +933,10 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     if (!use_tables) {
         PD_CUDA(g, launch_burst_records(s.I, s.d.prec, s.brec, g->stream));
         g->launches += 1;
+        if (s.d.micro_solver == PD_MICRO_ADI) {
+            PD_CUDA(g, launch_adi_records(s.I, s.d.prec, s.arec_c, s.arec_r, g->stream));
+            g->launches += 1;
+        }
     }
     PD_CUDA(g, cudaStreamSynchronize(g->stream));
     // cross term present unless K^{xi eta} vanishes identically (orthogonal map, K = d m I,
@@ -939,7 +968,8 @@ pd_status pd_query(const pd_grid* gc, int inst, pd_info* o)
     o->dt_micro = s.dt; o->tau = s.tau; o->dt_macro_suggested = s.dtm_sugg;
     layout(g, s, *o);
     if (use_batch(g)) o->exec_path = all_batch_supported(g) ? 3 : 0;
-    else o->exec_path = !fused_supported(s.I) ? 0 : (g->persist && s.coef_set && persist_fits(s.I, s.d.prec)) ? 2 : 1;
+    else o->exec_path = !fused_supported(s.I) ? 0
+                      : (g->persist && s.coef_set && s.I.micro == PD_MICRO_FE && persist_fits(s.I, s.d.prec)) ? 2 : 1;
     o->chunk_steps = o->exec_path == 2 ? persist_max_steps(s.I, s.d.prec) : 1;
     return PD_OK;
 }
@@ -1012,6 +1042,8 @@ pd_status pd_micro_burst(pd_grid* g, void* state, double t, int k_steps)
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
     if (k_steps == 0) return PD_OK;
+    for (auto& s : g->inst)
+        if (s.I.micro != PD_MICRO_FE) return fail(g, PD_EINVAL, "the ADI micro solver runs inside pd_step only");
     for (auto& s : g->inst) {
         pd_info lay;
         layout(g, s, lay);

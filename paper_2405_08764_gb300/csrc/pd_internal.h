@@ -61,6 +61,9 @@ struct InstDev {
     // reciprocals of the nano steps (division-free stencil weights)
     double inv_dx, inv_dy, inv_dx2, inv_dy2, inv_4dxdy;
     int ppw;                     // patches per warp in the batched kernel (<= 32 / mx)
+    int micro;                   // pd_micro_solver
+    const void* arec_c;          // ADI line records, eta lines (8 per point, see pd_adi.cu)
+    const void* arec_r;          // ADI line records, xi lines (8 per point, patch-transposed)
 };
 
 enum CoefMode { COEF_RECORDS = 0, COEF_SEPARABLE = 1, COEF_POLAR = 2 };
@@ -406,6 +409,13 @@ void grid_count_launches(pd_grid* g, long long n);
 // restricted change of every patch (or of the *list_n patches of list) after
 // k_steps micro steps from the lift of U; tab_row is a time-table row built
 // for k_steps
+// ADI micro solver (pd_adi.cu): line records once per pd_set_coeffs, and the
+// fused macro step / restricted change with ADI bursts
+cudaError_t launch_adi_records(const InstDev& I, int prec, void* arec_c, void* arec_r, cudaStream_t st);
+cudaError_t launch_adi_fused(const InstDev& I, int prec, const double* Uc, double* Un, const double* tab_row,
+                             double dtm, cudaStream_t st);
+cudaError_t launch_adi_dU(const InstDev& I, int prec, const double* U, const double* tab_row, double* dU,
+                          const int* list, const int* list_n, cudaStream_t st);
 cudaError_t launch_patch_dU(const InstDev& I, int prec, const double* U, const double* tab_row, int k_steps,
                             double* dU, const int* list, const int* list_n, cudaStream_t st);
 // second-order outer integrators: Heun's combination and the AB2 update

@@ -561,6 +561,10 @@ bool fused_supported(const InstDev& I)
 cudaError_t launch_patch_dU(const InstDev& I, int prec, const double* U, const double* tab_row, int k_steps,
                             double* dU, const int* list, const int* list_n, cudaStream_t st)
 {
+    if (I.micro == PD_MICRO_ADI) {
+        if (k_steps != I.K) return cudaErrorInvalidValue;   // ADI bursts always run the instance's K steps
+        return launch_adi_dU(I, prec, U, tab_row, dU, list, list_n, st);
+    }
     if (prec == PD_FP32)
         return dispatch_m<float, MODE_DU>(I, U, nullptr, tab_row, 0.0, k_steps, nullptr, nullptr, st, dU, list, list_n);
     return dispatch_m<double, MODE_DU>(I, U, nullptr, tab_row, 0.0, k_steps, nullptr, nullptr, st, dU, list, list_n);
@@ -611,6 +615,7 @@ cudaError_t launch_fused_step(const InstDev& I, const InstDev*, int prec, const 
                               const double* tab_row, double dtm, cudaStream_t st, int* n_launch)
 {
     if (n_launch) ++*n_launch;
+    if (I.micro == PD_MICRO_ADI) return launch_adi_fused(I, prec, Uc, Un, tab_row, dtm, st);
     if (prec == PD_FP32)
         return dispatch_m<float, MODE_FUSED>(I, Uc, Un, tab_row, dtm, 0, nullptr, nullptr, st);
     return dispatch_m<double, MODE_FUSED>(I, Uc, Un, tab_row, dtm, 0, nullptr, nullptr, st);

@@ -421,7 +421,9 @@ __global__ void table_get_coeffs_kernel(const InstDev I, double* __restrict__ ou
 }
 
 // row s: ds_k = s(T + k dt) - s(T) (k < K), s(T), T, T_next with T = t0 + s dtm
-__global__ void time_table_kernel(int K, int tkind, double tc, double dt, double t0, double dtm,
+// koff = 0: s(t_k) - s(T) at the start of forward-Euler step k; koff = 1/2:
+// at the middle of ADI step k
+__global__ void time_table_kernel(int K, int tkind, double tc, double dt, double koff, double t0, double dtm,
                                   int n_steps, double* tab)
 {
     int stride = K + kTabExtra;
@@ -430,7 +432,7 @@ __global__ void time_table_kernel(int K, int tkind, double tc, double dt, double
     int s = (int)(idx / stride), k = (int)(idx % stride);
     double T = t0 + s * dtm;
     double v;
-    if (k < K) v = time_factor(tkind, tc, T + k * dt) - time_factor(tkind, tc, T);
+    if (k < K) v = time_factor(tkind, tc, T + (k + koff) * dt) - time_factor(tkind, tc, T);
     else if (k == K) v = time_factor(tkind, tc, T);
     else if (k == K + 1) v = T;
     else v = t0 + (s + 1) * dtm;
@@ -580,7 +582,8 @@ cudaError_t launch_init_field(const InstDev& I, const pd_coeff_desc& c, int kind
 cudaError_t launch_time_table(const InstDev& I, double t0, double dtm, int n_steps, double* tab, cudaStream_t st)
 {
     long long n = (long long)n_steps * (I.K + kTabExtra);
-    time_table_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(I.K, I.tkind, I.tc, I.dt, t0, dtm, n_steps, tab);
+    time_table_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(I.K, I.tkind, I.tc, I.dt,
+                                                                 I.micro == PD_MICRO_ADI ? 0.5 : 0.0, t0, dtm, n_steps, tab);
     return cudaGetLastError();
 }
 

@@ -288,10 +288,11 @@ pd_status pd_surrogate_create(pd_grid* g, pd_mlp* m, pd_surrogate** out)
     if (rc) { delete s; return rc; }
     const InstDev& I = s->ga.I;
     if (s->ga.n_inst != 1) { delete s; grid_message(g, "the surrogate takes a grid of one instance"); return PD_EINVAL; }
-    if (I.coef_mode != COEF_RECORDS || !fused_supported(I) || I.restrict_mode != PD_RESTRICT_LIFTED) {
+    if (I.coef_mode != COEF_RECORDS || !fused_supported(I) || I.restrict_mode != PD_RESTRICT_LIFTED
+        || I.micro != PD_MICRO_FE) {
         delete s;
-        grid_message(g, "the surrogate needs per-point coefficient records, m_xi == m_eta in {3,5,7,9,11} and the "
-                        "lifted restriction");
+        grid_message(g, "the surrogate needs per-point coefficient records, m_xi == m_eta in {3,5,7,9,11}, the "
+                        "lifted restriction and forward-Euler micro steps");
         return PD_EINVAL;
     }
     s->n = I.n_patch;
