@@ -463,6 +463,129 @@ def run_passes(args):
     return 0
 
 
+def run_adi(args):
+    """Section 4.1.1 at the paper's patch settings (h = 1e-3, n = 10 nano
+    intervals, bursts of tau = 1e-6 made of n_t = 2 ADI steps, lambda = 0.1) on
+    an N x N macro grid, FP32 bursts: one bench step = 20 macro steps through
+    pd_step (one ADI kernel per macro step, graph-captured), L2 flushed between
+    steps.  Beside it the same bursts made of forward-Euler steps (K = tau / dt
+    at the explicit bound) on the same grid."""
+    import numpy as np
+    import torch
+
+    from paper_2405_08764_gb300 import workloads as W
+    from paper_2405_08764_gb300.api import Grid
+
+    torch.cuda.set_device(0)
+    n = args.adi_n
+    p = W.paper_cdr_adi(False, 0.1, n, 2000)
+    g = Grid(p, prec=args.prec)
+    info = g.info()
+    P, m, K = info["n_patch"], info["m_xi"], info["k_micro"]
+    pts = P * m * m
+    n_macro = 20
+    dtm = info["dt_macro_suggested"]
+    es = 4 if args.prec == "fp32" else 8
+    U0 = g.init_field()
+    U = U0.clone()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run(grid, steps, warm):
+        for _ in range(warm):
+            U.copy_(U0)
+            grid.step(U, 0.0, dtm, n_macro)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        l0 = grid.launches()
+        for s in range(steps):
+            U.copy_(U0)
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            grid.step(U, 0.0, dtm, n_macro)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev), grid.launches() - l0
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    ms, launches = run(g, args.steps, args.warmup)
+    clocks = sampler.stop()
+    U_adi = U.clone()
+    value = pts * K * n_macro * args.steps / (ms / 1e3)
+    # forward-Euler bursts of the same length tau
+    probe = Grid(dict(p, micro="fe", dt_micro=None, k_micro=1, cfl_micro=1.0), prec=args.prec)
+    k_fe = int(math.ceil(info["tau"] / probe.info()["dt_micro"]))
+    del probe
+    gf = Grid(dict(p, micro="fe", dt_micro=info["tau"] / k_fe, k_micro=k_fe), prec=args.prec)
+    fe_steps = max(1, min(3, args.steps))
+    ms_fe, _ = run(gf, fe_steps, 1)
+    diff = (torch.linalg.norm(U - U_adi) / torch.linalg.norm(U)).item()
+    del gf
+    # end to end through the public API: host field in, host field out, every step
+    Uh = U0.cpu().pin_memory()
+    Uo = torch.empty_like(Uh).pin_memory()
+    e2e_steps = max(1, args.steps // 2)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        U.copy_(Uh, non_blocking=True)
+        g.step(U, 0.0, dtm, n_macro)
+        Uo.copy_(U, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e = pts * K * n_macro * e2e_steps / (time.perf_counter() - t)
+    nbytes = U0.numel() * 8
+    pk = peaks()
+    kern_s = ms / 1e3 / (args.steps * n_macro)
+    # per micro point: the forcing basis of the burst record (12 values) once,
+    # the eta-line and xi-line records (2 x 8 values) in every ADI step; per
+    # patch the macro value out (the 3 x 3 stencil reads hit L2)
+    bytes_launch = pts * (12 * es + 16 * es * K) + P * 16
+    achieved = bytes_launch / kern_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "Section 4.1.1 (lambda = 0.1) at the paper's patch settings on a %dx%d macro grid: "
+                               "%d patches x %dx%d micro points, ADI bursts of %d steps (tau = %.3g), "
+                               "%d macro steps per step" % (n, n, P, m, m, K, info["tau"], n_macro),
+                   "point_updates_per_step": pts * K * n_macro,
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "macro_steps_per_s": n_macro * args.steps / (ms / 1e3),
+        "forward_euler_same_tau": {"k_micro": k_fe, "ms_per_macro_step": ms_fe / (fe_steps * n_macro),
+                                   "adi_speedup": (ms_fe / fe_steps) / (ms / args.steps),
+                                   "rel_l2_adi_vs_fe_after_20_steps": diff},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "patch_adi_kernel<11,-,tsrc,%s,fused> (one macro step per launch)"
+                               % ("float" if es == 4 else "double"),
+                     "bytes_per_launch": bytes_launch, "kernel_ms_per_macro_step": 1e3 * kern_s,
+                     "peak_source": "%s hbm_gbs" % pk["source"]},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        o = oracle.Oracle(p)
+        Uc = U0.cpu().numpy()
+        sel = np.random.default_rng(0).choice(o.n_patch, size=min(2000, o.n_patch), replace=False)
+        t = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t < 10.0:
+            o.patch_dU(Uc, 0.0, sel)
+            reps += 1
+        el = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": reps * len(sel) * m * m * K / el, "unit": UNIT,
+                                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                                "kind": "oracle",
+                                "sample": "ADI bursts of %d random patches, %d repetitions (%.1f s)"
+                                          % (len(sel), reps, el)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -609,10 +732,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "passes"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "passes", "adi"],
                     help="c2: the benchmark workload (default); c4: the 4096-instance batch; "
                          "c5: the surrogate against the plain scheme on the 512x2048 annulus; "
-                         "passes: the separate C-ABI passes on that annulus")
+                         "passes: the separate C-ABI passes on that annulus; "
+                         "adi: ADI bursts at the paper's Section 4.1 patch settings")
+    ap.add_argument("--adi-n", type=int, default=400, help="adi: macro intervals per side")
     ap.add_argument("--epochs", type=int, default=80, help="c5: training epochs")
     ap.add_argument("--c5-grid", default="511x2048", help="c5: radial intervals x angular nodes")
     ap.add_argument("--batch", type=int, default=2048, help="c5: training minibatch")
@@ -629,6 +754,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "passes":
         return run_passes(args)
+    if args.workload == "adi":
+        return run_adi(args)
     return run_gpu(args)
 
 
