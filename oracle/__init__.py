@@ -63,6 +63,7 @@ class Problem(C.Structure):
         ("tkind", C.c_int), ("tc", C.c_double),
         ("sol", C.c_int),
         ("micro", C.c_int), ("dt_micro_fixed", C.c_double),
+        ("q_refresh", C.c_int),
     ]
 
 
@@ -158,6 +159,7 @@ class Oracle:
         s.sol = SOL[p["sol"]]
         s.micro = MICRO[p.get("micro", "fe")]
         s.dt_micro_fixed = float(p.get("dt_micro") or 0.0)
+        s.q_refresh = int(p.get("q_refresh") or 1)
         self.s = s
         self.L = L
         rc = L.orc_validate(C.byref(s))

@@ -47,6 +47,8 @@ int orc_validate(const orc_problem* P)
     if (!(P->xi1 > P->xi0) || !(P->eta1 > P->eta0)) return 5;
     if (P->micro != ORC_MICRO_FE && P->micro != ORC_MICRO_ADI) return 6;
     if (!(P->dt_micro_fixed >= 0.0) || !isfinite(P->dt_micro_fixed)) return 6;
+    if (P->q_refresh < 0 || (P->q_refresh > 1 && (P->k_micro % P->q_refresh != 0 || P->micro != ORC_MICRO_FE)))
+        return 7;
     return 0;
 }
 
@@ -998,8 +1000,115 @@ void orc_project(const orc_problem* P, double* U, const double* dU, double t, do
     orc_apply_bc(P, U, t + dtm);
 }
 
+/* Q > 1: the burst is cut into Q sub-bursts of K/Q forward-Euler steps.
+   Section 3 keeps the edge data fixed over the whole burst (the Q = 1 case of
+   the patch schemes it cites) and names refreshing them as the more accurate
+   alternative.  Reading: before sub-burst q >= 1 the edge data of every patch
+   are rebuilt by eq. (edge) from the macro estimate V_q, which is U plus each
+   patch's restricted change of the departure so far on the interior nodes and
+   the Dirichlet data at the sub-burst's start time T + q (K/Q) dt on the
+   boundary nodes; the micro field goes on from its current state (no new
+   lift).  In the split form the departure's ghost points carry the difference
+   between the new and the lifted edge data.  The restricted change that
+   enters the projection is that of the whole burst (plus the MACRO bias). */
+static void step_refresh(const orc_problem* P, double* U, double t0, double dtm, int n_steps, double dt, int form)
+{
+    int np = orc_n_patch(P), mx = P->m_xi, my = P->m_eta, mm = mx * my, nx = mx - 1, ny = my - 1;
+    int ne = (mx + 2) * (my + 2), Q = P->q_refresh, Ks = P->k_micro / Q;
+    int nmac = orc_n_macro(P), nxp = n_xpts(P);
+    double tau = P->k_micro * dt;
+    double* coef = all_coeffs(P);
+    double* u = (double*)calloc((size_t)np * ne, sizeof(double));
+    double* u0 = (double*)calloc((size_t)np * ne, sizeof(double));
+    double* r0 = (double*)calloc((size_t)np * mm, sizeof(double));
+    patch_edge* e0 = (patch_edge*)calloc((size_t)np, sizeof(patch_edge));
+    double* dR = (double*)calloc((size_t)np, sizeof(double));
+    double* V = (double*)malloc(sizeof(double) * nmac);
+    for (int s = 0; s < n_steps; ++s) {
+        double T = t0 + s * dtm;
+        double sT = orc_time_factor(P, T);
+        #pragma omp parallel for schedule(static)
+        for (int p = 0; p < np; ++p) {
+            patch_geo g = patch_of(P, p);
+            double* up = u + (size_t)p * ne;
+            double* u0p = u0 + (size_t)p * ne;
+            const double* c = coef + (size_t)7 * mm * p;
+            double amp = (P->src == ORC_SRC_GAUSS_PATCH && P->src_amp) ? P->src_amp[p] : 1.0;
+            memset(up, 0, sizeof(double) * ne);
+            memset(u0p, 0, sizeof(double) * ne);
+            edge_data(P, U, &g, &e0[p]);
+            lift_patch(&g, &e0[p], u0p);
+            fill_ghosts(&g, &e0[p], u0p, 0);
+            for (int b = 0; b < my; ++b)
+                for (int a = 0; a < mx; ++a) {
+                    r0[(size_t)p * mm + b * mx + a] = op_at(P, &g, c + 7 * (b * mx + a), u0p, a, b) + sT * amp * c[7 * (b * mx + a) + 6];
+                    if (form == ORC_FORM_LITERAL) EXT(up, a, b, mx) = EXT(u0p, a, b, mx);
+                }
+            dR[p] = 0.0;
+        }
+        for (int q = 0; q < Q; ++q) {
+            double Tq = T + q * Ks * dt;
+            /* the macro estimate at the start of sub-burst q */
+            memcpy(V, U, sizeof(double) * nmac);
+            if (q > 0) {
+                for (int p = 0; p < np; ++p) {
+                    patch_geo g = patch_of(P, p);
+                    V[g.j * nxp + g.i] = U[g.j * nxp + g.i] + dR[p];
+                }
+                orc_apply_bc(P, V, Tq);
+            }
+            #pragma omp parallel for schedule(static)
+            for (int p = 0; p < np; ++p) {
+                patch_geo g = patch_of(P, p);
+                double* up = u + (size_t)p * ne;
+                double* un = (double*)calloc((size_t)ne, sizeof(double));
+                const double* c = coef + (size_t)7 * mm * p;
+                double amp = (P->src == ORC_SRC_GAUSS_PATCH && P->src_amp) ? P->src_amp[p] : 1.0;
+                patch_edge eq;
+                edge_data(P, V, &g, &eq);
+                if (form == ORC_FORM_SPLIT) {
+                    /* ghost data of the departure: new minus lifted edge data */
+                    for (int k = 0; k < ORC_MAXM + 2; ++k) {
+                        eq.gL[k] -= e0[p].gL[k]; eq.gR[k] -= e0[p].gR[k];
+                        eq.gB[k] -= e0[p].gB[k]; eq.gT[k] -= e0[p].gT[k];
+                    }
+                }
+                for (int k = 0; k < Ks; ++k) {
+                    double tk = Tq + k * dt;
+                    fill_ghosts(&g, &eq, up, 0);
+                    for (int b = 0; b <= ny; ++b)
+                        for (int a = 0; a <= nx; ++a) {
+                            const double* cc = c + 7 * (b * mx + a);
+                            double f = form == ORC_FORM_SPLIT
+                                ? r0[(size_t)p * mm + b * mx + a] + (orc_time_factor(P, tk) - sT) * amp * cc[6]
+                                : orc_time_factor(P, tk) * amp * cc[6];
+                            EXT(un, a, b, mx) = EXT(up, a, b, mx) + dt * (op_at(P, &g, cc, up, a, b) + f);
+                        }
+                    for (int b = 0; b <= ny; ++b)
+                        for (int a = 0; a <= nx; ++a) EXT(up, a, b, mx) = EXT(un, a, b, mx);
+                }
+                free(un);
+                /* restricted change of the departure so far */
+                dR[p] = form == ORC_FORM_SPLIT ? trapezoid(&g, up) : trapezoid(&g, up) - trapezoid(&g, u0 + (size_t)p * ne);
+            }
+        }
+        for (int p = 0; p < np; ++p) {
+            patch_geo g = patch_of(P, p);
+            double d = dR[p];
+            if (P->restrict_mode == ORC_RESTRICT_MACRO) d += trapezoid(&g, u0 + (size_t)p * ne) - U[g.j * nxp + g.i];
+            U[g.j * nxp + g.i] = U[g.j * nxp + g.i] + dtm * (d / tau);
+        }
+        orc_apply_bc(P, U, t0 + (s + 1) * dtm);
+    }
+    free(coef); free(u); free(u0); free(r0); free(e0); free(dR); free(V);
+}
+
 void orc_step(const orc_problem* P, double* U, double t0, double dtm, int n_steps, double dt, int form)
 {
+    if (P->q_refresh > 1) {
+        step_refresh(P, U, t0, dtm, n_steps, dt, form);
+        return;
+    }
     int np = orc_n_patch(P), mm = P->m_xi * P->m_eta;
     double* coef = all_coeffs(P);
     double* dU = (double*)malloc(sizeof(double) * np);

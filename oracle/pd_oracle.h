@@ -62,6 +62,9 @@ typedef struct {
        Section 4.1; a positive dt_micro_fixed replaces the cfl rule (G8) */
     int micro;
     double dt_micro_fixed;
+    /* Q: edge data refreshed Q times per burst (Q = 1 or 0: fixed over the
+       burst, Section 3); Q > 1 needs k_micro divisible by Q and forward Euler */
+    int q_refresh;
 } orc_problem;
 
 /* sizes */

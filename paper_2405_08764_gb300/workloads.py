@@ -18,6 +18,7 @@ Problem dictionary keys (all plain Python values or numpy arrays):
   sol in {"none", "exp_xyt", "sinprod_decay"}
   init in {"zero", "exact", "bessel", "bump", "annulus_poly"}, init_p (list of floats)
   micro in {"fe", "adi"} (micro time stepper), dt_micro (float or None = cfl rule)
+  q_refresh (edge data refreshed q times per burst, 1 = fixed)
   dt_macro (float or None = suggested), n_macro, t0
 """
 from __future__ import annotations
@@ -46,7 +47,7 @@ def base(**kw) -> dict:
         va=(0.0, 0.0, 0.0), vb=(0.0, 0.0, 0.0), f0=0.0,
         src="none", src_p=(0.0, 0.0, 0.0), src_amp=None,
         time="const", tc=0.0, sol="none", init="zero", init_p=[],
-        micro="fe", dt_micro=None,
+        micro="fe", dt_micro=None, q_refresh=1,
         dt_macro=None, n_macro=1, t0=0.0,
     )
     p.update(kw)

@@ -10,7 +10,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = ["tests/test_oracle_coeffs.py", "tests/test_oracle_scheme.py", "tests/test_oracle_bruteforce.py",
-        "tests/test_oracle_adi.py"]
+        "tests/test_oracle_adi.py", "tests/test_oracle_refresh.py"]
 
 MUTATIONS = {
     "cross_term_sign": ("- EXT(u, a + 1, b - 1, mx)\n                - EXT(u, a - 1, b + 1, mx)",
@@ -42,6 +42,13 @@ MUTATIONS = {
                             "EXT(u, -1, line, g->mx) = EXT(u, 1, line, g->mx) + 2.0 * g->dx * gl;"),
     "adi_explicit_direction": ("+ h * (op_part(P, g, c, u, a, b, 1) + op_part(P, g, c, u, a, b, 2) + f);",
                                "+ h * (op_part(P, g, c, u, a, b, 0) + op_part(P, g, c, u, a, b, 2) + f);"),
+    "refresh_stale_estimate": ("V[g.j * nxp + g.i] = U[g.j * nxp + g.i] + dR[p];",
+                               "V[g.j * nxp + g.i] = U[g.j * nxp + g.i];"),
+    "refresh_boundary_time": ("orc_apply_bc(P, V, Tq);", "orc_apply_bc(P, V, T);"),
+    "refresh_subburst_time": ("double tk = Tq + k * dt;\n                    fill_ghosts(&g, &eq, up, 0);",
+                              "double tk = T + k * dt;\n                    fill_ghosts(&g, &eq, up, 0);"),
+    "refresh_split_ghost_data": ("eq.gL[k] -= e0[p].gL[k]; eq.gR[k] -= e0[p].gR[k];",
+                                 "eq.gR[k] -= e0[p].gR[k];"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }
