@@ -603,6 +603,20 @@ static double op_at(const orc_problem* P, const patch_geo* g, const double* c,
     return c[0] * uxx + c[1] * uxy + c[2] * uyy - nu * ux - om * uy + c[5] * uc;
 }
 
+/* Trapezoid average of the lifted field minus U_ij (reading G4, MACRO
+   reference): by eqs. (Lifting), (C_0) and the trapezoid rule on the nano grid
+   it equals (dxi^2 U_xixi + deta^2 U_etaeta) / 12 exactly (the lift's
+   continuous average is U_ij; the trapezoid rule adds d^2/12 times the second
+   derivative).  The split form uses this closed form, so that no difference of
+   two nearly equal averages is formed for small patches. */
+static double lift_trapezoid_bias(const patch_geo* g, const patch_edge* e)
+{
+    const double (*S)[3] = (const double (*)[3])e->st;
+    double Uxx = (S[2][1] - 2.0 * S[1][1] + S[0][1]) / (g->Dx * g->Dx);
+    double Uyy = (S[1][2] - 2.0 * S[1][1] + S[1][0]) / (g->Dy * g->Dy);
+    return (g->dx * g->dx * Uxx + g->dy * g->dy * Uyy) / 12.0;
+}
+
 /* composite trapezoid average over the patch (eq. (Restriction), Section 4.1) */
 static double trapezoid(const patch_geo* g, const double* u)
 {
@@ -873,7 +887,7 @@ static double run_patch(const orc_problem* P, const double* U, int p, const doub
         dU = U1 - (P->restrict_mode == ORC_RESTRICT_MACRO ? Uij : trapezoid(&g, u0));
     } else {
         dU = trapezoid(&g, u);
-        if (P->restrict_mode == ORC_RESTRICT_MACRO) dU += trapezoid(&g, u0) - Uij;
+        if (P->restrict_mode == ORC_RESTRICT_MACRO) dU += lift_trapezoid_bias(&g, &e);
     }
 
     if (po) {
@@ -964,7 +978,7 @@ void orc_restrict(const orc_problem* P, const double* U, const double* bo, int f
             d = trapezoid(&g, u) - (P->restrict_mode == ORC_RESTRICT_MACRO ? Uij : trapezoid(&g, u0));
         else {
             d = trapezoid(&g, u);
-            if (P->restrict_mode == ORC_RESTRICT_MACRO) d += trapezoid(&g, u0) - Uij;
+            if (P->restrict_mode == ORC_RESTRICT_MACRO) d += lift_trapezoid_bias(&g, &e);
         }
         dU[p] = d;
         free(u); free(u0);
@@ -1095,7 +1109,7 @@ static void step_refresh(const orc_problem* P, double* U, double t0, double dtm,
         for (int p = 0; p < np; ++p) {
             patch_geo g = patch_of(P, p);
             double d = dR[p];
-            if (P->restrict_mode == ORC_RESTRICT_MACRO) d += trapezoid(&g, u0 + (size_t)p * ne) - U[g.j * nxp + g.i];
+            if (P->restrict_mode == ORC_RESTRICT_MACRO) d += lift_trapezoid_bias(&g, &e0[p]);
             U[g.j * nxp + g.i] = U[g.j * nxp + g.i] + dtm * (d / tau);
         }
         orc_apply_bc(P, U, t0 + (s + 1) * dtm);
