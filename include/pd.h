@@ -238,6 +238,21 @@ pd_status pd_set_graph_mode(pd_grid* g, int enabled);
 typedef enum { PD_INT_EULER = 0, PD_INT_HEUN = 1, PD_INT_AB2 = 2 } pd_integrator;
 pd_status pd_set_integrator(pd_grid* g, int kind);
 
+/* Edge-data refresh during the burst (Section 3: the Neumann data of eq. (edge)
+ * are held fixed over the burst, the Q = 1 case; refreshing them is named as
+ * the more accurate alternative).  With q > 1 every burst of pd_step is cut
+ * into q sub-bursts of K/q forward-Euler steps, and before sub-burst s >= 1 the
+ * edge data of every patch are rebuilt from the interpolant of the macro
+ * estimate U + (restricted change of the departure so far) on interior nodes
+ * and the Dirichlet data at the sub-burst start time on boundary nodes; the
+ * micro field is not lifted again.  pd_step then runs the separate passes
+ * (lift, q bursts, q restrictions, q - 1 refreshes, projection) for any m <= 32,
+ * without graph capture.  q = 1 restores fixed edge data.
+ * Errors: PD_EINVAL for q < 1, a K not divisible by q on some instance, or the
+ * ADI micro solver; pd_step returns PD_EINVAL when q > 1 meets a second-order
+ * outer integrator or 1-D coefficient tables. */
+pd_status pd_set_edge_refresh(pd_grid* g, int q);
+
 /* The same macro steps as pd_step with one fused kernel per step, for callers
  * that may not allocate device memory during a step.  The paper has no
  * counterpart; it is a deployment variant.  Such callers are, e.g., a

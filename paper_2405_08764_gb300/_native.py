@@ -82,6 +82,7 @@ SIGNATURES = {
     "pd_set_graph_mode": (C.c_int, [_GP, C.c_int]),
     "pd_set_persistent": (C.c_int, [_GP, C.c_int]),
     "pd_set_integrator": (C.c_int, [_GP, C.c_int]),
+    "pd_set_edge_refresh": (C.c_int, [_GP, C.c_int]),
     "pd_set_coeff_storage": (C.c_int, [_GP, C.c_int]),
     "pd_autotune": (C.c_int, [_GP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pd_set_autotune": (C.c_int, [_GP, C.c_int, C.c_int, C.c_int]),

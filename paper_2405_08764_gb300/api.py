@@ -99,6 +99,10 @@ class Grid:
         self.L.pd_set_graph_mode(self.h, 1 if graphs else 0)
         self.L.pd_set_persistent(self.h, 1 if persistent else 0)
         N.check(self.L.pd_set_integrator(self.h, N.INTEGRATORS[integrator]), self.h)
+        q = {int(p.get("q_refresh") or 1) for p in self.probs}
+        if len(q) != 1:
+            raise ValueError("all instances of a grid share one edge-refresh count")
+        N.check(self.L.pd_set_edge_refresh(self.h, q.pop()), self.h)
         N.check(self.L.pd_set_coeff_storage(self.h, {"auto": 0, "records": 1, "tables": 2}[storage]), self.h)
         if not autotune:
             N.check(self.L.pd_set_autotune(self.h, 0, 128, 0), self.h)

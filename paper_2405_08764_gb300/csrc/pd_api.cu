@@ -92,6 +92,11 @@ struct pd_grid {
     size_t flags_n = 0;
     bool persist = true;
     int integrator = PD_INT_EULER;   // outer (projective) integrator of pd_step
+    int q_refresh = 1;               // edge-data refreshes per burst
+    double* Dq = nullptr;            // refresh increment field (macro-sized)
+    double* dRa = nullptr;           // restricted changes so far (refresh)
+    double* dRb = nullptr;
+    double* dRz = nullptr;           // zeros (no reference bias)
     double* S2 = nullptr;            // second scratch field (Heun)
     double* dUa = nullptr;           // per-patch restricted changes (AB2 history)
     double* dUb = nullptr;
@@ -423,6 +428,60 @@ pd_status step_higher(pd_grid* g, double* U, double t0, double dtm, int n_macro)
     }
     g->launches += nl;
     return rc;
+}
+
+// pd_step with the edge data refreshed q times per burst, through the separate
+// passes: lift; q bursts of K/q steps, each but the first preceded by a
+// restriction (restricted change so far) and a refresh of the edge forcing;
+// restriction of the whole burst; projection
+pd_status step_refresh(pd_grid* g, double* U, double t0, const std::vector<double>& dtm, int n_macro)
+{
+    if (!g->state) {
+        PD_CUDA(g, cudaMalloc(&g->state, g->state_bytes));
+        PD_CUDA(g, cudaMalloc(&g->dU, sizeof(double) * g->n_patch_total));
+    }
+    if (!g->Dq) {
+        PD_CUDA(g, cudaMalloc(&g->Dq, sizeof(double) * (size_t)g->n_macro_total));
+        PD_CUDA(g, cudaMalloc(&g->dRa, sizeof(double) * (size_t)g->n_patch_total));
+        PD_CUDA(g, cudaMalloc(&g->dRb, sizeof(double) * (size_t)g->n_patch_total));
+        PD_CUDA(g, cudaMalloc(&g->dRz, sizeof(double) * (size_t)g->n_patch_total));
+        PD_CUDA(g, cudaMemsetAsync(g->dRz, 0, sizeof(double) * (size_t)g->n_patch_total, g->stream));
+    }
+    const int Q = g->q_refresh;
+    for (int t = 0; t < n_macro; ++t) {
+        for (size_t k = 0; k < g->inst.size(); ++k) {
+            Inst& s = g->inst[k];
+            const InstDev& I = s.I;
+            pd_info lay;
+            layout(g, s, lay);
+            const double T = t0 + t * dtm[k];
+            const int Ks = I.K / Q;
+            // restricted changes of the departure alone (no reference bias, whose
+            // subtraction would cancel digits); zero before the first sub-burst
+            double* cur = g->dRa;
+            const double* prev = g->dRz;
+            cudaError_t e = launch_lift(I, nullptr, s.d.prec, U + I.u_off, T, g->state, lay, g->stream);
+            for (int q = 0; q < Q && e == cudaSuccess; ++q) {
+                const double Tq = T + q * Ks * I.dt;
+                if (q > 0) {
+                    e = launch_restrict(I, s.d.prec, g->state, lay, cur, g->stream, g->dRz);
+                    if (e == cudaSuccess)
+                        e = launch_refresh(I, s.d.prec, U + I.u_off, cur, prev, T + (q - 1) * Ks * I.dt, Tq, q == 1,
+                                           g->Dq + I.u_off, g->state + lay.off_r, g->stream);
+                    prev = cur;
+                    cur = (cur == g->dRa) ? g->dRb : g->dRa;
+                    g->launches += 3;
+                }
+                if (e == cudaSuccess) e = launch_burst(I, nullptr, s.d.prec, g->state, lay, Tq, Ks, g->stream);
+                g->launches += 2;
+            }
+            if (e == cudaSuccess) e = launch_restrict(I, s.d.prec, g->state, lay, g->dU, g->stream);
+            if (e == cudaSuccess) e = launch_project(I, U + I.u_off, g->dU, T, dtm[k], g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "step with edge refresh");
+            g->launches += 4;
+        }
+    }
+    return PD_OK;
 }
 
 pd_status step_fallback(pd_grid* g, double* U, double t0, const std::vector<double>& dtm, int n_macro)
@@ -822,6 +881,7 @@ pd_status pd_destroy_grid(pd_grid* g)
     for (auto& s : g->inst) { cudaFree(s.rec); cudaFree(s.brec); cudaFree(s.arec_c); cudaFree(s.arec_r); cudaFree(s.bnd_off); cudaFree(s.bnd_idx); cudaFree(s.col_tab); cudaFree(s.row_tab); cudaFree(s.col_tab_f); cudaFree(s.row_tab_f); cudaFree(s.bnd_ij); cudaFree(s.bnd_xy); cudaFree(s.amp); }
     cudaFree(g->err); cudaFree(g->acc); cudaFree(g->U_scratch); cudaFree(g->tab);
     cudaFree(g->S2); cudaFree(g->dUa); cudaFree(g->dUb);
+    cudaFree(g->Dq); cudaFree(g->dRa); cudaFree(g->dRb); cudaFree(g->dRz);
     cudaFree(g->state); cudaFree(g->dU); cudaFree(g->flags);
     cudaFree(g->insts_dev); cudaFree(g->items_dev); cudaFree(g->dtm_dev); cudaFree(g->tab_off_dev); cudaFree(g->counters);
     if (g->cap) cudaStreamDestroy(g->cap);
@@ -967,7 +1027,8 @@ pd_status pd_query(const pd_grid* gc, int inst, pd_info* o)
     o->edge_offset = s.I.e_off;
     o->dt_micro = s.dt; o->tau = s.tau; o->dt_macro_suggested = s.dtm_sugg;
     layout(g, s, *o);
-    if (use_batch(g)) o->exec_path = all_batch_supported(g) ? 3 : 0;
+    if (g->q_refresh > 1) o->exec_path = 0;
+    else if (use_batch(g)) o->exec_path = all_batch_supported(g) ? 3 : 0;
     else o->exec_path = !fused_supported(s.I) ? 0
                       : (g->persist && s.coef_set && s.I.micro == PD_MICRO_FE && persist_fits(s.I, s.d.prec)) ? 2 : 1;
     o->chunk_steps = o->exec_path == 2 ? persist_max_steps(s.I, s.d.prec) : 1;
@@ -1093,6 +1154,13 @@ pd_status pd_step(pd_grid* g, double* U, double t0, double dt_macro, int n_macro
     cudaSetDevice(g->device);
     std::vector<double> dtm(g->inst.size());
     for (size_t k = 0; k < g->inst.size(); ++k) dtm[k] = dt_macro > 0 ? dt_macro : g->inst[k].dtm_sugg;
+    if (g->q_refresh > 1) {
+        if (g->integrator != PD_INT_EULER) return fail(g, PD_EINVAL, "edge refresh runs with the forward-Euler outer step");
+        for (auto& s : g->inst)
+            if (s.I.coef_mode != COEF_RECORDS || s.I.micro != PD_MICRO_FE || s.I.K % g->q_refresh != 0)
+                return fail(g, PD_EINVAL, "edge refresh needs per-point records, forward-Euler bursts and K divisible by q");
+        return step_refresh(g, U, t0, dtm, n_macro);
+    }
     if (g->integrator != PD_INT_EULER) {
         if (g->inst.size() != 1 || use_batch(g) || !fused_supported(g->inst[0].I))
             return fail(g, PD_EINVAL, "second-order integrators need a grid of one instance with per-point records "
@@ -1197,6 +1265,18 @@ pd_status pd_set_integrator(pd_grid* g, int kind)
     if (!g) return PD_EINVAL;
     if (kind != PD_INT_EULER && kind != PD_INT_HEUN && kind != PD_INT_AB2) return fail(g, PD_EINVAL, "unknown integrator");
     g->integrator = kind;
+    return PD_OK;
+}
+
+pd_status pd_set_edge_refresh(pd_grid* g, int q)
+{
+    if (!g) return PD_EINVAL;
+    if (q < 1) return fail(g, PD_EINVAL, "q must be >= 1");
+    for (auto& s : g->inst) {
+        if (s.I.K % q != 0) return fail(g, PD_EINVAL, "k_micro must be divisible by q");
+        if (q > 1 && s.I.micro != PD_MICRO_FE) return fail(g, PD_EINVAL, "edge refresh needs forward-Euler bursts");
+    }
+    g->q_refresh = q;
     return PD_OK;
 }
 

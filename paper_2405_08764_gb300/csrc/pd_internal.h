@@ -383,8 +383,10 @@ cudaError_t launch_lift(const InstDev& I, const InstDev* I_dev, int prec, const 
                         char* state, const pd_info& lay, cudaStream_t st);
 cudaError_t launch_burst(const InstDev& I, const InstDev* I_dev, int prec, char* state,
                          const pd_info& lay, double t, int k_steps, cudaStream_t st);
+// bias_override: per-patch reference offsets to add instead of the state's
+// bias section (global patch index), e.g. zeros for the change of the departure
 cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const pd_info& lay,
-                            double* dU, cudaStream_t st);
+                            double* dU, cudaStream_t st, const double* bias_override = nullptr);
 cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm,
                            cudaStream_t st);
 bool fused_supported(const InstDev& I);
@@ -416,6 +418,10 @@ cudaError_t launch_adi_fused(const InstDev& I, int prec, const double* Uc, doubl
                              double dtm, cudaStream_t st);
 cudaError_t launch_adi_dU(const InstDev& I, int prec, const double* U, const double* tab_row, double* dU,
                           const int* list, const int* list_n, cudaStream_t st);
+// edge-data refresh (pd_refresh.cu): D = V_q - V_{q-1} on the macro nodes, then
+// r += e(D) at the edge points of every patch
+cudaError_t launch_refresh(const InstDev& I, int prec, const double* U, const double* dR_cur, const double* dR_prev,
+                           double t_prev, double t_cur, int first, double* D, void* r_state, cudaStream_t st);
 cudaError_t launch_patch_dU(const InstDev& I, int prec, const double* U, const double* tab_row, int k_steps,
                             double* dU, const int* list, const int* list_n, cudaStream_t st);
 // second-order outer integrators: Heun's combination and the AB2 update

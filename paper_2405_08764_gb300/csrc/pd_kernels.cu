@@ -676,9 +676,9 @@ cudaError_t launch_burst(const InstDev& I, const InstDev*, int prec, char* state
 }
 
 cudaError_t launch_restrict(const InstDev& I, int prec, const char* state, const pd_info& lay, double* dU,
-                            cudaStream_t st)
+                            cudaStream_t st, const double* bias_override)
 {
-    const double* bias = reinterpret_cast<const double*>(state + lay.off_bias);
+    const double* bias = bias_override ? bias_override : reinterpret_cast<const double*>(state + lay.off_bias);
     const size_t es = prec == PD_FP32 ? sizeof(float) : sizeof(double);
     const size_t per = es * (size_t)I.mx * I.my;
     const int ppb = (int)std::max<size_t>(1, std::min<size_t>(kRestrictPatches, kRestrictStage / per - 1));
