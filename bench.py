@@ -586,6 +586,85 @@ def run_adi(args):
     return 0
 
 
+def run_refresh(args):
+    """Edge-data refresh (Q > 1) on the 512x2048-node annulus (84.6 M micro
+    points, K = 20, FP32 bursts): pd_step over 2 macro steps per bench step for
+    Q = 2, 4, 10 (separate passes with refreshes) beside Q = 1 (fixed edge data,
+    the fused path), L2 flushed between bench steps.  Roofline of the refresh
+    path: its algorithmic HBM bytes per macro step against the copy bandwidth."""
+    import torch
+
+    from paper_2405_08764_gb300 import workloads as W
+    from paper_2405_08764_gb300.api import Grid
+
+    torch.cuda.set_device(0)
+    n_r, n_theta = (int(v) for v in args.c5_grid.split("x"))
+    base = W.c5_surrogate_field(n_r=n_r, n_theta=n_theta)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    n_macro = 2
+    es = 4
+    pk = peaks()
+    res = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for Q in (1, 2, 4, 10):
+        g = Grid(dict(base, q_refresh=Q), prec="fp32")
+        info = g.info()
+        P, m, K = info["n_patch"], info["m_xi"], info["k_micro"]
+        pts = P * m * m
+        dtm = info["dt_macro_suggested"]
+        U0 = g.init_field()
+        U = U0.clone()
+        for _ in range(args.warmup):
+            U.copy_(U0)
+            g.step(U, 0.0, dtm, n_macro)
+        torch.cuda.synchronize()
+        ms = 0.0
+        l0 = g.launches()
+        for s in range(args.steps):
+            U.copy_(U0)
+            flush.fill_(float(s))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.step(U, 0.0, dtm, n_macro)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        ms_macro = ms / (args.steps * n_macro)
+        r = {"ms_per_macro_step": ms_macro, "exec_path": info["exec_path"],
+             "point_updates_per_s": pts * K / (ms_macro / 1e3),
+             "launches_per_macro_step": (g.launches() - l0) / (args.steps * n_macro)}
+        if Q > 1:
+            # lift (record in; u0, r, w out), Q bursts (w, r, 64 B record in; w out), Q restrictions
+            # (w in), Q - 1 refreshes (edge points: record in, r in and out), projection
+            edge_pts = P * 4 * (m - 1)
+            nbytes = (pts * (32 + 8 + 2 * es) + P * (4 * (m + 2) * 8 + 8)
+                      + Q * pts * (3 * es + 64) + Q * (pts * es + P * 16)
+                      + (Q - 1) * (edge_pts * (32 + 2 * es) + 3 * P * 8) + P * 24)
+            r["bytes_per_macro_step"] = nbytes
+            r["GB_per_s"] = nbytes / (ms_macro / 1e3) / 1e9
+            r["frac_hbm"] = r["GB_per_s"] / pk["hbm_gbs"]
+        res["Q=%d" % Q] = r
+        del g
+    clocks = sampler.stop()
+    q4 = res["Q=4"]
+    line = {
+        "metric": "edge-refresh path: point-updates/s and achieved HBM GB/s per Q", "value": q4["point_updates_per_s"],
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "annulus %dx%d macro nodes, %dx%d micro, K=%d, %d macro steps per step, Q in 1,2,4,10"
+                               % (n_r + 1, n_theta, m, m, K, n_macro),
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "roofline": {"bound": "hbm", "achieved": q4["GB_per_s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": q4["frac_hbm"], "traffic": None, "kernel": "refresh path at Q = 4 (all its passes)",
+                     "peak_source": "%s hbm_gbs" % pk["source"]},
+        "per_q": res, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -732,11 +811,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "passes", "adi"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "passes", "adi", "refresh"],
                     help="c2: the benchmark workload (default); c4: the 4096-instance batch; "
                          "c5: the surrogate against the plain scheme on the 512x2048 annulus; "
                          "passes: the separate C-ABI passes on that annulus; "
-                         "adi: ADI bursts at the paper's Section 4.1 patch settings")
+                         "adi: ADI bursts at the paper's Section 4.1 patch settings; "
+                         "refresh: edge-data refresh Q = 1, 2, 4, 10 on the annulus")
     ap.add_argument("--adi-n", type=int, default=400, help="adi: macro intervals per side")
     ap.add_argument("--epochs", type=int, default=80, help="c5: training epochs")
     ap.add_argument("--c5-grid", default="511x2048", help="c5: radial intervals x angular nodes")
@@ -756,6 +836,8 @@ def main():
         return run_passes(args)
     if args.workload == "adi":
         return run_adi(args)
+    if args.workload == "refresh":
+        return run_refresh(args)
     return run_gpu(args)
 
 

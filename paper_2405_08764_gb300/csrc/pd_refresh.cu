@@ -12,7 +12,8 @@
 // macro field, so the forcing of the micro state is updated by e(V_q - V_{q-1})
 // before each sub-burst: refresh_field_kernel forms the increment field
 // D = V_q - V_{q-1} on the macro nodes and refresh_kernel adds e(D) to r at
-// the edge points (any m <= 32, both precisions).
+// the edge points (any m <= 32, both precisions, in the grid's working
+// precision).
 #include "pd_device.cuh"
 
 #include <math.h>
@@ -45,78 +46,104 @@ __global__ void refresh_field_kernel(const InstDev I, const double* __restrict__
 }
 
 // derivatives of the biquadratic interpolant with monomial coefficients c
-__device__ __forceinline__ double dxi_poly(const double c[9], double s, double t)
+template <typename real>
+__device__ __forceinline__ real dxi_poly(const real (&c)[9], real s, real t)
 {
-    return c[1] + 2.0 * c[3] * s + c[4] * t + 2.0 * c[6] * s * t + c[7] * t * t + 2.0 * c[8] * s * t * t;
+    return c[1] + real(2) * c[3] * s + c[4] * t + real(2) * c[6] * s * t + c[7] * t * t + real(2) * c[8] * s * t * t;
 }
 
-__device__ __forceinline__ double deta_poly(const double c[9], double s, double t)
+template <typename real>
+__device__ __forceinline__ real deta_poly(const real (&c)[9], real s, real t)
 {
-    return c[2] + 2.0 * c[5] * t + c[4] * s + c[6] * s * s + 2.0 * c[7] * s * t + 2.0 * c[8] * s * s * t;
+    return c[2] + real(2) * c[5] * t + c[4] * s + c[6] * s * s + real(2) * c[7] * s * t + real(2) * c[8] * s * s * t;
 }
 
 // change of the ghost value at (ap, bp) (outside the patch) for the edge-data
 // change of the interpolant c, in the ghost order of the explicit scheme:
 // eta-ghost rows from the bottom/top data, then xi-ghost columns (corners
 // included) from the left/right data
-__device__ __forceinline__ double ghost_delta(const double c[9], const PatchGeo<double>& g, int ap, int bp)
+template <typename real>
+__device__ __forceinline__ real ghost_delta(const real (&c)[9], const PatchGeo<real>& g, int ap, int bp)
 {
-    double v = 0.0;
+    real v = real(0);
     int ain = ap;
-    if (ap < 0) { v -= 2.0 * g.dx * dxi_poly(c, -0.5 * g.hx, g.t(bp)); ain = 1; }
-    else if (ap > g.nx) { v += 2.0 * g.dx * dxi_poly(c, 0.5 * g.hx, g.t(bp)); ain = g.nx - 1; }
-    if (bp < 0) v -= 2.0 * g.dy * deta_poly(c, g.s(ain), -0.5 * g.hy);
-    else if (bp > g.ny) v += 2.0 * g.dy * deta_poly(c, g.s(ain), 0.5 * g.hy);
+    if (ap < 0) { v -= real(2) * g.dx * dxi_poly(c, real(-0.5) * g.hx, g.t(bp)); ain = 1; }
+    else if (ap > g.nx) { v += real(2) * g.dx * dxi_poly(c, real(0.5) * g.hx, g.t(bp)); ain = g.nx - 1; }
+    if (bp < 0) v -= real(2) * g.dy * deta_poly(c, g.s(ain), real(-0.5) * g.hy);
+    else if (bp > g.ny) v += real(2) * g.dy * deta_poly(c, g.s(ain), real(0.5) * g.hy);
     return v;
 }
 
-// one thread per micro point; interior points return at once
+// One warp per patch.  Lane s < 9 forms stencil difference s of D in FP64
+// (the slots of the fused kernel: second and first differences and the
+// centre value), converts it once, and coefficient k of the interpolant
+// combines up to three slots in the working precision, so that no difference
+// of nearly equal values is formed after the conversion.  The lanes then share
+// out the 2 m_xi + 2 (m_eta - 2) edge points and add e(D) to r there, in the
+// working precision; instance constants and slot weights are converted once
+// per block (a double -> float conversion issues on the FP64 pipe, a small
+// fraction of the FP32 rate on this part).
 template <typename real>
-__global__ void refresh_kernel(const InstDev I, const double* __restrict__ D, const real* __restrict__ rec,
-                               real* __restrict__ r)
+__global__ void __launch_bounds__(256)
+refresh_kernel(const InstDev I, const double* __restrict__ D, const real* __restrict__ rec, real* __restrict__ r)
 {
-    const long long n = (long long)I.n_patch * I.mx * I.my;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
-    const int mm = I.mx * I.my;
-    const int p = (int)(idx / mm);
-    const int rem = (int)(idx - (long long)p * mm);
-    const int b = rem / I.mx, a = rem - b * I.mx;
-    const int nx = I.mx - 1, ny = I.my - 1;
-    if (a != 0 && a != nx && b != 0 && b != ny) return;
+    __shared__ real cw_s[9][3];
+    __shared__ int slot_s[9][3];
+    __shared__ RealConsts<real> kc_s;
+    __shared__ PatchGeo<real> g_s;
+    for (int t = threadIdx.x; t < 27; t += blockDim.x) {
+        cw_s[t / 3][t % 3] = (real)I.c2w[t / 3][t % 3];
+        slot_s[t / 3][t % 3] = I.c2slot[t / 3][t % 3];
+    }
+    if (threadIdx.x == 0) {
+        kc_s = real_consts<real>(I);
+        g_s = PatchGeo<real>{ (real)I.hx, (real)I.hy, (real)I.dx, (real)I.dy, I.mx - 1, I.my - 1 };
+    }
+    __syncthreads();
+    const int p = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (p >= I.n_patch) return;                      // whole warp
     const int jr = p / I.ncols, ic = p - jr * I.ncols;
     const int i = I.i0 + ic, j = 1 + jr;
-    // monomial coefficients of the interpolant of D (the constant term is not needed)
-    double st[9];
-    for (int pp = 0; pp < 3; ++pp)
-        for (int qq = 0; qq < 3; ++qq)
-            st[pp * 3 + qq] = D[(long long)(j + qq - 1) * I.nxp + wrap_col(I, i + pp - 1)];
-    double c[9];
-    c[0] = 0.0;
-    for (int k = 1; k < 9; ++k) {
-        double v = 0.0;
-        for (int q = 0; q < 9; ++q) v = fma(I.lw[k][q], st[q], v);
-        c[k] = v;
+    const real sv = lane < 9 ? (real)stencil_slot<false>(I, D, i, j, lane) : real(0);
+    real ck = real(0);                               // lane k: coefficient k (the constant term is not needed)
+    {
+        const int k = lane < 9 ? lane : 0;
+        const real P0 = __shfl_sync(kFull, sv, slot_s[k][0]);
+        const real P1 = __shfl_sync(kFull, sv, slot_s[k][1]);
+        const real P2 = __shfl_sync(kFull, sv, slot_s[k][2]);
+        if (lane >= 1 && lane < 9) ck = cw_s[k][2] * fma(cw_s[k][1], P2, fma(cw_s[k][0], P1, P0));
     }
-    const long long pt = (((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a;
-    const real* cr = rec + pt * 8;
-    PointW<double> w = point_weights<double>((double)cr[0], (double)cr[1], (double)cr[2], (double)cr[3],
-                                             (double)cr[4], (double)cr[5], I.dx, I.dy, I.conv);
-    PatchGeo<double> g = { I.hx, I.hy, I.dx, I.dy, nx, ny };
-    double e = 0.0;
-    if (a == 0) e += w.wW * ghost_delta(c, g, -1, b);
-    if (a == nx) e += w.wE * ghost_delta(c, g, nx + 1, b);
-    if (b == 0) e += w.wS * ghost_delta(c, g, a, -1);
-    if (b == ny) e += w.wN * ghost_delta(c, g, a, ny + 1);
-    if ((double)cr[1] != 0.0) {
-        auto out = [&](int ap, int bp) { return ap < 0 || ap > nx || bp < 0 || bp > ny; };
-        if (out(a + 1, b + 1)) e += w.wX * ghost_delta(c, g, a + 1, b + 1);
-        if (out(a - 1, b - 1)) e += w.wX * ghost_delta(c, g, a - 1, b - 1);
-        if (out(a + 1, b - 1)) e -= w.wX * ghost_delta(c, g, a + 1, b - 1);
-        if (out(a - 1, b + 1)) e -= w.wX * ghost_delta(c, g, a - 1, b + 1);
+    real c[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c[k] = __shfl_sync(kFull, ck, k);
+    const RealConsts<real> kc = kc_s;
+    const PatchGeo<real> g = g_s;
+    const int nx = g.nx, ny = g.ny;
+    const int n_edge = 2 * I.mx + 2 * (I.my - 2);
+    for (int e = lane; e < n_edge; e += 32) {
+        int a, b;
+        if (e < I.mx) { a = e; b = 0; }
+        else if (e < 2 * I.mx) { a = e - I.mx; b = ny; }
+        else { const int t = e - 2 * I.mx; b = 1 + (t >> 1); a = (t & 1) ? nx : 0; }
+        const long long pt = (((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a;
+        const real* cr = rec + pt * 8;
+        const real be = cr[1];
+        const PointW<real> w = point_weights_k<real>(I, kc, cr[0], be, cr[2], cr[3], cr[4], cr[5]);
+        real v = real(0);
+        if (a == 0) v += w.wW * ghost_delta(c, g, -1, b);
+        if (a == nx) v += w.wE * ghost_delta(c, g, nx + 1, b);
+        if (b == 0) v += w.wS * ghost_delta(c, g, a, -1);
+        if (b == ny) v += w.wN * ghost_delta(c, g, a, ny + 1);
+        if (be != real(0)) {
+            auto out = [&](int ap, int bp) { return ap < 0 || ap > nx || bp < 0 || bp > ny; };
+            if (out(a + 1, b + 1)) v += w.wX * ghost_delta(c, g, a + 1, b + 1);
+            if (out(a - 1, b - 1)) v += w.wX * ghost_delta(c, g, a - 1, b - 1);
+            if (out(a + 1, b - 1)) v -= w.wX * ghost_delta(c, g, a + 1, b - 1);
+            if (out(a - 1, b + 1)) v -= w.wX * ghost_delta(c, g, a - 1, b + 1);
+        }
+        r[I.pt_off + (long long)p * I.mx * I.my + b * I.mx + a] += v;
     }
-    real* rp = r + I.pt_off + idx;
-    *rp = (real)((double)*rp + e);
 }
 
 }  // namespace
@@ -128,12 +155,11 @@ cudaError_t launch_refresh(const InstDev& I, int prec, const double* U, const do
     refresh_field_kernel<<<(nn + 127) / 128, 128, 0, st>>>(I, U, dR_cur, dR_prev, t_prev, t_cur, first, D);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const long long n = (long long)I.n_patch * I.mx * I.my;
-    const unsigned nb = (unsigned)((n + 127) / 128);
+    const unsigned nb = (unsigned)(((long long)I.n_patch * 32 + 255) / 256);
     if (prec == PD_FP32)
-        refresh_kernel<float><<<nb, 128, 0, st>>>(I, D, static_cast<const float*>(I.rec), static_cast<float*>(r_state));
+        refresh_kernel<float><<<nb, 256, 0, st>>>(I, D, static_cast<const float*>(I.rec), static_cast<float*>(r_state));
     else
-        refresh_kernel<double><<<nb, 128, 0, st>>>(I, D, static_cast<const double*>(I.rec), static_cast<double*>(r_state));
+        refresh_kernel<double><<<nb, 256, 0, st>>>(I, D, static_cast<const double*>(I.rec), static_cast<double*>(r_state));
     return cudaGetLastError();
 }
 
