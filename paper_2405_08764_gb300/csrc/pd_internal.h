@@ -132,6 +132,20 @@ struct PatchGeo {
     __device__ __forceinline__ real t(int b) const { return real(-0.5) * hy + real(b) * dy; }
 };
 
+// The same geometry with the micro coordinates read from tables (s(a) at
+// sv[a + 1], t(b) at tv[b + 1], a, b = -1 .. m): no integer -> float
+// conversion per use, which matters in per-point loops (conversions issue on
+// the slow FP64 pipe of this part).
+template <typename real>
+struct PatchGeoTab {
+    real hx, hy, dx, dy;
+    int nx, ny;
+    const real* sv;
+    const real* tv;
+    __device__ __forceinline__ real s(int a) const { return sv[a + 1]; }
+    __device__ __forceinline__ real t(int b) const { return tv[b + 1]; }
+};
+
 // d/dxi of (P - u0): the part of the Neumann data of eq. (edge) that the
 // quadratic lift does not carry.
 template <typename real>
@@ -149,8 +163,8 @@ __device__ __forceinline__ real edge_gap_eta(const Poly<real>& c, real s, real t
 // Ghost-point value minus the quadratic lift extended to the ghost position
 // (a', b'), for the ghost rule: eta-ghost rows from the bottom/top Neumann data,
 // then xi-ghost columns (corners included) from the left/right data.
-template <typename real>
-__device__ __forceinline__ real ghost_offset(const Poly<real>& c, const PatchGeo<real>& g, int ap, int bp)
+template <typename real, typename Geo>
+__device__ __forceinline__ real ghost_offset(const Poly<real>& c, const Geo& g, int ap, int bp)
 {
     real v = real(0);
     int ain = ap;
@@ -315,8 +329,8 @@ __device__ __forceinline__ PointW<real> point_weights_fast(const InstDev& I, rea
 // the midpoint, and every ghost neighbour adds weight * ghost_offset.  No
 // difference of nearly equal lifted values is formed, so FP32 evaluation keeps
 // full relative precision.
-template <typename real>
-__device__ __forceinline__ real burst_forcing(const Poly<real>& c, const PatchGeo<real>& g, int a, int b,
+template <typename real, typename Geo>
+__device__ __forceinline__ real burst_forcing(const Poly<real>& c, const Geo& g, int a, int b,
                                               real al, real be, real ga, real nu, real om, real ph,
                                               real G, real sT, const PointW<real>& w)
 {

@@ -247,7 +247,7 @@ __device__ __forceinline__ long long rec_index(const InstDev& I, int jr, int ic,
 // A = C0 + c10 s + c20 s^2, B = c01 + c11 s, Q = c02 t^2 (one FP64 fma and one
 // add per point).
 template <typename real>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restrict__ tab, double* u0,
             real* r_out, real* w_out, double* edge, double* bias_out, int edge_stride, int ppb)
 {
@@ -258,12 +258,33 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
     __shared__ double ecoef[PPB][4][3];      // edge data as a quadratic along each edge
     __shared__ real csr[PPB][9];             // coefficients in the working precision
     __shared__ double gs[34], gt[34];        // micro coordinates s_a, t_b for a, b = -1 .. m
+    __shared__ real gsr[34], gtr[34];        // the same in the working precision
+    __shared__ int4 pij_s[PPB];              // (i, j, ic, jr) of every patch of the block
+    __shared__ int ab_s[1024];               // (b << 16) | a of in-patch point tl
     const int p0 = blockIdx.x * ppb;
     const int mm = I.mx * I.my;
+    // instance constants in the working precision, converted once per block
+    __shared__ RealConsts<real> kc_s;
+    __shared__ PatchGeo<real> grc_s;
+    __shared__ real sT_s;
+    if (threadIdx.x == 0) {
+        kc_s = real_consts<real>(I);
+        grc_s = PatchGeo<real>{ (real)I.hx, (real)I.hy, (real)I.dx, (real)I.dy, I.mx - 1, I.my - 1 };
+        sT_s = (real)tab[0];
+    }
     PatchGeo<double> gd = { I.hx, I.hy, I.dx, I.dy, I.mx - 1, I.my - 1 };
     for (int t = threadIdx.x; t < 34; t += blockDim.x) {
         gs[t] = gd.s(t - 1);
         gt[t] = gd.t(t - 1);
+    }
+    for (int t = threadIdx.x; t < mm; t += blockDim.x) {
+        const int b = t / I.mx;
+        ab_s[t] = (b << 16) | (t - b * I.mx);
+    }
+    for (int t = threadIdx.x; t < ppb; t += blockDim.x) {
+        int i = 0, j = 0, ic = 0, jr = 0;
+        if (p0 + t < I.n_patch) patch_ij(I, p0 + t, i, j, ic, jr);
+        pij_s[t] = make_int4(i, j, ic, jr);
     }
     for (int t = threadIdx.x; t < ppb * 9; t += blockDim.x) {
         const int q = t / 9, k = t - q * 9;
@@ -280,72 +301,89 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
     for (int t = threadIdx.x; t < ppb * 9; t += blockDim.x) {
         const int q = t / 9, k = t - q * 9;
         const double* x = sl[q];
-        cs[q][k] = fma(I.c2w[k][1], x[I.c2slot[k][2]], fma(I.c2w[k][0], x[I.c2slot[k][1]], x[I.c2slot[k][0]])) * I.c2w[k][2];
+        const double c = fma(I.c2w[k][1], x[I.c2slot[k][2]], fma(I.c2w[k][0], x[I.c2slot[k][1]], x[I.c2slot[k][0]])) * I.c2w[k][2];
+        cs[q][k] = c;
+        csr[q][k] = (real)c;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < ppb * 32; t += blockDim.x) {
-        const int q = t >> 5, k = t & 31;
+    // per-patch tables, every phase dense over (patch, entry) so that the FP64
+    // pipe (a small fraction of the FP32 rate on this part) runs full warps
+    for (int t = threadIdx.x; t < ppb * I.mx; t += blockDim.x) {
+        const int q = t / I.mx, k = t - q * I.mx;
         const double* c = cs[q];
-        if (k < I.mx) {
-            const double sa = gs[k + 1];
-            tabA[q][k] = c[0] + sa * (c[1] + sa * c[3]);
-            tabB[q][k] = c[2] + c[4] * sa;
-        }
-        if (k < I.my) {
-            const double tb = gt[k + 1];
-            tabQ[q][k] = c[5] * tb * tb;
-        }
-        if (k < 9) csr[q][k] = (real)c[k];
-        if (k < 4) {
-            // d/dxi of P on xi = -+hx/2 as a quadratic in t; d/deta on eta = -+hy/2 in s
-            if (k < 2) {
-                const double s0 = (k == 0 ? -0.5 : 0.5) * I.hx;
-                ecoef[q][k][0] = c[1] + 2.0 * c[3] * s0;
-                ecoef[q][k][1] = c[4] + 2.0 * c[6] * s0;
-                ecoef[q][k][2] = c[7] + 2.0 * c[8] * s0;
-            } else {
-                const double t0 = (k == 2 ? -0.5 : 0.5) * I.hy;
-                ecoef[q][k][0] = c[2] + 2.0 * c[5] * t0;
-                ecoef[q][k][1] = c[4] + 2.0 * c[7] * t0;
-                ecoef[q][k][2] = c[6] + 2.0 * c[8] * t0;
-            }
+        const double sa = gs[k + 1];
+        tabA[q][k] = c[0] + sa * (c[1] + sa * c[3]);
+        tabB[q][k] = c[2] + c[4] * sa;
+    }
+    for (int t = threadIdx.x; t < ppb * I.my; t += blockDim.x) {
+        const int q = t / I.my, k = t - q * I.my;
+        const double tb = gt[k + 1];
+        tabQ[q][k] = cs[q][5] * tb * tb;
+    }
+    for (int t = threadIdx.x; t < ppb * 4; t += blockDim.x) {
+        const int q = t >> 2, k = t & 3;
+        const double* c = cs[q];
+        // d/dxi of P on xi = -+hx/2 as a quadratic in t; d/deta on eta = -+hy/2 in s
+        if (k < 2) {
+            const double s0 = (k == 0 ? -0.5 : 0.5) * I.hx;
+            ecoef[q][k][0] = c[1] + 2.0 * c[3] * s0;
+            ecoef[q][k][1] = c[4] + 2.0 * c[6] * s0;
+            ecoef[q][k][2] = c[7] + 2.0 * c[8] * s0;
+        } else {
+            const double t0 = (k == 2 ? -0.5 : 0.5) * I.hy;
+            ecoef[q][k][0] = c[2] + 2.0 * c[5] * t0;
+            ecoef[q][k][1] = c[4] + 2.0 * c[7] * t0;
+            ecoef[q][k][2] = c[6] + 2.0 * c[8] * t0;
         }
     }
+    for (int t = threadIdx.x; t < 34; t += blockDim.x) {
+        gsr[t] = grc_s.s(t - 1);
+        gtr[t] = grc_s.t(t - 1);
+    }
     __syncthreads();
-    const RealConsts<real> kc = real_consts<real>(I);
-    PatchGeo<real> gr = { (real)I.hx, (real)I.hy, kc.dx, kc.dy, I.mx - 1, I.my - 1 };
+    const RealConsts<real> kc = kc_s;
+    const PatchGeoTab<real> gr = { grc_s.hx, grc_s.hy, grc_s.dx, grc_s.dy, I.mx - 1, I.my - 1, gsr, gtr };
     const real* rec = static_cast<const real*>(I.rec);
-    const real sT = (real)tab[0];
-    for (int t = threadIdx.x; t < ppb * mm; t += blockDim.x) {
-        const int q = t / mm, tl = t - q * mm;
+    const real sT = sT_s;
+    // points t = threadIdx.x + k blockDim.x of the block's ppb * mm, patch q and
+    // in-patch index tl advanced without division; (a, b) from the table
+    int q = 0, tl = threadIdx.x;
+    while (tl >= mm) { tl -= mm; ++q; }
+    for (; q < ppb; ) {
         const int p = p0 + q;
-        if (p >= I.n_patch) continue;
-        int i, j, ic, jr;
-        patch_ij(I, p, i, j, ic, jr);
-        const real* cq = csr[q];
-        Poly<real> cr = { cq[0], cq[1], cq[2], cq[3], cq[4], cq[5], cq[6], cq[7], cq[8] };
-        const int b = tl / I.mx, a = tl - b * I.mx;
-        real v[8];
-        if (I.coef_mode != COEF_RECORDS) {
-            table_coeffs_k<real>(I, kc, ic, a, jr, b, v);
-            v[6] = real(0);
-        } else {
-            const real* rr = rec + ((((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a) * 8;
-            for (int k = 0; k < 8; ++k) v[k] = rr[k];
+        if (p < I.n_patch) {
+            const int4 pq = pij_s[q];
+            const int i = pq.x, j = pq.y, ic = pq.z, jr = pq.w;
+            (void)i; (void)j;
+            const real* cq = csr[q];
+            Poly<real> cr = { cq[0], cq[1], cq[2], cq[3], cq[4], cq[5], cq[6], cq[7], cq[8] };
+            const int ab = ab_s[tl];
+            const int b = ab >> 16, a = ab & 0xffff;
+            real v[8];
+            if (I.coef_mode != COEF_RECORDS) {
+                table_coeffs_k<real>(I, kc, ic, a, jr, b, v);
+                v[6] = real(0);
+            } else {
+                const real* rr = rec + ((((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a) * 8;
+                for (int k = 0; k < 8; ++k) v[k] = rr[k];
+            }
+            const long long o = I.pt_off + (long long)p * mm + tl;
+            u0[o] = fma(gt[b + 1], tabB[q][a], tabA[q][a] + tabQ[q][b]);
+            PointW<real> pw = point_weights_k<real>(I, kc, v[0], v[1], v[2], v[3], v[4], v[5]);
+            r_out[o] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
+            w_out[o] = real(0);
         }
-        const long long o = I.pt_off + (long long)p * mm + tl;
-        u0[o] = fma(gt[b + 1], tabB[q][a], tabA[q][a] + tabQ[q][b]);
-        PointW<real> pw = point_weights_k<real>(I, kc, v[0], v[1], v[2], v[3], v[4], v[5]);
-        r_out[o] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
-        w_out[o] = real(0);
+        tl += blockDim.x;
+        while (tl >= mm) { tl -= mm; ++q; }
     }
     // edge data of eq. (edge) = d/dxi, d/deta of the interpolant P at the edges
+    // (dense over (patch, side, entry))
     for (int t = threadIdx.x; t < ppb * 4 * edge_stride; t += blockDim.x) {
-        const int q = t / (4 * edge_stride), tl = t - q * 4 * edge_stride;
-        const int p = p0 + q;
+        const int qq = t / (4 * edge_stride), tl = t - qq * 4 * edge_stride;
+        const int p = p0 + qq;
         if (p >= I.n_patch) continue;
-        const int side = tl / edge_stride, e = tl % edge_stride;
-        const double* ec = ecoef[q][side];
+        const int side = tl / edge_stride, e = tl - side * edge_stride;
+        const double* ec = ecoef[qq][side];
         double val = 0.0;
         if ((side < 2 && e < I.my + 2) || (side >= 2 && e < I.mx + 2)) {
             const double x = side < 2 ? gt[e] : gs[e];
@@ -451,22 +489,23 @@ restrict_kernel(const InstDev I, const real* __restrict__ w, const double* __res
     acc += __shfl_xor_sync(FULL, acc, 2);
     if (q < np && sub == 0) {
         const long long pg = (long long)I.p_off + p0 + q;
-        double v = (double)acc / ((double)(I.mx - 1) * (I.my - 1)) + bias[pg];
+        double v = fma((double)acc, I.inv_nn, bias[pg]);
         if (!isfinite(v)) atomicOr(I.err, ERR_NONFINITE);
         dU[pg] = v;
     }
 }
 
 // eq. (Extrapolation) on interior nodes + Dirichlet data at t + dt_macro
+// (scale = dt_macro / tau, formed on the host: no FP64 division per node)
 __global__ void project_kernel(const InstDev I, double* __restrict__ U, const double* __restrict__ dU,
-                               double t_next, double dtm)
+                               double t_next, double scale)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < I.n_patch) {
         int i, j, ic, jr;
         patch_ij(I, k, i, j, ic, jr);
         long long node = (long long)j * I.nxp + i;
-        U[node] = U[node] + dtm * (dU[(long long)I.p_off + k] / I.tau);
+        U[node] = fma(scale, dU[(long long)I.p_off + k], U[node]);
     } else if (k < I.n_patch + I.n_bnd) {
         int q = k - I.n_patch;
         int2 ij = I.bnd_ij[q];
@@ -756,7 +795,7 @@ cudaError_t launch_ab2(const InstDev& I, double* U, const double* dUn, const dou
 cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm, cudaStream_t st)
 {
     int n = I.n_patch + I.n_bnd;
-    project_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, U, dU, t + dtm, dtm);
+    project_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, U, dU, t + dtm, dtm * I.inv_tau);
     return cudaGetLastError();
 }
 
