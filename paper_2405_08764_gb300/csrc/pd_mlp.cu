@@ -66,22 +66,33 @@ __host__ __device__ constexpr size_t gemm_smem_bytes(int BN, int S)
     return 1024 + (size_t)S * (kBM * kBK * 2 + (size_t)BN * kBK * 2) + (2 * S + 1) * 8 + 16 + kBM * 4;
 }
 
+// tanh(u) = 1 - 2 / (exp(2u) + 1) from the hardware base-2 exponential and
+// reciprocal approximations: absolute error a few 1e-7 for every u (the ends go
+// to +-1 through exp -> inf or 0), five instructions
+__device__ __forceinline__ float tanh_acc(float u)
+{
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(u * 2.8853900817779268f));   // 2 / ln 2
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.0f));
+    return fmaf(-2.0f, r, 1.0f);
+}
+
 __device__ __forceinline__ float gelu_f(float x)
 {
     const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
-    return 0.5f * x * (1.0f + tanhf(u));
+    return 0.5f * x * (1.0f + tanh_acc(u));
 }
 
 __device__ __forceinline__ float gelu_grad_f(float x)
 {
     const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
-    const float t = tanhf(u);
+    const float t = tanh_acc(u);
     return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * x * x);
 }
 
 // Hidden layers (their outputs are rounded to BF16) evaluate tanh with the
 // hardware approximation tanh.approx.f32 (absolute error of order 2^-11, below
-// the BF16 rounding step); the output layer keeps tanhf.
+// the BF16 rounding step); the output layer keeps the accurate tanh_acc.
 __device__ __forceinline__ float tanh_fast(float u)
 {
     float t;
@@ -745,29 +756,42 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                 tc_fence_after();
                 if (L < 2) {
                     const float* bias = L == 0 ? a.b1 : a.b2;
+                    // 64 columns per TMEM load (one wait), then 16-column pieces
 #pragma unroll 1
-                    for (int c = 0; c < 8; ++c) {
-                        const int col = half * 128 + c * 16;
-                        float v[16];
-                        tmem_ld16(tbase + col, v);
+                    for (int c2 = 0; c2 < 2; ++c2) {
+                        const int col0 = half * 128 + c2 * 64;
+                        float v[64];
+                        tmem_ld64(tbase + col0, v);
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) v[k] = gelu_fast(v[k] + bias[col + k]);
-                        uint4 q[2];
+                        for (int c = 0; c < 4; ++c) {
+                            const int col = col0 + c * 16;
+                            float* vv = v + 16 * c;
+                            const float4* bq = reinterpret_cast<const float4*>(bias + col);
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            __nv_bfloat162 p0 = __floats2bfloat162_rn(v[8 * h + 0], v[8 * h + 1]);
-                            __nv_bfloat162 p1 = __floats2bfloat162_rn(v[8 * h + 2], v[8 * h + 3]);
-                            __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * h + 4], v[8 * h + 5]);
-                            __nv_bfloat162 p3 = __floats2bfloat162_rn(v[8 * h + 6], v[8 * h + 7]);
-                            q[h].x = *reinterpret_cast<uint32_t*>(&p0);
-                            q[h].y = *reinterpret_cast<uint32_t*>(&p1);
-                            q[h].z = *reinterpret_cast<uint32_t*>(&p2);
-                            q[h].w = *reinterpret_cast<uint32_t*>(&p3);
+                            for (int k4 = 0; k4 < 4; ++k4) {
+                                const float4 bb = __ldg(bq + k4);
+                                vv[4 * k4 + 0] = gelu_fast(vv[4 * k4 + 0] + bb.x);
+                                vv[4 * k4 + 1] = gelu_fast(vv[4 * k4 + 1] + bb.y);
+                                vv[4 * k4 + 2] = gelu_fast(vv[4 * k4 + 2] + bb.z);
+                                vv[4 * k4 + 3] = gelu_fast(vv[4 * k4 + 3] + bb.w);
+                            }
+                            uint4 q[2];
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                __nv_bfloat162 p0 = __floats2bfloat162_rn(vv[8 * h + 0], vv[8 * h + 1]);
+                                __nv_bfloat162 p1 = __floats2bfloat162_rn(vv[8 * h + 2], vv[8 * h + 3]);
+                                __nv_bfloat162 p2 = __floats2bfloat162_rn(vv[8 * h + 4], vv[8 * h + 5]);
+                                __nv_bfloat162 p3 = __floats2bfloat162_rn(vv[8 * h + 6], vv[8 * h + 7]);
+                                q[h].x = *reinterpret_cast<uint32_t*>(&p0);
+                                q[h].y = *reinterpret_cast<uint32_t*>(&p1);
+                                q[h].z = *reinterpret_cast<uint32_t*>(&p2);
+                                q[h].w = *reinterpret_cast<uint32_t*>(&p3);
+                            }
+                            const int kc = col >> 6, j = (col & 63) >> 3;
+                            uint8_t* rowp = act + kc * kActChunk + r * 128;
+                            *reinterpret_cast<uint4*>(rowp + (((j) ^ (r & 7)) << 4)) = q[0];
+                            *reinterpret_cast<uint4*>(rowp + (((j + 1) ^ (r & 7)) << 4)) = q[1];
                         }
-                        const int kc = col >> 6, j = (col & 63) >> 3;
-                        uint8_t* rowp = act + kc * kActChunk + r * 128;
-                        *reinterpret_cast<uint4*>(rowp + (((j) ^ (r & 7)) << 4)) = q[0];
-                        *reinterpret_cast<uint4*>(rowp + (((j + 1) ^ (r & 7)) << 4)) = q[1];
                     }
                     fence_async_shared();
                     tc_fence_before();
@@ -776,12 +800,20 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                 } else {
                     float part = 0.0f;
 #pragma unroll 1
-                    for (int c = 0; c < 8; ++c) {
-                        const int col = half * 128 + c * 16;
-                        float v[16];
-                        tmem_ld16(tbase + col, v);
+                    for (int c2 = 0; c2 < 2; ++c2) {
+                        const int col0 = half * 128 + c2 * 64;
+                        float v[64];
+                        tmem_ld64(tbase + col0, v);
+                        const float4* bq = reinterpret_cast<const float4*>(a.b3 + col0);
+                        const float4* wq = reinterpret_cast<const float4*>(a.w4 + col0);
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) part = fmaf(gelu_f(v[k] + a.b3[col + k]), a.w4[col + k], part);
+                        for (int k4 = 0; k4 < 16; ++k4) {
+                            const float4 bb = __ldg(bq + k4), ww = __ldg(wq + k4);
+                            part = fmaf(gelu_f(v[4 * k4 + 0] + bb.x), ww.x, part);
+                            part = fmaf(gelu_f(v[4 * k4 + 1] + bb.y), ww.y, part);
+                            part = fmaf(gelu_f(v[4 * k4 + 2] + bb.z), ww.z, part);
+                            part = fmaf(gelu_f(v[4 * k4 + 3] + bb.w), ww.w, part);
+                        }
                     }
                     tc_fence_before();
                     if (half == 1) {
