@@ -100,6 +100,28 @@ __device__ __forceinline__ float tanh_fast(float u)
     return t;
 }
 
+// Packed FP32 pairs (one instruction for two lanes of data on this part's
+// FMA pipes) for the hidden-layer epilogue.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) { f32x2 r; asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b)); return r; }
+__device__ __forceinline__ void upk2(f32x2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) { f32x2 d; asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c)); return d; }
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) { f32x2 d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) { f32x2 d; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+
+// gelu_fast of (x0 + b0, x1 + b1) as a pair: x (1 + 0.044715 x^2) C, tanh by
+// tanh.approx per element, x (1/2 + t/2)
+__device__ __forceinline__ void gelu_fast2(float& x0, float& x1, float b0, float b1)
+{
+    const f32x2 x = add2(pk2(x0, x1), pk2(b0, b1));
+    const f32x2 p = mul2(x, fma2(mul2(x, x), pk2(0.044715f, 0.044715f), pk2(1.0f, 1.0f)));
+    const f32x2 u = mul2(p, pk2(0.7978845608028654f, 0.7978845608028654f));
+    float u0, u1;
+    upk2(u, u0, u1);
+    const f32x2 h = fma2(pk2(tanh_fast(u0), tanh_fast(u1)), pk2(0.5f, 0.5f), pk2(0.5f, 0.5f));
+    upk2(mul2(x, h), x0, x1);
+}
+
 __device__ __forceinline__ float gelu_fast(float x)
 {
     const float u = 0.7978845608028654f * fmaf(0.044715f * x, x * x, x);
@@ -770,10 +792,8 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
 #pragma unroll
                             for (int k4 = 0; k4 < 4; ++k4) {
                                 const float4 bb = __ldg(bq + k4);
-                                vv[4 * k4 + 0] = gelu_fast(vv[4 * k4 + 0] + bb.x);
-                                vv[4 * k4 + 1] = gelu_fast(vv[4 * k4 + 1] + bb.y);
-                                vv[4 * k4 + 2] = gelu_fast(vv[4 * k4 + 2] + bb.z);
-                                vv[4 * k4 + 3] = gelu_fast(vv[4 * k4 + 3] + bb.w);
+                                gelu_fast2(vv[4 * k4 + 0], vv[4 * k4 + 1], bb.x, bb.y);
+                                gelu_fast2(vv[4 * k4 + 2], vv[4 * k4 + 3], bb.z, bb.w);
                             }
                             uint4 q[2];
 #pragma unroll
