@@ -623,17 +623,19 @@ struct FusedArgs {
     unsigned long long wait_ns;
 };
 
-constexpr int kFS = 4;                         // weight ring stages
+constexpr int kFS = 3;                         // weight ring stages
 constexpr int kFEpi = 8;                       // epilogue warps: two per TMEM lane quadrant
 constexpr int kFThreads = 64 + 32 * kFEpi;
 constexpr uint32_t kActChunk = 128 * 64 * 2;   // [128 rows][64] BF16
-constexpr uint32_t kActBytes = 4 * kActChunk;
+constexpr uint32_t kActBytes = 4 * kActChunk;  // one tile's activations
 constexpr uint32_t kWChunk = 256 * 64 * 2;     // [256 rows][64] BF16
+constexpr int kFBars = 2 * kFS + 12;
 
 __host__ __device__ constexpr size_t fused_smem_bytes()
 {
-    return 1024 + kActBytes + (size_t)kFS * kWChunk + 16 * 8 + 16 + 128 * 4;
+    return 1024 + 2 * (size_t)kActBytes + (size_t)kFS * kWChunk + kFBars * 8 + 16 + 2 * 128 * 4;
 }
+static_assert(fused_smem_bytes() <= 232448, "fused MLP shared memory");
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
@@ -645,6 +647,14 @@ __device__ __forceinline__ void fence_async_shared()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Two tiles in flight per block (slots 0 and 1, each with its own activation
+// buffer and 256-column TMEM accumulator), processed layer by layer in the
+// job order (A, L1), (B, L1), (A, L2), (B, L2), (A, L3), (B, L3) for each pair
+// of tiles A = blockIdx.x + 2 p gridDim.x, B = A + gridDim.x: while the
+// epilogue warps turn one slot's accumulator into the next layer's operand,
+// the tensor core runs the other slot's layer.  Every role walks the same job
+// order; per slot, barrier phases count tiles (input, activation free) or
+// jobs (accumulator full, epilogue done).
 __global__ void __launch_bounds__(kFThreads, 1)
 mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
                  const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmW3, const FusedArgs a)
@@ -652,37 +662,42 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     using namespace tc;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* act = smem;
-    uint8_t* ring = smem + kActBytes;
+    uint8_t* act0 = smem;                                   // slot s at act0 + s kActBytes
+    uint8_t* ring = smem + 2 * kActBytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kFS * kWChunk);
-    // bars: wfull[kFS], wempty[kFS], xfull, accfull, actready, accfree, actfree, done, ydotready
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kFBars);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
-    float* ydot = reinterpret_cast<float*>(tslot + 4);                 // [128]: second half partial sums
+    float* ydot0 = reinterpret_cast<float*>(tslot + 4);    // [2][128]: second-half partial sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t b0 = smem_u32(bars);
     auto wfull = [&](int s) { return b0 + 8 * s; };
     auto wempty = [&](int s) { return b0 + 8 * (kFS + s); };
-    const uint32_t xfull = b0 + 8 * (2 * kFS), accfull = xfull + 8, actready = xfull + 16, accfree = xfull + 24,
-                   actfree = xfull + 32, done = xfull + 40, ydotready = xfull + 48;
+    const uint32_t bslot = b0 + 8 * (2 * kFS);              // six per-slot barriers, two slots each
+    auto xfull = [&](int s) { return bslot + 8 * (0 + s); };
+    auto accfull = [&](int s) { return bslot + 8 * (2 + s); };
+    auto epidone = [&](int s) { return bslot + 8 * (4 + s); };
+    auto actfree = [&](int s) { return bslot + 8 * (6 + s); };
+    auto ydotready = [&](int s) { return bslot + 8 * (8 + s); };
+    const uint32_t done = bslot + 8 * 10;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kFS; ++s) {
             mbar_init(wfull(s), 1);
             mbar_init(wempty(s), 1);
         }
-        mbar_init(xfull, 1);
-        mbar_init(accfull, 1);
-        mbar_init(actready, kFEpi);
-        mbar_init(accfree, kFEpi);
-        mbar_init(actfree, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(xfull(s), 1);
+            mbar_init(accfull(s), 1);
+            mbar_init(epidone(s), kFEpi);
+            mbar_init(actfree(s), 1);
+            mbar_init(ydotready(s), kFEpi / 2);
+        }
         mbar_init(done, 1);
-        mbar_init(ydotready, kFEpi / 2);
         *abort_flag = 0;
         mbar_fence_init();
     }
-    if (warp == 1) tmem_alloc(smem_u32(tslot), 256);
+    if (warp == 1) tmem_alloc(smem_u32(tslot), 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -696,6 +711,8 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         *abort_flag = 1;
         return false;
     };
+    const int n_pairs = (a.n_tiles - (int)blockIdx.x + 2 * (int)gridDim.x - 1) / (2 * (int)gridDim.x);
+    auto tile_of = [&](int pi, int s) { return (int)blockIdx.x + (2 * pi + s) * (int)gridDim.x; };
 
     if (warp == 0) {
         if (lane == 0) {
@@ -703,57 +720,78 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
             tma_prefetch_map(&tmW1);
             tma_prefetch_map(&tmW2);
             tma_prefetch_map(&tmW3);
-            int wc = 0, ti = 0, xi = 0;
+            int wc = 0;
+            int last_x[2] = { -1, -1 };          // pair of the last input copy issued per slot
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x, ++ti) {
-                if (ti > 0 && !(ok = wait(actfree, (ti - 1) & 1))) break;
-                mbar_expect_tx(xfull, 2 * kActChunk);
-                tma_load_2d(smem_u32(act), &tmX, xfull, 0, tile * 128);
-                tma_load_2d(smem_u32(act + kActChunk), &tmX, xfull, 64, tile * 128);
-                ++xi;
+            for (int pi = 0; ok && pi < n_pairs; ++pi) {
+                for (int s = 0; ok && s < 2; ++s) {
+                    const int tile = tile_of(pi, s);
+                    if (tile >= a.n_tiles) continue;
+                    if (pi > 0 && !(ok = wait(actfree(s), (pi - 1) & 1))) break;
+                    uint8_t* act = act0 + s * kActBytes;
+                    mbar_expect_tx(xfull(s), 2 * kActChunk);
+                    tma_load_2d(smem_u32(act), &tmX, xfull(s), 0, tile * 128);
+                    tma_load_2d(smem_u32(act + kActChunk), &tmX, xfull(s), 64, tile * 128);
+                    last_x[s] = pi;
+                }
                 for (int L = 0; ok && L < 3; ++L) {
                     const CUtensorMap* mp = L == 0 ? &tmW1 : (L == 1 ? &tmW2 : &tmW3);
                     const int nk = L == 0 ? 2 : 4;
-                    for (int kc = 0; kc < nk; ++kc, ++wc) {
-                        const int s = wc % kFS;
-                        if (wc >= kFS && !(ok = wait(wempty(s), ((wc / kFS) & 1) ^ 1))) break;
-                        mbar_expect_tx(wfull(s), kWChunk);
-                        tma_load_2d(smem_u32(ring + s * kWChunk), mp, wfull(s), kc * 64, 0);
+                    for (int s = 0; ok && s < 2; ++s) {
+                        if (tile_of(pi, s) >= a.n_tiles) continue;
+                        for (int kc = 0; kc < nk; ++kc, ++wc) {
+                            const int st = wc % kFS;
+                            if (wc >= kFS && !(ok = wait(wempty(st), ((wc / kFS) & 1) ^ 1))) break;
+                            mbar_expect_tx(wfull(st), kWChunk);
+                            tma_load_2d(smem_u32(ring + st * kWChunk), mp, wfull(st), kc * 64, 0);
+                        }
                     }
                 }
             }
             // the copies in flight land before the block can exit
             for (int k = max(0, wc - kFS); k < wc; ++k)
                 if (!mbar_wait(wfull(k % kFS), (k / kFS) & 1, a.wait_ns)) atomicOr(a.err, kErrTimeout);
-            if (xi > 0 && !mbar_wait(xfull, (xi - 1) & 1, a.wait_ns)) atomicOr(a.err, kErrTimeout);
+            for (int s = 0; s < 2; ++s)
+                if (last_x[s] >= 0 && !mbar_wait(xfull(s), last_x[s] & 1, a.wait_ns)) atomicOr(a.err, kErrTimeout);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16_f32(128, 256);
-            int wc = 0, ti = 0;
+            int wc = 0;
             bool ok = true, issued = false;
-            for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x, ++ti) {
-                if (ti > 0 && !(ok = wait(accfree, (ti - 1) & 1))) break;
-                if (!(ok = wait(xfull, ti & 1))) break;
+            for (int pi = 0; ok && pi < n_pairs; ++pi) {
                 for (int L = 0; ok && L < 3; ++L) {
-                    if (L > 0 && !(ok = wait(actready, (2 * ti + L - 1) & 1))) break;
-                    tc_fence_after();
-                    const int nk = L == 0 ? 2 : 4;
-                    for (int kc = 0; kc < nk; ++kc, ++wc) {
-                        const int s = wc % kFS;
-                        if (!(ok = wait(wfull(s), (wc / kFS) & 1))) break;
+                    for (int s = 0; ok && s < 2; ++s) {
+                        if (tile_of(pi, s) >= a.n_tiles) continue;
+                        const int job = 3 * pi + L;              // jobs of this slot so far
+                        if (L == 0) {
+                            // the slot's accumulator is free once the epilogue finished the previous tile
+                            if (pi > 0 && !(ok = wait(epidone(s), (job - 1) & 1))) break;
+                            if (!(ok = wait(xfull(s), pi & 1))) break;
+                        } else {
+                            if (!(ok = wait(epidone(s), (job - 1) & 1))) break;
+                        }
                         tc_fence_after();
-                        const uint64_t ad = sdesc_sw128(smem_u32(act + kc * kActChunk));
-                        const uint64_t bd = sdesc_sw128(smem_u32(ring + s * kWChunk));
+                        const uint8_t* act = act0 + s * kActBytes;
+                        const uint32_t acc = tmem + (uint32_t)(s * 256);
+                        const int nk = L == 0 ? 2 : 4;
+                        for (int kc = 0; kc < nk; ++kc, ++wc) {
+                            const int st = wc % kFS;
+                            if (!(ok = wait(wfull(st), (wc / kFS) & 1))) break;
+                            tc_fence_after();
+                            const uint64_t ad = sdesc_sw128(smem_u32(act + kc * kActChunk));
+                            const uint64_t bd = sdesc_sw128(smem_u32(ring + st * kWChunk));
 #pragma unroll
-                        for (int kk = 0; kk < kBK / 16; ++kk)
-                            mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                        mma_commit(wempty(s));
-                        issued = true;
+                            for (int kk = 0; kk < kBK / 16; ++kk)
+                                mma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                            mma_commit(wempty(st));
+                            issued = true;
+                        }
+                        if (!ok) break;
+                        mma_commit(accfull(s));
+                        if (L == 2) mma_commit(actfree(s));
                     }
-                    if (ok) mma_commit(accfull);
                 }
-                if (ok) mma_commit(actfree);
             }
             // every MMA issued has completed before TMEM is freed
             if (issued) {
@@ -765,105 +803,109 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
         const int r = quad * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
-        int ac = 0, ti = 0;
-        for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ti) {
-            bool ok = true;
-            for (int L = 0; L < 3; ++L) {
-                int w_ok = 1;
-                if (lane == 0) w_ok = wait(accfull, ac & 1) ? 1 : 0;
-                w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
-                ++ac;
-                if (!w_ok) { ok = false; break; }
-                tc_fence_after();
-                if (L < 2) {
-                    const float* bias = L == 0 ? a.b1 : a.b2;
-                    // 64 columns per TMEM load (one wait), then 16-column pieces
+        bool ok = true;
+        for (int pi = 0; ok && pi < n_pairs; ++pi) {
+            for (int L = 0; ok && L < 3; ++L) {
+                for (int s = 0; ok && s < 2; ++s) {
+                    const int tile = tile_of(pi, s);
+                    if (tile >= a.n_tiles) continue;
+                    const int job = 3 * pi + L;
+                    int w_ok = 1;
+                    if (lane == 0) w_ok = wait(accfull(s), job & 1) ? 1 : 0;
+                    w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+                    if (!w_ok) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t tbase = tmem + (uint32_t)(s * 256) + ((uint32_t)(quad * 32) << 16);
+                    uint8_t* act = act0 + s * kActBytes;
+                    float* ydot = ydot0 + s * 128;
+                    if (L < 2) {
+                        const float* bias = L == 0 ? a.b1 : a.b2;
+                        // 64 columns per TMEM load (one wait), then 16-column pieces
 #pragma unroll 1
-                    for (int c2 = 0; c2 < 2; ++c2) {
-                        const int col0 = half * 128 + c2 * 64;
-                        float v[64];
-                        tmem_ld64(tbase + col0, v);
+                        for (int c2 = 0; c2 < 2; ++c2) {
+                            const int col0 = half * 128 + c2 * 64;
+                            float v[64];
+                            tmem_ld64(tbase + col0, v);
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int col = col0 + c * 16;
-                            float* vv = v + 16 * c;
-                            const float4* bq = reinterpret_cast<const float4*>(bias + col);
+                            for (int c = 0; c < 4; ++c) {
+                                const int col = col0 + c * 16;
+                                float* vv = v + 16 * c;
+                                const float4* bq = reinterpret_cast<const float4*>(bias + col);
 #pragma unroll
-                            for (int k4 = 0; k4 < 4; ++k4) {
-                                const float4 bb = __ldg(bq + k4);
-                                gelu_fast2(vv[4 * k4 + 0], vv[4 * k4 + 1], bb.x, bb.y);
-                                gelu_fast2(vv[4 * k4 + 2], vv[4 * k4 + 3], bb.z, bb.w);
+                                for (int k4 = 0; k4 < 4; ++k4) {
+                                    const float4 bb = __ldg(bq + k4);
+                                    gelu_fast2(vv[4 * k4 + 0], vv[4 * k4 + 1], bb.x, bb.y);
+                                    gelu_fast2(vv[4 * k4 + 2], vv[4 * k4 + 3], bb.z, bb.w);
+                                }
+                                uint4 q[2];
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    __nv_bfloat162 p0 = __floats2bfloat162_rn(vv[8 * h + 0], vv[8 * h + 1]);
+                                    __nv_bfloat162 p1 = __floats2bfloat162_rn(vv[8 * h + 2], vv[8 * h + 3]);
+                                    __nv_bfloat162 p2 = __floats2bfloat162_rn(vv[8 * h + 4], vv[8 * h + 5]);
+                                    __nv_bfloat162 p3 = __floats2bfloat162_rn(vv[8 * h + 6], vv[8 * h + 7]);
+                                    q[h].x = *reinterpret_cast<uint32_t*>(&p0);
+                                    q[h].y = *reinterpret_cast<uint32_t*>(&p1);
+                                    q[h].z = *reinterpret_cast<uint32_t*>(&p2);
+                                    q[h].w = *reinterpret_cast<uint32_t*>(&p3);
+                                }
+                                const int kc = col >> 6, j = (col & 63) >> 3;
+                                uint8_t* rowp = act + kc * kActChunk + r * 128;
+                                *reinterpret_cast<uint4*>(rowp + (((j) ^ (r & 7)) << 4)) = q[0];
+                                *reinterpret_cast<uint4*>(rowp + (((j + 1) ^ (r & 7)) << 4)) = q[1];
                             }
-                            uint4 q[2];
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                __nv_bfloat162 p0 = __floats2bfloat162_rn(vv[8 * h + 0], vv[8 * h + 1]);
-                                __nv_bfloat162 p1 = __floats2bfloat162_rn(vv[8 * h + 2], vv[8 * h + 3]);
-                                __nv_bfloat162 p2 = __floats2bfloat162_rn(vv[8 * h + 4], vv[8 * h + 5]);
-                                __nv_bfloat162 p3 = __floats2bfloat162_rn(vv[8 * h + 6], vv[8 * h + 7]);
-                                q[h].x = *reinterpret_cast<uint32_t*>(&p0);
-                                q[h].y = *reinterpret_cast<uint32_t*>(&p1);
-                                q[h].z = *reinterpret_cast<uint32_t*>(&p2);
-                                q[h].w = *reinterpret_cast<uint32_t*>(&p3);
-                            }
-                            const int kc = col >> 6, j = (col & 63) >> 3;
-                            uint8_t* rowp = act + kc * kActChunk + r * 128;
-                            *reinterpret_cast<uint4*>(rowp + (((j) ^ (r & 7)) << 4)) = q[0];
-                            *reinterpret_cast<uint4*>(rowp + (((j + 1) ^ (r & 7)) << 4)) = q[1];
                         }
-                    }
-                    fence_async_shared();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(actready);
-                } else {
-                    float part = 0.0f;
-#pragma unroll 1
-                    for (int c2 = 0; c2 < 2; ++c2) {
-                        const int col0 = half * 128 + c2 * 64;
-                        float v[64];
-                        tmem_ld64(tbase + col0, v);
-                        const float4* bq = reinterpret_cast<const float4*>(a.b3 + col0);
-                        const float4* wq = reinterpret_cast<const float4*>(a.w4 + col0);
-#pragma unroll
-                        for (int k4 = 0; k4 < 16; ++k4) {
-                            const float4 bb = __ldg(bq + k4), ww = __ldg(wq + k4);
-                            part = fmaf(gelu_f(v[4 * k4 + 0] + bb.x), ww.x, part);
-                            part = fmaf(gelu_f(v[4 * k4 + 1] + bb.y), ww.y, part);
-                            part = fmaf(gelu_f(v[4 * k4 + 2] + bb.z), ww.z, part);
-                            part = fmaf(gelu_f(v[4 * k4 + 3] + bb.w), ww.w, part);
-                        }
-                    }
-                    tc_fence_before();
-                    if (half == 1) {
-                        // the second column half hands its partial sums over (bounded wait on the other side)
-                        ydot[r] = part;
+                        fence_async_shared();
+                        tc_fence_before();
                         __syncwarp();
-                        if (lane == 0) {
-                            mbar_arrive(accfree);
-                            mbar_arrive(ydotready);
-                        }
+                        if (lane == 0) mbar_arrive(epidone(s));
                     } else {
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(accfree);
-                        int y_ok = 1;
-                        if (lane == 0) y_ok = wait(ydotready, ti & 1) ? 1 : 0;
-                        y_ok = __shfl_sync(0xffffffffu, y_ok, 0);
-                        if (!y_ok) { ok = false; break; }
-                        const long long row = (long long)tile * 128 + r;
-                        if (row < a.n) a.y[row] = part + ydot[r] + *a.b4;
+                        float part = 0.0f;
+#pragma unroll 1
+                        for (int c2 = 0; c2 < 2; ++c2) {
+                            const int col0 = half * 128 + c2 * 64;
+                            float v[64];
+                            tmem_ld64(tbase + col0, v);
+                            const float4* bq = reinterpret_cast<const float4*>(a.b3 + col0);
+                            const float4* wq = reinterpret_cast<const float4*>(a.w4 + col0);
+#pragma unroll
+                            for (int k4 = 0; k4 < 16; ++k4) {
+                                const float4 bb = __ldg(bq + k4), ww = __ldg(wq + k4);
+                                part = fmaf(gelu_f(v[4 * k4 + 0] + bb.x), ww.x, part);
+                                part = fmaf(gelu_f(v[4 * k4 + 1] + bb.y), ww.y, part);
+                                part = fmaf(gelu_f(v[4 * k4 + 2] + bb.z), ww.z, part);
+                                part = fmaf(gelu_f(v[4 * k4 + 3] + bb.w), ww.w, part);
+                            }
+                        }
+                        tc_fence_before();
+                        if (half == 1) {
+                            // the second column half hands its partial sums over (bounded wait on the other side)
+                            ydot[r] = part;
+                            __syncwarp();
+                            if (lane == 0) {
+                                mbar_arrive(epidone(s));
+                                mbar_arrive(ydotready(s));
+                            }
+                        } else {
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(epidone(s));
+                            int y_ok = 1;
+                            if (lane == 0) y_ok = wait(ydotready(s), pi & 1) ? 1 : 0;
+                            y_ok = __shfl_sync(0xffffffffu, y_ok, 0);
+                            if (!y_ok) { ok = false; break; }
+                            const long long row = (long long)tile * 128 + r;
+                            if (row < a.n) a.y[row] = part + ydot[r] + *a.b4;
+                        }
                     }
                 }
             }
-            if (!ok) break;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, 512);
     }
 }
 
