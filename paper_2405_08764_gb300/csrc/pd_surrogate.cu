@@ -21,12 +21,15 @@ constexpr int kStatic = 10;
 
 __device__ __forceinline__ void diff_basis(const double u[5], double e[5])
 {
-    // offsets -2..2 -> value, first, second, third and fourth differences
+    // offsets -2..2 -> value, first, second, third and fourth differences, from
+    // the mirrored sums p_k and differences m_k (nine FP64 operations, not twelve)
+    const double p1 = u[3] + u[1], p2 = u[4] + u[0];
+    const double m1 = u[3] - u[1], m2 = u[4] - u[0];
     e[0] = u[2];
-    e[1] = 0.5 * (u[3] - u[1]);
-    e[2] = u[3] - 2.0 * u[2] + u[1];
-    e[3] = 0.5 * (u[4] - 2.0 * u[3] + 2.0 * u[1] - u[0]);
-    e[4] = u[4] - 4.0 * u[3] + 6.0 * u[2] - 4.0 * u[1] + u[0];
+    e[1] = 0.5 * m1;
+    e[2] = fma(-2.0, u[2], p1);
+    e[3] = fma(0.5, m2, -m1);
+    e[4] = fma(6.0, u[2], fma(-4.0, p1, p2));
 }
 
 // One patch per thread: the 5x5 stencil (xi wraps on periodic grids, clamps
@@ -70,13 +73,21 @@ __global__ void features_kernel(const InstDev I, const double* __restrict__ U, c
         diff_basis(u, e);
         for (int qo = 0; qo < 5; ++qo) D[5 * qo + po] = e[qo];
     }
-    double s = 0.0;
-    for (int k = 1; k < 25; ++k) s = fmax(s, fabs(D[k]));
+    // s = max |D[k]| (k >= 1) exactly, compared as integers: for doubles with the
+    // sign bit cleared the bit patterns order like the magnitudes (FP64
+    // comparisons would issue on the slow FP64 pipe)
+    unsigned long long sb = 0ull;
+    for (int k = 1; k < 25; ++k) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(D[k]) & 0x7fffffffffffffffull;
+        sb = b > sb ? b : sb;
+    }
+    const double s = __longlong_as_double((long long)sb);
     float x[kIn];
-    const double den = fabs(D[0]) + s;
-    x[0] = den > 0.0 ? (float)(D[0] / den) : 0.0f;
-    // the normalised differences need FP32 precision only: one FP64 reciprocal
-    const float inv_s = s > 0.0 ? (float)(1.0 / s) : 0.0f;
+    // the normalised features need FP32 precision only: FP32 quotients
+    const float sf = (float)s, d0 = (float)D[0];
+    const float den = fabsf(d0) + sf;
+    x[0] = den > 0.0f ? d0 / den : 0.0f;
+    const float inv_s = sf > 0.0f ? 1.0f / sf : 0.0f;
     for (int k = 1; k < 25; ++k) x[k] = (float)D[k] * inv_s;
     const float* st = stat + (long long)p * kStatic;
     x[25] = st[0] * x[2];
