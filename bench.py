@@ -117,30 +117,27 @@ class ClockSampler:
 
 def cpu_baseline(prob: dict, target_s: float = 12.0) -> dict:
     """The CPU oracle as it stands on the host cores, on a bounded sample of the
-    workload: the 200 macro steps of the same problem, repeated from the
-    initial field until about target_s seconds of CPU work have been done."""
+    workload: macro steps of the same problem from the initial field, in chunks
+    of 20, until about target_s seconds of CPU work have been done (one
+    untimed chunk first)."""
     import oracle
     o = oracle.Oracle(prob)
     U0 = o.init_field()
     dtm = 0.5 * o.dt_macro()
     dt = o.dt_micro()
-    n_macro = int(prob.get("n_macro") or 200)
     per_step = o.n_patch * o.mx * o.my * o.s.k_micro
+    chunk = 20
+    o.step(U0, 0.0, dtm, chunk, dt)
+    total = 0
     t = time.perf_counter()
-    o.step(U0, 0.0, dtm, 1, dt)
-    one = max(time.perf_counter() - t, 1e-3)
-    total = max(1, int(target_s / one))
-    reps, rest = divmod(total, n_macro)
-    t = time.perf_counter()
-    for _ in range(reps):
-        o.step(U0, 0.0, dtm, n_macro, dt)
-    if rest:
-        o.step(U0, 0.0, dtm, rest, dt)
+    while time.perf_counter() - t < target_s:
+        o.step(U0, 0.0, dtm, chunk, dt)
+        total += chunk
     el = time.perf_counter() - t
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": total * per_step / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d macro steps of the benchmark workload (%d full 200-step runs + %d steps, %.1f s)"
-                      % (total, reps, rest, el)}
+            "sample": "%d macro steps of the benchmark workload in chunks of %d from the initial field (%.1f s)"
+                      % (total, chunk, el)}
 
 
 def dist_env():
