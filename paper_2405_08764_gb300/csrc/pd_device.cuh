@@ -20,6 +20,20 @@ __device__ __forceinline__ void load_vec4(const real* __restrict__ p, real& x, r
     }
 }
 
+// four consecutive values of a 16-byte aligned shared array
+template <typename real>
+__device__ __forceinline__ void load_vec4_shared(const real* p, real& x, real& y, real& z, real& w)
+{
+    if constexpr (sizeof(real) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        x = q.x; y = q.y; z = q.z; w = q.w;
+    } else {
+        const double2 q0 = *reinterpret_cast<const double2*>(p);
+        const double2 q1 = *(reinterpret_cast<const double2*>(p) + 1);
+        x = q0.x; y = q0.y; z = q1.x; w = q1.y;
+    }
+}
+
 __device__ __forceinline__ int wrap_col(const InstDev& I, int i)
 {
     if (!I.periodic) return i;

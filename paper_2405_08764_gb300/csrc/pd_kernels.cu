@@ -256,11 +256,14 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
     __shared__ double cs[PPB][9];
     __shared__ double tabA[PPB][32], tabB[PPB][32], tabQ[PPB][32];
     __shared__ double ecoef[PPB][4][3];      // edge data as a quadratic along each edge
-    __shared__ real csr[PPB][9];             // coefficients in the working precision
+    __shared__ __align__(16) real csr[PPB][12];   // coefficients in the working precision (padded)
     __shared__ double gs[34], gt[34];        // micro coordinates s_a, t_b for a, b = -1 .. m
     __shared__ real gsr[34], gtr[34];        // the same in the working precision
     __shared__ int4 pij_s[PPB];              // (i, j, ic, jr) of every patch of the block
+    __shared__ long long recb_s[PPB];        // record index of point (0, 0) of every patch
+    __shared__ long long ob_s[PPB];          // micro-state index of point (0, 0)
     __shared__ int ab_s[1024];               // (b << 16) | a of in-patch point tl
+    __shared__ int se_s[4 * 34];             // (side << 8) | e of edge entry tl
     const int p0 = blockIdx.x * ppb;
     const int mm = I.mx * I.my;
     // instance constants in the working precision, converted once per block
@@ -281,19 +284,24 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
         const int b = t / I.mx;
         ab_s[t] = (b << 16) | (t - b * I.mx);
     }
+    for (int t = threadIdx.x; t < 4 * edge_stride; t += blockDim.x) {
+        const int side = t / edge_stride;
+        se_s[t] = (side << 8) | (t - side * edge_stride);
+    }
     for (int t = threadIdx.x; t < ppb; t += blockDim.x) {
         int i = 0, j = 0, ic = 0, jr = 0;
         if (p0 + t < I.n_patch) patch_ij(I, p0 + t, i, j, ic, jr);
         pij_s[t] = make_int4(i, j, ic, jr);
+        recb_s[t] = (((long long)jr * I.my) * I.ncols + ic) * I.mx;
+        ob_s[t] = I.pt_off + (long long)(p0 + t) * mm;
     }
+    __syncthreads();
     for (int t = threadIdx.x; t < ppb * 9; t += blockDim.x) {
         const int q = t / 9, k = t - q * 9;
-        const int p = p0 + q;
         double v = 0.0;
-        if (p < I.n_patch) {
-            int i, j, ic, jr;
-            patch_ij(I, p, i, j, ic, jr);
-            v = stencil_slot<false>(I, U, i, j, k);
+        if (p0 + q < I.n_patch) {
+            const int4 pq = pij_s[q];
+            v = stencil_slot<false>(I, U, pq.x, pq.y, k);
         }
         sl[q][k] = v;
     }
@@ -349,25 +357,30 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
     // in-patch index tl advanced without division; (a, b) from the table
     int q = 0, tl = threadIdx.x;
     while (tl >= mm) { tl -= mm; ++q; }
+    const int rowstride = I.ncols * I.mx;
     for (; q < ppb; ) {
         const int p = p0 + q;
         if (p < I.n_patch) {
-            const int4 pq = pij_s[q];
-            const int i = pq.x, j = pq.y, ic = pq.z, jr = pq.w;
-            (void)i; (void)j;
             const real* cq = csr[q];
-            Poly<real> cr = { cq[0], cq[1], cq[2], cq[3], cq[4], cq[5], cq[6], cq[7], cq[8] };
+            real c0, c1, c2, c3, c4, c5, c6, c7, c8, c9, c10, c11;
+            load_vec4_shared(cq, c0, c1, c2, c3);
+            load_vec4_shared(cq + 4, c4, c5, c6, c7);
+            load_vec4_shared(cq + 8, c8, c9, c10, c11);
+            (void)c9; (void)c10; (void)c11;
+            Poly<real> cr = { c0, c1, c2, c3, c4, c5, c6, c7, c8 };
             const int ab = ab_s[tl];
             const int b = ab >> 16, a = ab & 0xffff;
             real v[8];
             if (I.coef_mode != COEF_RECORDS) {
-                table_coeffs_k<real>(I, kc, ic, a, jr, b, v);
+                const int4 pq = pij_s[q];
+                table_coeffs_k<real>(I, kc, pq.z, a, pq.w, b, v);
                 v[6] = real(0);
             } else {
-                const real* rr = rec + ((((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a) * 8;
-                for (int k = 0; k < 8; ++k) v[k] = rr[k];
+                const real* rr = rec + (recb_s[q] + b * rowstride + a) * 8;
+                load_vec4<real>(rr, v[0], v[1], v[2], v[3]);
+                load_vec4<real>(rr + 4, v[4], v[5], v[6], v[7]);
             }
-            const long long o = I.pt_off + (long long)p * mm + tl;
+            const long long o = ob_s[q] + tl;
             u0[o] = fma(gt[b + 1], tabB[q][a], tabA[q][a] + tabQ[q][b]);
             PointW<real> pw = point_weights_k<real>(I, kc, v[0], v[1], v[2], v[3], v[4], v[5]);
             r_out[o] = burst_forcing<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
@@ -378,18 +391,26 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
     }
     // edge data of eq. (edge) = d/dxi, d/deta of the interpolant P at the edges
     // (dense over (patch, side, entry))
-    for (int t = threadIdx.x; t < ppb * 4 * edge_stride; t += blockDim.x) {
-        const int qq = t / (4 * edge_stride), tl = t - qq * 4 * edge_stride;
-        const int p = p0 + qq;
-        if (p >= I.n_patch) continue;
-        const int side = tl / edge_stride, e = tl - side * edge_stride;
-        const double* ec = ecoef[qq][side];
-        double val = 0.0;
-        if ((side < 2 && e < I.my + 2) || (side >= 2 && e < I.mx + 2)) {
-            const double x = side < 2 ? gt[e] : gs[e];
-            val = fma(fma(ec[2], x, ec[1]), x, ec[0]);
+    {
+        const int ne = 4 * edge_stride;
+        int qq = 0, tle = threadIdx.x;
+        while (tle >= ne) { tle -= ne; ++qq; }
+        for (; qq < ppb; ) {
+            const int p = p0 + qq;
+            if (p < I.n_patch) {
+                const int se = se_s[tle];
+                const int side = se >> 8, e = se & 0xff;
+                const double* ec = ecoef[qq][side];
+                double val = 0.0;
+                if ((side < 2 && e < I.my + 2) || (side >= 2 && e < I.mx + 2)) {
+                    const double x = side < 2 ? gt[e] : gs[e];
+                    val = fma(fma(ec[2], x, ec[1]), x, ec[0]);
+                }
+                edge[I.e_off + ((long long)p * 4 + side) * edge_stride + e] = val;
+            }
+            tle += blockDim.x;
+            while (tle >= ne) { tle -= ne; ++qq; }
         }
-        edge[I.e_off + ((long long)p * 4 + side) * edge_stride + e] = val;
     }
     for (int q = threadIdx.x; q < ppb; q += blockDim.x) {
         const int p = p0 + q;
