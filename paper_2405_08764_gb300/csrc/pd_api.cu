@@ -988,6 +988,7 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     s.tau = s.d.k_micro * s.dt;
     s.dtm_sugg = mrate > 0 ? 0.5 / mrate : s.tau;
     s.I.dt = s.dt; s.I.tau = s.tau;
+    fill_float_consts(s.I);
     s.I.inv_tau = 1.0 / s.tau;
     s.I.inv_nn = 1.0 / ((double)(s.d.m_xi - 1) * (s.d.m_eta - 1));
     if (!use_tables) {

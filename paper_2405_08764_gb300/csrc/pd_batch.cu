@@ -47,9 +47,11 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
 
     const RealConsts<real> kc = real_consts<real>(I);
     PatchGeo<real> g;
-    g.hx = (real)I.hx; g.hy = (real)I.hy; g.dx = kc.dx; g.dy = kc.dy;
+    if constexpr (sizeof(real) == 4) { g.hx = I.kf[13]; g.hy = I.kf[14]; }
+    else { g.hx = I.hx; g.hy = I.hy; }
+    g.dx = kc.dx; g.dy = kc.dy;
     g.nx = M - 1; g.ny = M - 1;
-    const real dt = (real)I.dt;
+    const real dt = sizeof(real) == 4 ? (real)I.kf[15] : (real)I.dt;
     const real* rec = static_cast<const real*>(I.rec);
     const long long rowstride = (long long)I.ncols * M;
     const long long base = (long long)jr * M * rowstride + (long long)icl * M + a;

@@ -62,11 +62,23 @@ struct InstDev {
     double inv_dx, inv_dy, inv_dx2, inv_dy2, inv_4dxdy;
     int ppw;                     // patches per warp in the batched kernel (<= 32 / mx)
     int micro;                   // pd_micro_solver
+    // FP32 copies of the instance constants, converted once on the host (a
+    // double -> float conversion issues on the slow FP64 pipe): K11, K12, K22,
+    // v1, v2, f0, 1/dx, 1/dy, 1/dx^2, 1/dy^2, 1/(4 dx dy), dx, dy, hx, hy, dt
+    float kf[16];
     const void* arec_c;          // ADI line records, eta lines (8 per point, see pd_adi.cu)
     const void* arec_r;          // ADI line records, xi lines (8 per point, patch-transposed)
 };
 
 enum CoefMode { COEF_RECORDS = 0, COEF_SEPARABLE = 1, COEF_POLAR = 2 };
+
+// fill InstDev::kf from the FP64 constants (host side, after every change of them)
+inline void fill_float_consts(InstDev& I)
+{
+    const double v[16] = { I.K11, I.K12, I.K22, I.v1, I.v2, I.f0, I.inv_dx, I.inv_dy, I.inv_dx2, I.inv_dy2,
+                           I.inv_4dxdy, I.dx, I.dy, I.hx, I.hy, I.dt };
+    for (int k = 0; k < 16; ++k) I.kf[k] = (float)v[k];
+}
 
 // Transformed coefficients (alpha, beta, gamma, nu, omega, phi) for constant K, v,
 // f from 1-D metric tables (eq. Computational_Problem with the operator of the
@@ -218,12 +230,19 @@ template <typename real>
 __device__ __forceinline__ RealConsts<real> real_consts(const InstDev& I)
 {
     RealConsts<real> k;
-    k.K11 = (real)I.K11; k.K12 = (real)I.K12; k.K22 = (real)I.K22;
-    k.v1 = (real)I.v1; k.v2 = (real)I.v2; k.f0 = (real)I.f0;
-    k.idx = (real)I.inv_dx; k.idy = (real)I.inv_dy; k.idx2 = (real)I.inv_dx2; k.idy2 = (real)I.inv_dy2;
-    k.i4dxdy = (real)I.inv_4dxdy; k.dx = (real)I.dx; k.dy = (real)I.dy;
-    if constexpr (sizeof(real) == 4) { k.col = I.col_tab_f; k.row = I.row_tab_f; }
-    else { k.col = I.col_tab; k.row = I.row_tab; }
+    if constexpr (sizeof(real) == 4) {
+        k.K11 = I.kf[0]; k.K12 = I.kf[1]; k.K22 = I.kf[2];
+        k.v1 = I.kf[3]; k.v2 = I.kf[4]; k.f0 = I.kf[5];
+        k.idx = I.kf[6]; k.idy = I.kf[7]; k.idx2 = I.kf[8]; k.idy2 = I.kf[9];
+        k.i4dxdy = I.kf[10]; k.dx = I.kf[11]; k.dy = I.kf[12];
+        k.col = I.col_tab_f; k.row = I.row_tab_f;
+    } else {
+        k.K11 = I.K11; k.K12 = I.K12; k.K22 = I.K22;
+        k.v1 = I.v1; k.v2 = I.v2; k.f0 = I.f0;
+        k.idx = I.inv_dx; k.idy = I.inv_dy; k.idx2 = I.inv_dx2; k.idy2 = I.inv_dy2;
+        k.i4dxdy = I.inv_4dxdy; k.dx = I.dx; k.dy = I.dy;
+        k.col = I.col_tab; k.row = I.row_tab;
+    }
     return k;
 }
 
