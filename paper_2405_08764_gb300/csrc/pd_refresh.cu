@@ -105,6 +105,27 @@ refresh_kernel(const InstDev I, const double* __restrict__ D, const real* __rest
     if (p >= I.n_patch) return;                      // whole warp
     const int jr = p / I.ncols, ic = p - jr * I.ncols;
     const int i = I.i0 + ic, j = 1 + jr;
+    const int n_edge = 2 * I.mx + 2 * (I.my - 2);
+    const int nx = I.mx - 1, ny = I.my - 1;
+    auto edge_point = [&](int e, int& a, int& b) {
+        if (e < I.mx) { a = e; b = 0; }
+        else if (e < 2 * I.mx) { a = e - I.mx; b = ny; }
+        else { const int t = e - 2 * I.mx; b = 1 + (t >> 1); a = (t & 1) ? nx : 0; }
+    };
+    // the first edge point's record and forcing do not depend on D: load them
+    // before the stencil so that the memory latencies overlap
+    int a0 = 0, b0 = 0;
+    real rc0[6] = { real(0), real(0), real(0), real(0), real(0), real(0) }, r0v = real(0);
+    real* const rbase = r + I.pt_off + (long long)p * I.mx * I.my;
+    if (lane < n_edge) {
+        edge_point(lane, a0, b0);
+        const real* cr = rec + ((((long long)jr * I.my + b0) * I.ncols + ic) * I.mx + a0) * 8;
+        real c6, c7;
+        load_vec4<real>(cr, rc0[0], rc0[1], rc0[2], rc0[3]);
+        load_vec4<real>(cr + 4, rc0[4], rc0[5], c6, c7);
+        (void)c6; (void)c7;
+        r0v = rbase[b0 * I.mx + a0];
+    }
     const real sv = lane < 9 ? (real)stencil_slot<false>(I, D, i, j, lane) : real(0);
     real ck = real(0);                               // lane k: coefficient k (the constant term is not needed)
     {
@@ -119,17 +140,21 @@ refresh_kernel(const InstDev I, const double* __restrict__ D, const real* __rest
     for (int k = 0; k < 9; ++k) c[k] = __shfl_sync(kFull, ck, k);
     const RealConsts<real> kc = kc_s;
     const PatchGeo<real> g = g_s;
-    const int nx = g.nx, ny = g.ny;
-    const int n_edge = 2 * I.mx + 2 * (I.my - 2);
     for (int e = lane; e < n_edge; e += 32) {
         int a, b;
-        if (e < I.mx) { a = e; b = 0; }
-        else if (e < 2 * I.mx) { a = e - I.mx; b = ny; }
-        else { const int t = e - 2 * I.mx; b = 1 + (t >> 1); a = (t & 1) ? nx : 0; }
-        const long long pt = (((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a;
-        const real* cr = rec + pt * 8;
-        const real be = cr[1];
-        const PointW<real> w = point_weights_k<real>(I, kc, cr[0], be, cr[2], cr[3], cr[4], cr[5]);
+        real cc[6], rv;
+        if (e == lane) {
+            a = a0; b = b0;
+            for (int k = 0; k < 6; ++k) cc[k] = rc0[k];
+            rv = r0v;
+        } else {
+            edge_point(e, a, b);
+            const real* cr = rec + ((((long long)jr * I.my + b) * I.ncols + ic) * I.mx + a) * 8;
+            for (int k = 0; k < 6; ++k) cc[k] = cr[k];
+            rv = rbase[b * I.mx + a];
+        }
+        const real be = cc[1];
+        const PointW<real> w = point_weights_k<real>(I, kc, cc[0], be, cc[2], cc[3], cc[4], cc[5]);
         real v = real(0);
         if (a == 0) v += w.wW * ghost_delta(c, g, -1, b);
         if (a == nx) v += w.wE * ghost_delta(c, g, nx + 1, b);
@@ -142,7 +167,7 @@ refresh_kernel(const InstDev I, const double* __restrict__ D, const real* __rest
             if (out(a + 1, b - 1)) v -= w.wX * ghost_delta(c, g, a + 1, b - 1);
             if (out(a - 1, b + 1)) v -= w.wX * ghost_delta(c, g, a - 1, b + 1);
         }
-        r[I.pt_off + (long long)p * I.mx * I.my + b * I.mx + a] += v;
+        rbase[b * I.mx + a] = rv + v;
     }
 }
 
