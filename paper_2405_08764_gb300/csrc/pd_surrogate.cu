@@ -158,16 +158,24 @@ __global__ void sumsq_kernel(int n, const double* __restrict__ F1, double* __res
 // The residual check: keep F_hat = yhat * scale when |F_hat - F1| <= eps (|F1| + rho),
 // rho = sqrt(sum F1^2 / n), writing its restricted change F_hat tau; append the
 // other patches to the fallback list.
-__global__ void check_kernel(int n, const float* __restrict__ yhat, const double* __restrict__ scale,
-                             const double* __restrict__ F1v, const double* __restrict__ sumsq, double tau, double eps,
-                             double* __restrict__ dUf, int* __restrict__ list, int* __restrict__ list_n,
-                             unsigned long long* __restrict__ n_fb)
+// One thread per patch, 256 per block: the RMS floor once per block, the
+// fallback patches of the block packed by warp ballots and one pair of atomics
+// per block (a single counter for every warp of the grid was the bottleneck)
+__global__ void __launch_bounds__(256)
+check_kernel(int n, const float* __restrict__ yhat, const double* __restrict__ scale,
+             const double* __restrict__ F1v, const double* __restrict__ sumsq, double tau, double eps,
+             double* __restrict__ dUf, int* __restrict__ list, int* __restrict__ list_n,
+             unsigned long long* __restrict__ n_fb)
 {
+    __shared__ double rho_s;
+    __shared__ int cnt_s[8], base_s;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) rho_s = sqrt(*sumsq / (double)n);
+    __syncthreads();
     bool fb = false;
     if (p < n) {
-        const double rho = sqrt(*sumsq / (double)n);
+        const double rho = rho_s;
         const double F1 = F1v[p];
         const double Fh = (double)yhat[p] * scale[p];
         const bool ok = eps >= 0.0 && isfinite(Fh) && fabs(Fh - F1) <= eps * (fabs(F1) + rho);
@@ -175,15 +183,20 @@ __global__ void check_kernel(int n, const float* __restrict__ yhat, const double
         fb = !ok;
     }
     const unsigned b = __ballot_sync(0xffffffffu, fb);
-    if (b) {
-        int base = 0;
-        if (lane == 0) {
-            base = atomicAdd(list_n, __popc(b));
-            atomicAdd(n_fb, (unsigned long long)__popc(b));
+    if (lane == 0) cnt_s[warp] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int c = cnt_s[w];
+            cnt_s[w] = tot;
+            tot += c;
         }
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (fb) list[base + __popc(b & ((1u << lane) - 1u))] = p;
+        base_s = tot ? atomicAdd(list_n, tot) : 0;
+        if (tot) atomicAdd(n_fb, (unsigned long long)tot);
     }
+    __syncthreads();
+    if (fb) list[base_s + cnt_s[warp] + __popc(b & ((1u << lane) - 1u))] = p;
 }
 
 __global__ void maxabs_kernel(long long n, const double* __restrict__ U, unsigned long long* __restrict__ out)
