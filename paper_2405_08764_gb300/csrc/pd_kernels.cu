@@ -92,6 +92,9 @@ patch_warp_kernel(const InstDev I, const double* __restrict__ Uc, double* __rest
     real* ds_s = reinterpret_cast<real*>(dyn_smem);   // TSRC: K entries
 
     const int K = (MODE == MODE_FUSED) ? I.K : k_steps;
+    // list-driven restricted changes: the grid covers every patch, the list only
+    // some; blocks past the list's end leave before the shared-memory prologue
+    if (MODE == MODE_DU && list && (int)(blockIdx.x * (blockDim.x >> 5)) * P >= *list_n) return;
     if (LIFT) {
         for (int t = threadIdx.x; t < 81; t += blockDim.x) lw_s[t / 9][t % 9] = I.lw[t / 9][t % 9];
         for (int t = threadIdx.x; t < 27; t += blockDim.x) { slot_s[t / 3][t % 3] = I.c2slot[t / 3][t % 3]; cw_s[t / 3][t % 3] = I.c2w[t / 3][t % 3]; }
