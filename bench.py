@@ -147,6 +147,24 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_workload(rank: int, ws: int) -> dict:
+    """The benchmark workload of one rank: the workload itself on one GPU; with
+    several ranks every rank runs an independent replica with its own seeded
+    source amplitudes (weak scaling, no data-path collective)."""
+    from paper_2405_08764_gb300 import workloads as W
+    return W.bench_workload() if ws == 1 else W.c2_heterogeneous(seed=2 + rank)
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it); ms unchanged without a group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -676,10 +694,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    prob = W.bench_workload()
-    if ws > 1:
-        # independent replica per rank: its own seeded source amplitudes
-        prob = W.c2_heterogeneous(seed=2 + rank)
+    prob = replica_workload(rank, ws)
     g = Grid(prob, prec="fp32")
     info = g.info()
     n_macro = prob["n_macro"]
@@ -719,11 +734,8 @@ def run_gpu(args):
     time.sleep(0.3)
     clocks = sampler.stop()
     g.sync()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     value = ws * updates * args.steps / (ms / 1e3)
 
@@ -741,11 +753,7 @@ def run_gpu(args):
         Uout.copy_(Ud, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     e2e = ws * updates * args.steps / (e2e_ms / 1e3)
     nbytes = U0.numel() * 8
 

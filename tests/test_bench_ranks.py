@@ -1,0 +1,90 @@
+"""The multi-rank path of bench.py on the CPU: two gloo ranks agree on the
+slowest rank's time, and every rank runs its own seeded replica of the
+benchmark workload (same shape, distinct source amplitudes, rank 0 equal to
+the one-GPU workload)."""
+import hashlib
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+torch = pytest.importorskip("torch")
+import torch.distributed as tdist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port() -> int:
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _summary(amp):
+    amp = np.ascontiguousarray(amp, dtype=np.float64)
+    return amp.shape, hashlib.sha256(amp.tobytes()).hexdigest(), float(amp.min()), float(amp.max())
+
+
+def _rank_main(rank, ws, port, times, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import bench
+    tdist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        got_ws, got_rank, got_local = bench.dist_env()
+        ms = bench.max_over_ranks(times[rank], tdist, "cpu")
+        amp = np.asarray(bench.replica_workload(got_rank, got_ws)["src_amp"], dtype=np.float64)
+        tdist.barrier()
+        # a digest, not the array: a pipe holds only a few tens of KB before a put blocks
+        out.put((rank, got_ws, got_local, ms, _summary(amp)))
+    finally:
+        tdist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time_and_run_distinct_replicas():
+    ws = 2
+    times = [3.25, 7.5]
+    ctx = mp.get_context("spawn")
+    out = ctx.SimpleQueue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, port, times, out)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=180)
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+            p.join()
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    res = sorted(out.get() for _ in range(ws))
+    assert [r[0] for r in res] == [0, 1]
+    for rank, got_ws, got_local, ms, _ in res:
+        assert got_ws == ws and got_local == rank
+        assert ms == max(times)
+    import bench
+    single = _summary(bench.replica_workload(0, 1)["src_amp"])
+    s0, s1 = res[0][4], res[1][4]
+    assert s0[0] == s1[0] == single[0]
+    assert s0[1] == single[1]                 # rank 0 runs the one-GPU workload itself
+    assert s1[1] != s0[1]                     # rank 1 its own amplitudes
+    assert s1[2] >= 0.5 and s1[3] <= 1.5
+
+
+def test_max_over_ranks_without_a_group_is_the_identity():
+    import bench
+    assert bench.max_over_ranks(4.5, None, "cpu") == 4.5
+
+
+def test_replicas_are_deterministic_and_keep_the_workload_shape():
+    import bench
+    a = bench.replica_workload(3, 4)
+    b = bench.replica_workload(3, 4)
+    one = bench.replica_workload(0, 1)
+    np.testing.assert_array_equal(np.asarray(a["src_amp"]), np.asarray(b["src_amp"]))
+    for key in ("n_xi", "n_eta", "m_xi", "m_eta", "k_micro", "n_macro"):
+        assert a[key] == one[key], key
