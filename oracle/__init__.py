@@ -162,6 +162,7 @@ class Oracle:
         s.q_refresh = int(p.get("q_refresh") or 1)
         self.s = s
         self.L = L
+        self._dt_micro = None
         rc = L.orc_validate(C.byref(s))
         if rc != 0:
             raise ValueError("invalid problem (code %d)" % rc)
@@ -195,7 +196,10 @@ class Oracle:
 
     # -- sizes ---------------------------------------------------------------
     def dt_micro(self):
-        return self.L.orc_dt_micro(C.byref(self.s))
+        # a minimum over every micro point of the instance: computed once
+        if self._dt_micro is None:
+            self._dt_micro = self.L.orc_dt_micro(C.byref(self.s))
+        return self._dt_micro
 
     def dt_macro(self):
         return self.L.orc_dt_macro(C.byref(self.s))

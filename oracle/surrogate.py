@@ -206,11 +206,17 @@ def basis_1d(u):
                      u2 - 4.0 * u1 + 6.0 * u0 - 4.0 * um1 + um2], -1)
 
 
-def stencils(o: Oracle, U):
-    """The 5x5 macro stencil of every patch: [n_patch, 5 (q: eta), 5 (p: xi)]."""
+def _patch_nodes(o: Oracle, sel):
+    I, J = o.patch_nodes()
+    return (I, J) if sel is None else (I[sel], J[sel])
+
+
+def stencils(o: Oracle, U, sel=None):
+    """The 5x5 macro stencil of every patch (or of the patches sel):
+    [n, 5 (q: eta), 5 (p: xi)]."""
     s = o.s
     Ug = np.asarray(U, dtype=np.float64).reshape(o.nyp, o.nxp)
-    I, J = o.patch_nodes()
+    I, J = _patch_nodes(o, sel)
     st = np.empty((len(I), 5, 5))
     for q in range(-2, 3):
         rows = np.clip(J + q, 0, s.n_eta)
@@ -234,14 +240,15 @@ def stencil_features(st):
     return x, s
 
 
-def static_features(o: Oracle):
+def static_features(o: Oracle, sel=None):
     """Per-patch features that do not change with U: 4 metric terms, 6
-    coefficient samples, and the rate R.  Returns (feat [n, 10], R [n])."""
+    coefficient samples, and the rate R, of every patch or of the patches
+    sel.  Returns (feat [n, 10], R [n])."""
     s = o.s
     dxi = (s.xi1 - s.xi0) / s.n_xi
     deta = (s.eta1 - s.eta0) / s.n_eta
     hx, hy = s.h_ratio_xi * dxi, s.h_ratio_eta * deta
-    I, J = o.patch_nodes()
+    I, J = _patch_nodes(o, sel)
     xi = s.xi0 + I * dxi
     eta = s.eta0 + J * deta
     n = len(I)
@@ -266,13 +273,13 @@ def static_features(o: Oracle):
     return out, R
 
 
-def features(o: Oracle, U, static=None):
+def features(o: Oracle, U, static=None, sel=None):
     """Raw (unstandardised) features [n_patch, 35], the scale s and the rate R:
     the stencil features, the metric terms times the stencil feature of the
     derivative each multiplies (x[2] = xi-second, x[10] = eta-second,
     x[1] = xi-first, x[5] = eta-first difference), the coefficient samples."""
-    fs, R = static_features(o) if static is None else static
-    x, s = stencil_features(stencils(o, U))
+    fs, R = static_features(o, sel) if static is None else static
+    x, s = stencil_features(stencils(o, U, sel))
     fs = fs.copy()
     fs[:, 0] *= x[:, 2]
     fs[:, 1] *= x[:, 10]

@@ -175,3 +175,30 @@ def test_batch_with_a_single_patch_instance(Grid, orc):
         for k, (a, b) in enumerate(zip(got, want)):
             err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
             assert err <= tol, (prec, k, err)
+
+
+def test_full_size_batch_sampled_instances(Grid, orc):
+    """The 4096-instance batch (N up to 128, m up to 11) in the launch
+    configuration the benchmark times (FP32, autotuned work queue, each
+    instance at its own suggested macro step), three macro steps, against the
+    oracle on sampled instances: the largest ones, every map and micro size,
+    both ends of the queue."""
+    probs = W.c4_batch(4096)
+    g = Grid(probs, prec="fp32")
+    U = g.init_field()
+    U0 = U.cpu().numpy()
+    g.step(U, 0.0, 0.0, 3)
+    g.sync()
+    got = U.cpu().numpy()
+    sel = {0, len(probs) - 1}
+    sel |= set([k for k, p in enumerate(probs) if p["n_xi"] == 128 and p["m_xi"] == 11][:2])
+    for key, vals in (("map", ("identity", "tanh", "polar")), ("m_xi", (5, 7, 9, 11))):
+        for v in vals:
+            sel.add(next(k for k, p in enumerate(probs) if p[key] == v and p["n_xi"] >= 64))
+    for k in sorted(sel):
+        i = g.info(k)
+        o = orc.Oracle(probs[k])
+        a = i["u_offset"]
+        want = o.step(U0[a:a + i["n_macro"]], 0.0, o.dt_macro(), 3)
+        err = np.linalg.norm(got[a:a + i["n_macro"]] - want) / np.linalg.norm(want)
+        assert err <= 1e-4, (k, probs[k]["map"], probs[k]["n_xi"], probs[k]["m_xi"], err)

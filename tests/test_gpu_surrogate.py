@@ -4,6 +4,8 @@ network's F, the all-fallback limit (the plain scheme) and the accept-all
 limit, and end to end: a network trained on the GPU from patch-solver data
 serves most patches of an unseen field within the 1e-3 tolerance of the plain
 scheme, where an untrained one serves none."""
+import math
+
 import numpy as np
 import pytest
 
@@ -27,8 +29,8 @@ def _small(seed=5):
     return W.c5_surrogate_field(n_r=15, n_theta=48, m=9, seed=seed)
 
 
-def _net(api, seed=3):
-    net = api.MLP(256)
+def _net(api, seed=3, max_batch=256):
+    net = api.MLP(max_batch)
     th = S.init_params(seed)
     p = S.unflatten(th)
     rng = np.random.default_rng(seed)
@@ -206,3 +208,65 @@ def test_trained_network_serves_most_patches(api):
     g2.sync()
     st2, fb2 = s2.counts()
     assert fb2 / st2 >= 0.99
+
+
+def test_full_size_annulus_sampled_patches(api):
+    """The 512 x 2048-node annulus (1,044,480 patches, 9 x 9 micro, FP32) in
+    the launch configuration the benchmark times: raw features, the full-burst
+    F and the check estimate F1 against the oracle on sampled patches (both
+    walls and the periodic seam included), the network's F_hat on those rows,
+    and one surrogate macro step whose check splits the patches about evenly
+    between the network and the burst fallback: at every sampled patch node
+    the step adds dt F_hat where the check accepts and dt F where it falls
+    back."""
+    p = W.c5_surrogate_field()
+    g = api.Grid(p, prec="fp32")
+    net = _net(api, max_batch=4096)
+    s = api.Surrogate(g, net)
+    U = g.init_field()
+    o = Oracle(p)
+    n = o.n_patch
+    ncol = p["n_xi"]
+    rng = np.random.default_rng(11)
+    sel = np.unique(np.concatenate([rng.integers(0, n, 250), [0, 1, ncol - 1, ncol, n - ncol, n - 1]]))
+    Uh = U.cpu().numpy()
+
+    f = s.features(U, standardised=False, raw=True)
+    X, sc, R = S.features(o, Uh, sel=sel)
+    np.testing.assert_allclose(f["X_raw"].cpu().numpy()[sel].astype(np.float64), X, rtol=2e-6, atol=2e-7)
+    np.testing.assert_allclose(f["Rs"].cpu().numpy()[sel], R * sc, rtol=1e-11)
+
+    ev = s.evaluate(U, 0.0)
+    Fh, F1, FK = (ev[k].cpu().numpy() for k in ("F_hat", "F1", "F"))
+    dt = o.dt_micro()
+    wantK = o.patch_dU(Uh, 0.0, sel, dt_micro=dt) / (p["k_micro"] * dt)
+    want1 = Oracle(dict(p, k_micro=1)).patch_dU(Uh, 0.0, sel, dt_micro=dt) / dt
+    tol = 2e-4
+    np.testing.assert_allclose(FK[sel], wantK, rtol=0, atol=tol * np.abs(wantK).max())
+    np.testing.assert_allclose(F1[sel], want1, rtol=0, atol=tol * np.abs(want1).max())
+
+    mu, sg, ys = net.norm()
+    Xs = (X.astype(np.float32) - mu) / sg
+    y, _ = S.forward(net.params().astype(np.float64), Xs.astype(np.float64), round_bf16=True)
+    want_h = y * ys * R * sc
+    err = np.abs(Fh[sel] - want_h) / np.abs(want_h).max()
+    assert np.quantile(err, 0.99) <= 2.5e-3 and err.max() <= 1e-2, (np.quantile(err, 0.99), err.max())
+
+    # the check threshold that accepts about half of the patches
+    rho = math.sqrt(float(np.mean(F1 ** 2)))
+    ratio = np.abs(Fh - F1) / (np.abs(F1) + rho)
+    eps = float(np.median(ratio))
+    U0 = U.clone()
+    dtm = g.info()["dt_macro_suggested"]
+    s.step(U, 0.0, dtm, 1, eps=eps)
+    g.sync()
+    steps, fb = s.counts()
+    assert steps == n and 0.3 * n <= fb <= 0.7 * n, (steps, fb)
+    I, J = o.patch_nodes()
+    d = (U - U0).cpu().numpy()[J[sel] * o.nxp + I[sel]]
+    r = ratio[sel]
+    clear = np.abs(r - eps) > 1e-6 * eps           # decisions away from the threshold
+    assert clear.sum() >= 0.9 * len(sel)
+    expect = dtm * np.where(r <= eps, Fh[sel], FK[sel])
+    scale = dtm * max(np.abs(Fh[sel]).max(), np.abs(FK[sel]).max())
+    np.testing.assert_allclose(d[clear], expect[clear], rtol=0, atol=1e-6 * scale)

@@ -174,6 +174,18 @@ def test_metric_features_multiply_the_matching_differences():
     np.testing.assert_array_equal(X[:, 29:], fs[:, 4:])
 
 
+def test_features_of_a_patch_subset_are_the_rows_of_the_full_set():
+    p = W.c5_surrogate_field(n_r=6, n_theta=12, m=5)
+    o = Oracle(p)
+    U = o.init_field()
+    X, s, R = S.features(o, U)
+    sel = np.array([0, 11, 12, 30, o.n_patch - 1])
+    Xs, ss, Rs = S.features(o, U, sel=sel)
+    np.testing.assert_array_equal(Xs, X[sel])
+    np.testing.assert_array_equal(ss, s[sel])
+    np.testing.assert_array_equal(Rs, R[sel])
+
+
 def test_split_input_carries_sixteen_bits():
     x = np.random.default_rng(3).normal(size=(200, S.N_PAD)) * 10.0 ** np.random.default_rng(4).uniform(-3, 3, (200, S.N_PAD))
     hi, lo = S.split_input(x)
