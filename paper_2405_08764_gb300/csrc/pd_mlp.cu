@@ -647,6 +647,55 @@ __device__ __forceinline__ void fence_async_shared()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Hidden-layer epilogue of 32 accumulator columns [col0, col0 + 32) of row r:
+// bias, GELU, BF16, stored into the next layer's operand in the
+// 128-byte-swizzled K-major layout (16-byte unit j of row r at j ^ (r & 7)).
+__device__ __forceinline__ void epi_hidden32(const uint32_t (&u)[32], int col0, const float* bias, uint8_t* act, int r)
+{
+    float v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(u[k]);
+    const float4* bq = reinterpret_cast<const float4*>(bias + col0);
+#pragma unroll
+    for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 bb = __ldg(bq + k4);
+        gelu_fast2(v[4 * k4 + 0], v[4 * k4 + 1], bb.x, bb.y);
+        gelu_fast2(v[4 * k4 + 2], v[4 * k4 + 3], bb.z, bb.w);
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        uint4 q;
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(v[8 * h + 0], v[8 * h + 1]);
+        __nv_bfloat162 p1 = __floats2bfloat162_rn(v[8 * h + 2], v[8 * h + 3]);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * h + 4], v[8 * h + 5]);
+        __nv_bfloat162 p3 = __floats2bfloat162_rn(v[8 * h + 6], v[8 * h + 7]);
+        q.x = *reinterpret_cast<uint32_t*>(&p0);
+        q.y = *reinterpret_cast<uint32_t*>(&p1);
+        q.z = *reinterpret_cast<uint32_t*>(&p2);
+        q.w = *reinterpret_cast<uint32_t*>(&p3);
+        const int col = col0 + 8 * h;
+        const int kc = col >> 6, j = (col & 63) >> 3;
+        *reinterpret_cast<uint4*>(act + kc * kActChunk + r * 128 + ((j ^ (r & 7)) << 4)) = q;
+    }
+}
+
+// Output-layer epilogue: part + sum over 32 columns of w4 * GELU(acc + b3), in
+// column order.
+__device__ __forceinline__ float epi_dot32(const uint32_t (&u)[32], int col0, const float* b3, const float* w4, float part)
+{
+    const float4* bq = reinterpret_cast<const float4*>(b3 + col0);
+    const float4* wq = reinterpret_cast<const float4*>(w4 + col0);
+#pragma unroll
+    for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 bb = __ldg(bq + k4), ww = __ldg(wq + k4);
+        part = fmaf(gelu_f(__uint_as_float(u[4 * k4 + 0]) + bb.x), ww.x, part);
+        part = fmaf(gelu_f(__uint_as_float(u[4 * k4 + 1]) + bb.y), ww.y, part);
+        part = fmaf(gelu_f(__uint_as_float(u[4 * k4 + 2]) + bb.z), ww.z, part);
+        part = fmaf(gelu_f(__uint_as_float(u[4 * k4 + 3]) + bb.w), ww.w, part);
+    }
+    return part;
+}
+
 // Two tiles in flight per block (slots 0 and 1, each with its own activation
 // buffer and 256-column TMEM accumulator), processed layer by layer in the
 // job order (A, L1), (B, L1), (A, L2), (B, L2), (A, L3), (B, L3) for each pair
@@ -818,65 +867,47 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                     const uint32_t tbase = tmem + (uint32_t)(s * 256) + ((uint32_t)(quad * 32) << 16);
                     uint8_t* act = act0 + s * kActBytes;
                     float* ydot = ydot0 + s * 128;
+                    // the warp's 128 columns in four 32-column TMEM loads, each
+                    // issued while the previous piece is processed
+                    const int colw = half * 128;
+                    uint32_t ra[32], rb[32];
+                    tmem_ld32_issue(tbase + colw, ra);
+                    tmem_ld_wait();
+                    tmem_reg_fence(ra);
                     if (L < 2) {
                         const float* bias = L == 0 ? a.b1 : a.b2;
-                        // 64 columns per TMEM load (one wait), then 16-column pieces
-#pragma unroll 1
-                        for (int c2 = 0; c2 < 2; ++c2) {
-                            const int col0 = half * 128 + c2 * 64;
-                            float v[64];
-                            tmem_ld64(tbase + col0, v);
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const int col = col0 + c * 16;
-                                float* vv = v + 16 * c;
-                                const float4* bq = reinterpret_cast<const float4*>(bias + col);
-#pragma unroll
-                                for (int k4 = 0; k4 < 4; ++k4) {
-                                    const float4 bb = __ldg(bq + k4);
-                                    gelu_fast2(vv[4 * k4 + 0], vv[4 * k4 + 1], bb.x, bb.y);
-                                    gelu_fast2(vv[4 * k4 + 2], vv[4 * k4 + 3], bb.z, bb.w);
-                                }
-                                uint4 q[2];
-#pragma unroll
-                                for (int h = 0; h < 2; ++h) {
-                                    __nv_bfloat162 p0 = __floats2bfloat162_rn(vv[8 * h + 0], vv[8 * h + 1]);
-                                    __nv_bfloat162 p1 = __floats2bfloat162_rn(vv[8 * h + 2], vv[8 * h + 3]);
-                                    __nv_bfloat162 p2 = __floats2bfloat162_rn(vv[8 * h + 4], vv[8 * h + 5]);
-                                    __nv_bfloat162 p3 = __floats2bfloat162_rn(vv[8 * h + 6], vv[8 * h + 7]);
-                                    q[h].x = *reinterpret_cast<uint32_t*>(&p0);
-                                    q[h].y = *reinterpret_cast<uint32_t*>(&p1);
-                                    q[h].z = *reinterpret_cast<uint32_t*>(&p2);
-                                    q[h].w = *reinterpret_cast<uint32_t*>(&p3);
-                                }
-                                const int kc = col >> 6, j = (col & 63) >> 3;
-                                uint8_t* rowp = act + kc * kActChunk + r * 128;
-                                *reinterpret_cast<uint4*>(rowp + (((j) ^ (r & 7)) << 4)) = q[0];
-                                *reinterpret_cast<uint4*>(rowp + (((j + 1) ^ (r & 7)) << 4)) = q[1];
-                            }
-                        }
+                        tmem_ld32_issue(tbase + colw + 32, rb);
+                        epi_hidden32(ra, colw, bias, act, r);
+                        tmem_ld_wait();
+                        tmem_reg_fence(rb);
+                        tmem_ld32_issue(tbase + colw + 64, ra);
+                        epi_hidden32(rb, colw + 32, bias, act, r);
+                        tmem_ld_wait();
+                        tmem_reg_fence(ra);
+                        tmem_ld32_issue(tbase + colw + 96, rb);
+                        epi_hidden32(ra, colw + 64, bias, act, r);
+                        tmem_ld_wait();
+                        tmem_reg_fence(rb);
+                        epi_hidden32(rb, colw + 96, bias, act, r);
                         fence_async_shared();
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(epidone(s));
                     } else {
                         float part = 0.0f;
-#pragma unroll 1
-                        for (int c2 = 0; c2 < 2; ++c2) {
-                            const int col0 = half * 128 + c2 * 64;
-                            float v[64];
-                            tmem_ld64(tbase + col0, v);
-                            const float4* bq = reinterpret_cast<const float4*>(a.b3 + col0);
-                            const float4* wq = reinterpret_cast<const float4*>(a.w4 + col0);
-#pragma unroll
-                            for (int k4 = 0; k4 < 16; ++k4) {
-                                const float4 bb = __ldg(bq + k4), ww = __ldg(wq + k4);
-                                part = fmaf(gelu_f(v[4 * k4 + 0] + bb.x), ww.x, part);
-                                part = fmaf(gelu_f(v[4 * k4 + 1] + bb.y), ww.y, part);
-                                part = fmaf(gelu_f(v[4 * k4 + 2] + bb.z), ww.z, part);
-                                part = fmaf(gelu_f(v[4 * k4 + 3] + bb.w), ww.w, part);
-                            }
-                        }
+                        tmem_ld32_issue(tbase + colw + 32, rb);
+                        part = epi_dot32(ra, colw, a.b3, a.w4, part);
+                        tmem_ld_wait();
+                        tmem_reg_fence(rb);
+                        tmem_ld32_issue(tbase + colw + 64, ra);
+                        part = epi_dot32(rb, colw + 32, a.b3, a.w4, part);
+                        tmem_ld_wait();
+                        tmem_reg_fence(ra);
+                        tmem_ld32_issue(tbase + colw + 96, rb);
+                        part = epi_dot32(ra, colw + 64, a.b3, a.w4, part);
+                        tmem_ld_wait();
+                        tmem_reg_fence(rb);
+                        part = epi_dot32(rb, colw + 96, a.b3, a.w4, part);
                         tc_fence_before();
                         if (half == 1) {
                             // the second column half hands its partial sums over (bounded wait on the other side)
