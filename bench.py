@@ -134,7 +134,7 @@ def cpu_baseline(prob: dict, target_s: float = 12.0) -> dict:
         o.step(U0, 0.0, dtm, chunk, dt)
         total += chunk
     el = time.perf_counter() - t
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.num_threads()
     return {"value": total * per_step / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d macro steps of the benchmark workload in chunks of %d from the initial field (%.1f s)"
                       % (total, chunk, el)}
@@ -186,7 +186,7 @@ def run_reference(args):
         times.append(time.perf_counter() - t)
     el = sum(times)
     value = args.steps * n_sample * per_macro / el
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.num_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,

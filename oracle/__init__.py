@@ -105,6 +105,7 @@ def lib():
                 "orc_bessel_norm": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_int]),
                 "orc_annulus_series": (C.c_double, [C.c_double, C.c_double, C.c_double,
                                                     C.c_double, C.c_double, C.c_int]),
+                "orc_num_threads": (C.c_int, []),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -317,6 +318,11 @@ class Oracle:
         xi = s.xi0 + np.arange(self.nxp) * dxi
         eta = s.eta0 + np.arange(self.nyp) * deta
         return np.meshgrid(xi, eta)
+
+
+def num_threads() -> int:
+    """Threads of the oracle's parallel loops over patches."""
+    return int(lib().orc_num_threads())
 
 
 def bessel_root(k, ra, rb, which=1):

@@ -141,6 +141,7 @@ double orc_bessel_norm(double mu, double ra, double rb, int n_int);
 /* eq. (Annulus_AS): diffusion (D = 1) of (r - ra)(rb - r) sin(theta) in the annulus,
    truncated at n_roots terms */
 double orc_annulus_series(double ra, double rb, double r, double theta, double t, int n_roots);
+int orc_num_threads(void);
 
 #ifdef __cplusplus
 }

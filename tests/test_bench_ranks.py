@@ -1,7 +1,8 @@
-"""The multi-rank path of bench.py on the CPU: two gloo ranks agree on the
-slowest rank's time, and every rank runs its own seeded replica of the
-benchmark workload (same shape, distinct source amplitudes, rank 0 equal to
-the one-GPU workload)."""
+"""bench.py on the CPU.  Multi-rank path: two gloo ranks agree on the slowest
+rank's time, and every rank runs its own seeded replica of the benchmark
+workload (same shape, distinct source amplitudes, rank 0 equal to the one-GPU
+workload).  Reference arm: the oracle's line carries the contract's keys and
+only rank 0 prints it."""
 import hashlib
 import os
 import socket
@@ -88,3 +89,30 @@ def test_replicas_are_deterministic_and_keep_the_workload_shape():
     np.testing.assert_array_equal(np.asarray(a["src_amp"]), np.asarray(b["src_amp"]))
     for key in ("n_xi", "n_eta", "m_xi", "m_eta", "k_micro", "n_macro"):
         assert a[key] == one[key], key
+
+
+def _bench(args, env_extra):
+    import json
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True, text=True,
+                         env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    return lines
+
+
+def test_reference_arm_prints_one_contract_line_on_rank_0_only():
+    lines = _bench(["--impl", "reference", "--steps", "1", "--warmup", "3"], {"OMP_NUM_THREADS": "2"})
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["steps"] == 1 and d["warmup"] == 3 and d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
+    assert d["cpu_baseline"]["value"] == d["value"] and d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["unit"] == d["e2e"]["unit"] == d["cpu_baseline"]["unit"]
+    assert "workload" in d["config"]
+    # other ranks of a torchrun launch exit without work
+    assert _bench(["--impl", "reference", "--steps", "1", "--warmup", "3"],
+                  {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
