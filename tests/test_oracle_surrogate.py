@@ -160,6 +160,43 @@ def test_static_features_identity_map_closed_form():
     np.testing.assert_allclose(fs, np.tile(want, (len(fs), 1)), rtol=1e-13, atol=1e-16)
 
 
+def test_rate_closed_form_with_a_cross_term_and_reaction():
+    """Identity map, constant tensor D = d [[1, c], [c, 1]], v constant, f0: the
+    rate is R = 2d/dxi^2 + 2d/deta^2 + 2 c d/(dxi deta) + |v1|/dxi + |v2|/deta
+    + |f0| (beta = 2 c d, phi = f0) and every one of its terms is positive."""
+    d, c, v1, v2, f0 = 0.04, 0.3, -0.7, 1.2, -0.9
+    p = W.base(n_xi=6, n_eta=5, M=(1.0, c, 1.0), d_aff=(d, 0.0, 0.0), va=(v1, 0.0, 0.0), vb=(v2, 0.0, 0.0),
+               f0=f0)
+    o = Oracle(p)
+    fs, R = S.static_features(o)
+    dx, dy = 1 / 6, 1 / 5
+    Rw = 2 * d / dx ** 2 + 2 * d / dy ** 2 + 2 * c * d / (dx * dy) + abs(v1) / dx + abs(v2) / dy + abs(f0)
+    np.testing.assert_allclose(R, Rw, rtol=1e-13)
+    want = [2 * d / dx ** 2 / Rw, 2 * d / dy ** 2 / Rw, v1 / dx / Rw, v2 / dy / Rw]
+    np.testing.assert_allclose(fs[:, :4], np.tile(want, (len(fs), 1)), rtol=1e-13)
+
+
+def test_edge_samples_of_a_diffusivity_linear_in_x():
+    """Identity map, D = (d0 + a x) I, v = 0, f = 0: half the trace at the
+    centre is d0 + a x_c; its relative change is +-a (h_xi/2) / (d0 + a x_c)
+    at the E and W edge midpoints and 0 at N and S; nu = -a enters R."""
+    d0, a = 0.2, 0.15
+    p = W.base(n_xi=6, n_eta=5, d_aff=(d0, a, 0.0), h_ratio_xi=0.3)
+    o = Oracle(p)
+    fs, R = S.static_features(o)
+    I, J = o.patch_nodes()
+    dx, dy = 1 / 6, 1 / 5
+    xc = I * dx
+    dc = d0 + a * xc
+    rel = a * (0.3 * dx / 2) / dc
+    np.testing.assert_allclose(fs[:, 4], dc, rtol=1e-13)
+    np.testing.assert_allclose(fs[:, 5], rel, rtol=1e-12)
+    np.testing.assert_allclose(fs[:, 6], -rel, rtol=1e-12)
+    np.testing.assert_allclose(fs[:, 7:9], 0.0, atol=1e-14)
+    np.testing.assert_allclose(R, 2 * dc / dx ** 2 + 2 * dc / dy ** 2 + a / dx, rtol=1e-13)
+    np.testing.assert_allclose(fs[:, 9], o.tau() * R, rtol=1e-13)
+
+
 def test_metric_features_multiply_the_matching_differences():
     p = W.c5_surrogate_field(n_r=6, n_theta=12, m=5)
     o = Oracle(p)
