@@ -49,6 +49,15 @@ MUTATIONS = {
                               "double tk = T + k * dt;\n                    fill_ghosts(&g, &eq, up, 0);"),
     "refresh_split_ghost_data": ("eq.gL[k] -= e0[p].gL[k]; eq.gR[k] -= e0[p].gR[k];",
                                  "eq.gR[k] -= e0[p].gR[k];"),
+    "lift_bias_divisor": ("return (g->dx * g->dx * Uxx + g->dy * g->dy * Uyy) / 12.0;",
+                          "return (g->dx * g->dx * Uxx + g->dy * g->dy * Uyy) / 6.0;"),
+    "macro_rate_cross_dropped": ("+ fabs(c[1]) / (g.Dx * g.Dy) + fabs(c[3]) / g.Dx", "+ fabs(c[3]) / g.Dx"),
+    "micro_rate_reaction_dropped": ("+ fabs(c[1]) / (hx * hy) + fabs(c[5]);", "+ fabs(c[1]) / (hx * hy);"),
+    "project_boundary_time": ("+ dtm * F;\n    }\n    orc_apply_bc(P, U, t + dtm);", "+ dtm * F;\n    }\n    orc_apply_bc(P, U, t);"),
+    "tanh_map_curvature_sign": ("*X2 = -2.0 * s * s * sech2 * th / (T * L);", "*X2 = 2.0 * s * s * sech2 * th / (T * L);"),
+    "radial_curvature_factor": ("rho2 = -4.0 * sr * sr * sech2 * th / T;", "rho2 = -2.0 * sr * sr * sech2 * th / T;"),
+    "source_amplitude_index": ("P->src_amp[p] : 1.0;", "P->src_amp[0] : 1.0;"),
+    "sine_map_curvature_sign": ("o[6] = -lam * M_PI * sin(M_PI * xi);", "o[6] = lam * M_PI * sin(M_PI * xi);"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }

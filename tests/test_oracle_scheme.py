@@ -172,3 +172,27 @@ def test_step_composes_burst_restrict_project(orc):
     U1 = o.project(U, o.restrict(U, w), 0.2, dtm, tau)
     U2 = o.step(U, 0.2, dtm, 1, dt)
     np.testing.assert_array_equal(U1, U2)
+
+
+@pytest.mark.parametrize("conv", ["upwind", "central"])
+def test_step_sizes_closed_form(orc, conv):
+    """Identity map with constant coefficients (cross term, convection,
+    reaction): the micro step is cfl over the forward-Euler rate bound of the
+    micro grid, 2 alpha/dxi^2 + 2 gamma/deta^2 + |beta|/(dxi deta) + |phi|
+    (+ |nu|/dxi + |omega|/deta with upwind convection; central differences
+    drop them), and the macro step half the inverse of the same bound on the
+    macro grid with the convection terms always in."""
+    d11, d12, d22, v1, v2, f0 = 0.05, 0.015, 0.08, 0.9, -1.3, -0.6
+    cfl, hr, m = 0.4, 0.2, 7
+    p = W.base(n_xi=8, n_eta=6, m_xi=m, m_eta=m, h_ratio_xi=hr, h_ratio_eta=hr, cfl_micro=cfl, conv=conv,
+               M=(d11, d12, d22), d_aff=(1.0, 0.0, 0.0), va=(v1, 0.0, 0.0), vb=(v2, 0.0, 0.0), f0=f0)
+    o = orc.Oracle(p)
+    Dx, Dy = 1 / 8, 1 / 6
+    dx, dy = hr * Dx / (m - 1), hr * Dy / (m - 1)
+    beta = 2 * d12
+    r_mic = 2 * d11 / dx ** 2 + 2 * d22 / dy ** 2 + abs(beta) / (dx * dy) + abs(f0)
+    if conv == "upwind":
+        r_mic += abs(v1) / dx + abs(v2) / dy
+    r_mac = 2 * d11 / Dx ** 2 + 2 * d22 / Dy ** 2 + abs(beta) / (Dx * Dy) + abs(v1) / Dx + abs(v2) / Dy + abs(f0)
+    assert o.dt_micro() == pytest.approx(cfl / r_mic, rel=1e-13)
+    assert o.dt_macro() == pytest.approx(0.5 / r_mac, rel=1e-13)
