@@ -168,3 +168,38 @@ def test_transformed_operator_equals_physical_operator(orc, case):
         c = o.coeffs(xi, eta)
         comp = c[0] * faa + c[1] * fab + c[2] * fbb - c[3] * fa - c[4] * fb + c[5] * u(x, y)
         assert abs(comp - phys) <= 1e-6 * (1 + abs(phys)), (case, xi, eta, comp, phys)
+
+
+def _d1(f, z, h):
+    """fourth-order central difference"""
+    return (8.0 * (f(z + h) - f(z - h)) - (f(z + 2 * h) - f(z - 2 * h))) / (12.0 * h)
+
+
+def test_manufactured_source_satisfies_the_pde(orc):
+    """u = exp(-t) sin(pi x) sin(pi y) solves u_t = div(K grad u - v u) + f u +
+    s(t) G for the manufactured source with a constant tensor K (cross term),
+    an affine v with non-zero divergence and f != 0: the residual, with every
+    derivative of u and of the flux taken by fourth-order central differences,
+    vanishes at random points."""
+    M, d, va, vb, f0 = (0.7, 0.2, 1.1), 0.05, (0.5, 0.3, 0.1), (-0.4, 0.2, -0.3), 0.3
+    o = orc.Oracle(W.base(M=M, d_aff=(d, 0.0, 0.0), va=va, vb=vb, f0=f0, src="mms_sinprod", time="exp",
+                          tc=-1.0))
+    K = d * np.array([[M[0], M[1]], [M[1], M[2]]])
+    h, t = 1e-3, 0.37
+
+    def u(x, y, s):
+        return math.exp(-s) * math.sin(math.pi * x) * math.sin(math.pi * y)
+
+    def flux(x, y):
+        ux = _d1(lambda z: u(z, y, t), x, h)
+        uy = _d1(lambda z: u(x, z, t), y, h)
+        v1 = va[0] + va[1] * x + va[2] * y
+        v2 = vb[0] + vb[1] * x + vb[2] * y
+        uu = u(x, y, t)
+        return K[0, 0] * ux + K[0, 1] * uy - v1 * uu, K[1, 0] * ux + K[1, 1] * uy - v2 * uu
+
+    for x, y in _pts(20):
+        div = _d1(lambda z: flux(z, y)[0], x, h) + _d1(lambda z: flux(x, z)[1], y, h)
+        g = _d1(lambda s: u(x, y, s), t, h) - div - f0 * u(x, y, t)
+        G = o.coeffs(x, y)[6]                      # identity map: computational = physical
+        assert abs(o.time_factor(t) * G - g) <= 1e-8 * (1.0 + abs(g)), (x, y, o.time_factor(t) * G, g)

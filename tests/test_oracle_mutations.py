@@ -58,6 +58,13 @@ MUTATIONS = {
     "radial_curvature_factor": ("rho2 = -4.0 * sr * sr * sech2 * th / T;", "rho2 = -2.0 * sr * sr * sech2 * th / T;"),
     "source_amplitude_index": ("P->src_amp[p] : 1.0;", "P->src_amp[0] : 1.0;"),
     "sine_map_curvature_sign": ("o[6] = -lam * M_PI * sin(M_PI * xi);", "o[6] = lam * M_PI * sin(M_PI * xi);"),
+    "mms_cross_term_dropped": (" + 2.0 * M_PI * M_PI * ph[1] * cx * cy;", ";"),
+    "mms_reaction_sign": ("+ (ph[11] - ph[12]) * S;", "+ (ph[12] - ph[11]) * S;"),
+    "mms_convection_swapped": ("M_PI * (ph[9] * cx * sy + ph[10] * sx * cy)", "M_PI * (ph[10] * cx * sy + ph[9] * sx * cy)"),
+    "sin_diffusivity_gradient": ("gx += P->ds * k2 * cos(k2 * x) * sy;", "gx += P->ds * k2 * cos(k2 * y) * sy;"),
+    "fourier_diffusivity_gradient": ("gx += ck * (ct * A * dB - st / r * dA * B);", "gx += ck * (ct * A * dB + st / r * dA * B);"),
+    "velocity_divergence_index": ("o[11] = P->va[1] + P->vb[2];", "o[11] = P->va[1] + P->vb[1];"),
+    "time_factor_sin_cos": ("case ORC_TIME_SIN: return sin(P->tc * t);", "case ORC_TIME_SIN: return cos(P->tc * t);"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }
