@@ -44,10 +44,13 @@ def test_annulus_series_reproduces_initial_data(orc):
             assert abs(orc.annulus_series(1, 2, r, th, 0.0, 40) - want) < 2e-5
 
 
-def test_bessel_mode_field_solves_the_heat_equation(orc):
-    """The eigenmode initial field decays as exp(-mu^2 t) and satisfies
-    u_t = Laplacian u (checked by finite differences in r, theta)."""
+@pytest.mark.parametrize("d0", [1.0, 0.4])
+def test_bessel_mode_field_solves_the_heat_equation(orc, d0):
+    """The eigenmode initial field decays as exp(-d0 mu^2 t) and satisfies
+    u_t = d0 Laplacian u for the diffusivity d0 (checked by finite differences
+    in r, theta)."""
     p = W.c3_annulus(n_r=15, n_theta=24, m=5)
+    p["d_aff"] = (d0, 0.0, 0.0)
     o = orc.Oracle(p)
     U1, U2 = o.init_field(t=0.01), o.init_field(t=0.01 + 1e-6)
     dUdt = (U2 - U1) / 1e-6
@@ -57,8 +60,8 @@ def test_bessel_mode_field_solves_the_heat_equation(orc):
     for (th, eta), ut in list(zip(zip(X.ravel(), Y.ravel()), dUdt))[::17]:
         r = o.map(th, eta)
         rr = math.hypot(r[0], r[1])
-        want = sum(-mu * mu * a * orc.bessel_Z(k, mu, 1.0, rr) * math.cos(k * th) * math.exp(-mu * mu * 0.01)
-                   for k, (mu, a) in enumerate(zip(mus, amps), start=1))
+        want = sum(-d0 * mu * mu * a * orc.bessel_Z(k, mu, 1.0, rr) * math.cos(k * th)
+                   * math.exp(-d0 * mu * mu * 0.01) for k, (mu, a) in enumerate(zip(mus, amps), start=1))
         assert abs(ut - want) < 1e-4 * (1 + abs(want))
         # and the mode satisfies Bessel's equation: Z'' + Z'/r + (mu^2 - k^2/r^2) Z = 0
         for k, mu in enumerate(mus, start=1):
@@ -130,6 +133,34 @@ def test_full_domain_solver_converges_to_manufactured_solution(orc):
         ex = (math.exp(-0.1) * np.sin(math.pi * X) * np.sin(math.pi * Y)).ravel()
         errs.append(np.abs(u - ex).max())
     assert math.log2(errs[0] / errs[1]) > 1.8, errs
+
+
+def test_full_domain_step_is_exact_on_quadratics(orc):
+    """Central differences are exact on quadratics, so one forward-Euler step
+    of the full-domain solver from u = q(x, y) (identity map, constant tensor
+    with a cross term, constant v, reaction, source s(t) G at the step's start
+    time) is q + dt (L q + s(t0) G) at every interior node, with L q in closed
+    form; the boundary nodes take the exact solution at t0 + dt."""
+    a11, a12, a22, d, v1, v2, f0 = 1.0, 0.3, 0.7, 0.05, 0.8, -0.6, 0.25
+    sp = (0.4, -1.0, 0.5)
+    p = W.base(n_xi=6, n_eta=5, conv="central", M=(a11, a12, a22), d_aff=(d, 0.0, 0.0), va=(v1, 0.0, 0.0),
+               vb=(v2, 0.0, 0.0), f0=f0, src="exp_linear", src_p=sp, time="exp", tc=1.0, sol="exp_xyt")
+    o = orc.Oracle(p)
+    refine = 2
+    ny, nx = o.full_domain_shape(refine)
+    X, Y = np.meshgrid(np.linspace(0, 1, nx), np.linspace(0, 1, ny))
+    q00, q10, q01, q20, q11, q02 = 0.3, -0.7, 0.4, 1.1, -0.9, 0.6
+    q = q00 + q10 * X + q01 * Y + q20 * X * X + q11 * X * Y + q02 * Y * Y
+    t0, dt = 0.2, 1e-4
+    got = o.full_domain(q.ravel(), refine, t0, dt, 1).reshape(ny, nx)
+    Lq = (d * a11 * 2 * q20 + 2 * d * a12 * q11 + d * a22 * 2 * q02
+          - v1 * (q10 + 2 * q20 * X + q11 * Y) - v2 * (q01 + q11 * X + 2 * q02 * Y) + f0 * q)
+    G = (sp[0] + sp[1] * X + sp[2] * Y) * np.exp(X + Y)
+    want = q + dt * (Lq + math.exp(t0) * G)
+    np.testing.assert_allclose(got[1:-1, 1:-1], want[1:-1, 1:-1], rtol=0, atol=1e-12)
+    bnd = np.ones_like(q, dtype=bool)
+    bnd[1:-1, 1:-1] = False
+    np.testing.assert_allclose(got[bnd], np.exp(X + Y + t0 + dt)[bnd], rtol=1e-14)
 
 
 def _max_pct_error(orc, p, n_steps, t_end=1.0, chunks=20):

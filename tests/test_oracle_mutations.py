@@ -69,11 +69,26 @@ MUTATIONS = {
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }
 
+# mistakes in the initial fields and the full-domain solver, caught by pins of
+# the convergence file (run by node id: the rest of that file is slow)
+CONV_PINS = ["tests/test_oracle_convergence.py::test_bessel_mode_field_solves_the_heat_equation",
+             "tests/test_oracle_convergence.py::test_full_domain_step_is_exact_on_quadratics",
+             "tests/test_oracle_convergence.py::test_paper_table7_annulus"]
+MUTATIONS_CONV = {
+    "bessel_angular_factor": ("* orc_bessel_Z(k, mu[k - 1], prm[1], r) * cos(k * th)",
+                              "* orc_bessel_Z(k, mu[k - 1], prm[1], r) * sin(k * th)"),
+    "bessel_decay_diffusivity": ("* exp(-P->d0 * mu[k - 1] * mu[k - 1] * t);", "* exp(-mu[k - 1] * mu[k - 1] * t);"),
+    "annulus_initial_angular_factor": ("val = (r - prm[0]) * (prm[1] - r) * sin(th);",
+                                       "val = (r - prm[0]) * (prm[1] - r) * cos(th);"),
+    "full_domain_cross_sign": ("double uxy = (uNE - uSE - uNW + uSW) / (4.0 * hx * hy);",
+                               "double uxy = (uNE - uSE + uNW + uSW) / (4.0 * hx * hy);"),
+    "full_domain_source_time": ("double st = orc_time_factor(P, t);", "double st = orc_time_factor(P, t + dt);"),
+    "full_domain_boundary_time": ("un[o] = orc_exact(P, m[0], m[1], tn);", "un[o] = orc_exact(P, m[0], m[1], tn - dt);"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_planted_mistake_is_caught(tmp_path, name):
+
+def _caught(tmp_path, name, old, new, pins):
     src = open(os.path.join(ROOT, "oracle", "pd_oracle.c")).read()
-    old, new = MUTATIONS[name]
     assert old in src, "mutation anchor missing: " + name
     d = tmp_path / name
     d.mkdir()
@@ -83,6 +98,18 @@ def test_planted_mistake_is_caught(tmp_path, name):
     subprocess.run(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fopenmp",
                     "-fPIC", "-shared", "-o", so, str(d / "pd_oracle.c"), "-lm"], check=True)
     env = dict(os.environ, ORC_SO_OVERRIDE=so)
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider"] + PINS,
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider"] + pins,
                        cwd=ROOT, env=env, capture_output=True, text=True)
     assert r.returncode != 0, "planted mistake %s passed every pin:\n%s" % (name, r.stdout[-2000:])
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_CONV))
+def test_planted_mistake_in_fields_or_full_domain_is_caught(tmp_path, name):
+    old, new = MUTATIONS_CONV[name]
+    _caught(tmp_path, name, old, new, CONV_PINS)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTATIONS[name]
+    _caught(tmp_path, name, old, new, PINS)
