@@ -65,6 +65,16 @@ MUTATIONS = {
     "fourier_diffusivity_gradient": ("gx += ck * (ct * A * dB - st / r * dA * B);", "gx += ck * (ct * A * dB + st / r * dA * B);"),
     "velocity_divergence_index": ("o[11] = P->va[1] + P->vb[2];", "o[11] = P->va[1] + P->vb[1];"),
     "time_factor_sin_cos": ("case ORC_TIME_SIN: return sin(P->tc * t);", "case ORC_TIME_SIN: return cos(P->tc * t);"),
+    "lift_cross_factor": ("+ 0.5 * (s * s * Uxx + 2.0 * s * t * Uxy + t * t * Uyy);",
+                          "+ 0.5 * (s * s * Uxx + s * t * Uxy + t * t * Uyy);"),
+    "lift_eta_slope_operand": ("double Uy = (S[1][2] - S[1][0]) / (2.0 * g->Dy);",
+                               "double Uy = (S[2][1] - S[0][1]) / (2.0 * g->Dy);"),
+    "edge_top_middle_sign": ("e->gT[a + 1] = ((-0.5 + ry) * B[0] - 2.0 * ry * B[1]", "e->gT[a + 1] = ((-0.5 + ry) * B[0] + 2.0 * ry * B[1]"),
+    "edge_row_offset": ("double t = -0.5 * g->hy + b * g->dy;\n        double A[3];",
+                        "double t = 0.5 * g->hy + b * g->dy;\n        double A[3];"),
+    "ghost_top_sign": ("EXT(u, a, ny + 1, g->mx) = EXT(u, a, ny - 1, g->mx) + 2.0 * g->dy * gt;",
+                       "EXT(u, a, ny + 1, g->mx) = EXT(u, a, ny - 1, g->mx) - 2.0 * g->dy * gt;"),
+    "lagrange_node": ("double nodes[3] = { -D, 0.0, D };", "double nodes[3] = { -D, 0.0, 2.0 * D };"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }
@@ -73,7 +83,8 @@ MUTATIONS = {
 # the convergence file (run by node id: the rest of that file is slow)
 CONV_PINS = ["tests/test_oracle_convergence.py::test_bessel_mode_field_solves_the_heat_equation",
              "tests/test_oracle_convergence.py::test_full_domain_step_is_exact_on_quadratics",
-             "tests/test_oracle_convergence.py::test_paper_table7_annulus"]
+             "tests/test_oracle_convergence.py::test_paper_table7_annulus",
+             "tests/test_oracle_convergence.py::test_bessel_roots_match_scipy"]
 MUTATIONS_CONV = {
     "bessel_angular_factor": ("* orc_bessel_Z(k, mu[k - 1], prm[1], r) * cos(k * th)",
                               "* orc_bessel_Z(k, mu[k - 1], prm[1], r) * sin(k * th)"),
@@ -83,6 +94,7 @@ MUTATIONS_CONV = {
     "full_domain_cross_sign": ("double uxy = (uNE - uSE - uNW + uSW) / (4.0 * hx * hy);",
                                "double uxy = (uNE - uSE + uNW + uSW) / (4.0 * hx * hy);"),
     "full_domain_source_time": ("double st = orc_time_factor(P, t);", "double st = orc_time_factor(P, t + dt);"),
+    "bessel_root_index": ("if (++found == which) {", "if (++found == which + 1) {"),
     "full_domain_boundary_time": ("un[o] = orc_exact(P, m[0], m[1], tn);", "un[o] = orc_exact(P, m[0], m[1], tn - dt);"),
 }
 
