@@ -44,6 +44,19 @@ def test_annulus_series_reproduces_initial_data(orc):
             assert abs(orc.annulus_series(1, 2, r, th, 0.0, 40) - want) < 2e-5
 
 
+def test_annulus_initial_data_of_section_4_2(orc):
+    """The Section 4.2 initial field at the macro nodes of a stretched annulus:
+    (r - 1)(2 - r) sin(theta), with r and theta of each node's physical point."""
+    p = W.c3_annulus(n_r=9, n_theta=16, m=5)
+    o = orc.Oracle(p)
+    U = o.init_field(kind="annulus_poly", params=[1.0, 2.0])
+    X, Y = o.node_coords()
+    for (xi, eta), u in zip(zip(X.ravel(), Y.ravel()), U):
+        m = o.map(xi, eta)
+        r, th = math.hypot(m[0], m[1]), math.atan2(m[1], m[0])
+        assert abs(u - (r - 1.0) * (2.0 - r) * math.sin(th)) <= 1e-14
+
+
 @pytest.mark.parametrize("d0", [1.0, 0.4])
 def test_bessel_mode_field_solves_the_heat_equation(orc, d0):
     """The eigenmode initial field decays as exp(-d0 mu^2 t) and satisfies
