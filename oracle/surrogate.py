@@ -307,7 +307,11 @@ def patch_F(o: Oracle, U, t, k_micro=None):
 
 
 def check(F_hat, F1, eps=1e-3):
-    """Accept mask of the residual check: |F_hat - F1| <= eps (|F1| + rms(F1))."""
+    """Accept mask of the residual check: |F_hat - F1| <= eps (|F1| + rms(F1)).
+    A negative eps accepts nothing (every patch takes the burst), also where
+    F_hat = F1 = 0 would meet the bound with equality."""
+    if eps < 0:
+        return np.zeros(len(F1), dtype=bool)
     rho = math.sqrt(float(np.mean(np.asarray(F1) ** 2))) if len(F1) else 0.0
     return np.abs(F_hat - F1) <= eps * (np.abs(F1) + rho)
 

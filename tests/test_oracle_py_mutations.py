@@ -30,6 +30,12 @@ MUTATIONS = {
     "adam_bias_correction_dropped": ("surrogate", "mh = m / (1.0 - b1 ** step)", "mh = m"),
     "backward_transposed_weight": ("surrogate", 'g["W2"] = dz2.T @ c["h1"]', 'g["W2"] = c["h1"].T @ dz2'),
     "forward_bias_dropped": ("surrogate", 'z2 = h1 @ r(p["W2"]).T + p["b2"]', 'z2 = h1 @ r(p["W2"]).T'),
+    "input_not_standardised": ("surrogate", "y, _ = forward(theta, standardise(X, mu, sigma), round_bf16)",
+                               "y, _ = forward(theta, X, round_bf16)"),
+    "fallback_takes_F1": ("surrogate", "F[~ok] = patch_F(o, U, t)[~ok]", "F[~ok] = F1[~ok]"),
+    "surrogate_step_time_frozen": ("surrogate", "        t = t0 + k * dt_macro\n        F, ok, _, _ = surrogate_F(",
+                                   "        t = t0\n        F, ok, _, _ = surrogate_F("),
+    "negative_eps_accepts_zeros": ("surrogate", "    if eps < 0:\n        return np.zeros(len(F1), dtype=bool)\n", ""),
     "heun_stage_time": ("integrators", "F2 = patch_F(o, Us, t + dt)", "F2 = patch_F(o, Us, t)"),
     "ab2_history_sign": ("integrators", "(1.5 * F - 0.5 * F_prev)", "(1.5 * F + 0.5 * F_prev)"),
 }

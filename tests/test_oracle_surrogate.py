@@ -262,8 +262,15 @@ def test_patch_F_is_independent_of_K_for_constant_diffusion():
     np.testing.assert_allclose(b, a, rtol=0, atol=1e-11 * np.abs(a).max())
 
 
-def test_all_fallback_surrogate_step_is_the_plain_scheme():
-    p = W.c5_surrogate_field(n_r=6, n_theta=12, m=5)
+def _time_dependent_case():
+    p = W.c2_heterogeneous(n=6, m=5, n_macro=3)
+    p["src_amp"] = p["src_amp"] * 50.0           # a source that moves F within three steps
+    return p
+
+
+@pytest.mark.parametrize("case", ["annulus", "time_dependent_source"])
+def test_all_fallback_surrogate_step_is_the_plain_scheme(case):
+    p = W.c5_surrogate_field(n_r=6, n_theta=12, m=5) if case == "annulus" else _time_dependent_case()
     o = Oracle(p)
     U0 = o.init_field()
     dtm = o.dt_macro()
@@ -273,9 +280,28 @@ def test_all_fallback_surrogate_step_is_the_plain_scheme():
     want = o.step(U0, 0.0, dtm, 3)
     assert n_fb == 3 * o.n_patch
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-14 * np.abs(want).max())
+    if case != "annulus":
+        return
     # with every patch accepted, F is the network's prediction scaled by R s
     X, s, R = S.features(o, U0)
     F, ok, F_hat, _ = S.surrogate_F(o, U0, 0.0, th, mu, sig, 2.0, eps=np.inf)
     assert ok.all()
     y, _ = S.forward(th, X)
     np.testing.assert_allclose(F, 2.0 * y * R * s, rtol=1e-15)
+
+
+def test_network_input_is_standardised():
+    """F-hat = y((x - mu) / sigma) y_scale R s with the standardisation applied
+    before the network, for non-trivial mu and sigma."""
+    p = W.c5_surrogate_field(n_r=6, n_theta=12, m=5)
+    o = Oracle(p)
+    U0 = o.init_field()
+    th = _theta()
+    rng = np.random.default_rng(5)
+    mu, sig = rng.normal(size=S.N_IN) * 0.2, rng.uniform(0.5, 2.0, S.N_IN)
+    X, s, R = S.features(o, U0)
+    F, ok, F_hat, _ = S.surrogate_F(o, U0, 0.0, th, mu, sig, 1.5, eps=np.inf)
+    y, _ = S.forward(th, (X - mu) / sig)
+    np.testing.assert_allclose(F_hat, 1.5 * y * R * s, rtol=1e-14)
+    y0, _ = S.forward(th, X)
+    assert np.abs(F_hat - 1.5 * y0 * R * s).max() > 1e-6 * np.abs(F_hat).max()
