@@ -140,6 +140,28 @@ def cpu_baseline(prob: dict, target_s: float = 12.0) -> dict:
                       % (total, chunk, el)}
 
 
+def cpu_baseline_batch(probs: list, target_s: float = 12.0) -> dict:
+    """The CPU oracle on a fixed seeded subset of the batch workload: one macro
+    step of each instance in turn (each at its own suggested step) until about
+    target_s seconds of CPU work, reported per point-update."""
+    import oracle
+    orcs = [oracle.Oracle(p) for p in probs]
+    state = [(o, o.init_field(), 0.5 * o.dt_macro(), o.dt_micro()) for o in orcs]
+    state[0][0].step(state[0][1], 0.0, state[0][2], 1, state[0][3])
+    done = 0
+    k = 0
+    t = time.perf_counter()
+    while time.perf_counter() - t < target_s or k < len(state):
+        o, U, dtm, dt = state[k % len(state)]
+        o.step(U, 0.0, dtm, 1, dt)
+        done += o.n_patch * o.mx * o.my * o.s.k_micro
+        k += 1
+    el = time.perf_counter() - t
+    return {"value": done / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d macro steps over the first %d instances of the batch, one step each in turn (%.1f s)"
+                      % (k, len(state), el)}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,6 +289,8 @@ def run_batch(args):
                      "kernel": "batch_kernel (work queue, one launch per macro step)"},
         "gpu_launches": launches, "clocks": clocks,
     }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batch(probs[:64])
     print(json.dumps(line), flush=True)
     return 0
 
@@ -593,7 +617,7 @@ def run_adi(args):
             reps += 1
         el = time.perf_counter() - t
         line["cpu_baseline"] = {"value": reps * len(sel) * m * m * K / el, "unit": UNIT,
-                                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                                "cores": oracle.num_threads(),
                                 "kind": "oracle",
                                 "sample": "ADI bursts of %d random patches, %d repetitions (%.1f s)"
                                           % (len(sel), reps, el)}
