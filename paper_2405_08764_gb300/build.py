@@ -46,6 +46,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return OUT
     os.makedirs(OBJ, exist_ok=True)
+    # one build at a time (several ranks of one launch may start together);
+    # the others find the library up to date once they hold the lock
+    import fcntl
+    with open(os.path.join(OBJ, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not _stale():
+            return OUT
+        return _compile(verbose)
+
+
+def _compile(verbose: bool) -> str:
     procs = []
     objs = []
     for src in sources():
