@@ -825,7 +825,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:      # the host baseline is a one-GPU figure
         line["cpu_baseline"] = cpu_baseline(prob)
     print(json.dumps(line), flush=True)
     if dist:
