@@ -75,6 +75,8 @@ MUTATIONS = {
     "ghost_top_sign": ("EXT(u, a, ny + 1, g->mx) = EXT(u, a, ny - 1, g->mx) + 2.0 * g->dy * gt;",
                        "EXT(u, a, ny + 1, g->mx) = EXT(u, a, ny - 1, g->mx) - 2.0 * g->dy * gt;"),
     "lagrange_node": ("double nodes[3] = { -D, 0.0, D };", "double nodes[3] = { -D, 0.0, 2.0 * D };"),
+    "sampled_patch_index": ("dU[s] = run_patch(P, U, sel[s], c, t, P->k_micro, dt, form, NULL);",
+                            "dU[s] = run_patch(P, U, s, c, t, P->k_micro, dt, form, NULL);"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }

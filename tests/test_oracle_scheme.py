@@ -196,3 +196,16 @@ def test_step_sizes_closed_form(orc, conv):
     r_mac = 2 * d11 / Dx ** 2 + 2 * d22 / Dy ** 2 + abs(beta) / (Dx * Dy) + abs(v1) / Dx + abs(v2) / Dy + abs(f0)
     assert o.dt_micro() == pytest.approx(cfl / r_mic, rel=1e-13)
     assert o.dt_macro() == pytest.approx(0.5 / r_mac, rel=1e-13)
+
+
+def test_sampled_patches_equal_the_full_passes(orc):
+    """patch_dU on a shuffled subset of patches returns, for each selected
+    patch, the restricted change that the full lift -> burst -> restrict passes
+    give that patch."""
+    p = W.c2_heterogeneous(n=7, m=5, n_macro=1)
+    o = orc.Oracle(p)
+    U = o.init_field() + np.random.default_rng(4).normal(size=o.n_macro) * 0.1
+    t, K, dt = 0.3, p["k_micro"], o.dt_micro()
+    full = o.restrict(U, o.burst(U, t, K, dt))
+    sel = np.random.default_rng(5).permutation(o.n_patch)[:17]
+    np.testing.assert_allclose(o.patch_dU(U, t, sel), full[sel], rtol=1e-13, atol=1e-15 * np.abs(full).max())
