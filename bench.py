@@ -802,6 +802,9 @@ def run_gpu(args):
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
         "frac": (achieved / pk["fp32_tflops"]) if achieved else None, "traffic": traffic,
+        "traffic_note": None if traffic is not None else
+        ("no DRAM capture of this kernel: ncu fails the cooperative launch before it runs; a cold launch "
+         "reads the 30.7 MB of burst records once, later steps find them in L2"),
         "kernel": ("patch_persist_kernel<11,cross,tsrc,float> (cooperative, %d macro steps per launch)"
                    % info["chunk_steps"] if info["exec_path"] == 2 else
                    "patch_warp_kernel<11,cross,tsrc,float,fused> (one macro step per launch)"),
