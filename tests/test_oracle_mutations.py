@@ -77,6 +77,9 @@ MUTATIONS = {
     "lagrange_node": ("double nodes[3] = { -D, 0.0, D };", "double nodes[3] = { -D, 0.0, 2.0 * D };"),
     "sampled_patch_index": ("dU[s] = run_patch(P, U, sel[s], c, t, P->k_micro, dt, form, NULL);",
                             "dU[s] = run_patch(P, U, s, c, t, P->k_micro, dt, form, NULL);"),
+    "refresh_macro_bias_omitted": ("            if (P->restrict_mode == ORC_RESTRICT_MACRO) d += lift_trapezoid_bias(&g, &e0[p]);\n"
+                                   "            U[g.j * nxp + g.i] = U[g.j * nxp + g.i] + dtm * (d / tau);",
+                                   "            U[g.j * nxp + g.i] = U[g.j * nxp + g.i] + dtm * (d / tau);"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }

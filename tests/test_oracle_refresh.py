@@ -137,3 +137,27 @@ def test_refresh_descriptor_checks(orc):
         orc.Oracle(p)
     with pytest.raises(ValueError):
         orc.Oracle(dict(_tensor_problem(3), micro="adi"))
+
+
+@pytest.mark.parametrize("Q", [2, 4])
+def test_refresh_macro_reference_adds_the_lift_bias(orc, Q):
+    """Reading G4 with Q > 1: the sub-bursts are the same in both restriction
+    modes, so one refreshed macro step with the paper-literal reference
+    U^0 = U_ij differs from the lifted one at every interior node by
+    dt_macro / tau times the bias (dxi^2 U_xixi + deta^2 U_etaeta) / 12 of the
+    step's starting field, and not at all on the boundary."""
+    pl, pm = _tensor_problem(Q), _tensor_problem(Q, "macro")
+    ol, om = orc.Oracle(pl), orc.Oracle(pm)
+    U = ol.apply_bc(ol.init_field() + 0.3 * np.random.default_rng(2).normal(size=ol.n_macro), 0.1)
+    dtm = 0.5 * ol.dt_macro()
+    diff = (om.step(U, 0.1, dtm, 1) - ol.step(U, 0.1, dtm, 1)).reshape(ol.nyp, ol.nxp)
+    Ug = U.reshape(ol.nyp, ol.nxp)
+    Dx, Dy = 1.0 / pl["n_xi"], 1.0 / pl["n_eta"]
+    dx, dy = pl["h_ratio_xi"] * Dx / (pl["m_xi"] - 1), pl["h_ratio_eta"] * Dy / (pl["m_eta"] - 1)
+    uxx = (Ug[1:-1, 2:] - 2 * Ug[1:-1, 1:-1] + Ug[1:-1, :-2]) / Dx ** 2
+    uyy = (Ug[2:, 1:-1] - 2 * Ug[1:-1, 1:-1] + Ug[:-2, 1:-1]) / Dy ** 2
+    want = dtm / ol.tau() * (dx * dx * uxx + dy * dy * uyy) / 12.0
+    np.testing.assert_allclose(diff[1:-1, 1:-1], want, rtol=1e-8, atol=1e-12 * np.abs(want).max())
+    inner = np.zeros_like(diff, dtype=bool)
+    inner[1:-1, 1:-1] = True
+    assert np.all(diff[~inner] == 0.0)
