@@ -80,6 +80,10 @@ MUTATIONS = {
     "refresh_macro_bias_omitted": ("            if (P->restrict_mode == ORC_RESTRICT_MACRO) d += lift_trapezoid_bias(&g, &e0[p]);\n"
                                    "            U[g.j * nxp + g.i] = U[g.j * nxp + g.i] + dtm * (d / tau);",
                                    "            U[g.j * nxp + g.i] = U[g.j * nxp + g.i] + dtm * (d / tau);"),
+    "boundary_top_row_dropped": ("int bnd = (j == 0 || j == ny - 1) || (!P->periodic_xi && (i == 0 || i == nx - 1));\n            if (!bnd) continue;",
+                                 "int bnd = (j == 0) || (!P->periodic_xi && (i == 0 || i == nx - 1));\n            if (!bnd) continue;"),
+    "boundary_periodic_sides_set": ("int bnd = (j == 0 || j == ny - 1) || (!P->periodic_xi && (i == 0 || i == nx - 1));\n            if (!bnd) continue;",
+                                    "int bnd = (j == 0 || j == ny - 1) || (i == 0 || i == nx - 1);\n            if (!bnd) continue;"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }

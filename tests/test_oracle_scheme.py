@@ -209,3 +209,28 @@ def test_sampled_patches_equal_the_full_passes(orc):
     full = o.restrict(U, o.burst(U, t, K, dt))
     sel = np.random.default_rng(5).permutation(o.n_patch)[:17]
     np.testing.assert_allclose(o.patch_dU(U, t, sel), full[sel], rtol=1e-13, atol=1e-15 * np.abs(full).max())
+
+
+@pytest.mark.parametrize("periodic", [0, 1])
+def test_boundary_data_on_exactly_the_boundary_nodes(orc, periodic):
+    """Dirichlet data at time t go to the first and last node rows and, unless
+    xi is periodic, the first and last node columns: the exact solution at each
+    node's physical point (zero without one); interior nodes are untouched."""
+    if periodic:
+        p = W.paper_annulus(n_theta=12, n_r=6, m=5)
+    else:
+        p = W.paper_cdr(False, lam=0.3, n=7, m=5)
+    o = orc.Oracle(p)
+    U = np.random.default_rng(6).normal(size=o.n_macro)
+    t = 0.45
+    V = o.apply_bc(U, t).reshape(o.nyp, o.nxp)
+    bnd = np.zeros((o.nyp, o.nxp), dtype=bool)
+    bnd[[0, -1], :] = True
+    if not periodic:
+        bnd[:, [0, -1]] = True
+    np.testing.assert_array_equal(V[~bnd], U.reshape(o.nyp, o.nxp)[~bnd])
+    X, Y = o.node_coords()
+    for (xi, eta), v in zip(zip(X[bnd], Y[bnd]), V[bnd]):
+        m = o.map(xi, eta)
+        want = 0.0 if periodic else math.exp(m[0] + m[1] + t)
+        assert v == pytest.approx(want, rel=1e-15, abs=0.0)
