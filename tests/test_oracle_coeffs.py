@@ -203,3 +203,42 @@ def test_manufactured_source_satisfies_the_pde(orc):
         g = _d1(lambda s: u(x, y, s), t, h) - div - f0 * u(x, y, t)
         G = o.coeffs(x, y)[6]                      # identity map: computational = physical
         assert abs(o.time_factor(t) * G - g) <= 1e-8 * (1.0 + abs(g)), (x, y, o.time_factor(t) * G, g)
+
+
+def test_manufactured_exact_solution_solves_the_problem_with_its_source(orc):
+    """The oracle's exact solution of the manufactured problem (Dirichlet and
+    initial data) and its source belong together: the residual of
+    u_t = div(K grad u - v u) + f u + s(t) G with u = the oracle's exact
+    solution, derivatives by fourth-order central differences, vanishes."""
+    M, d, va, vb, f0 = (0.9, -0.15, 0.6), 0.07, (0.2, -0.4, 0.3), (0.5, 0.1, 0.2), -0.2
+    o = orc.Oracle(W.base(M=M, d_aff=(d, 0.0, 0.0), va=va, vb=vb, f0=f0, src="mms_sinprod", time="exp",
+                          tc=-1.0, sol="sinprod_decay"))
+    K = d * np.array([[M[0], M[1]], [M[1], M[2]]])
+    h = 1e-3
+    for (x, y), t in zip(_pts(12), np.linspace(0.1, 0.9, 12)):
+        def flux(a, b):
+            ux = _d1(lambda z: o.exact(z, b, t), a, h)
+            uy = _d1(lambda z: o.exact(a, z, t), b, h)
+            uu = o.exact(a, b, t)
+            v1 = va[0] + va[1] * a + va[2] * b
+            v2 = vb[0] + vb[1] * a + vb[2] * b
+            return K[0, 0] * ux + K[0, 1] * uy - v1 * uu, K[1, 0] * ux + K[1, 1] * uy - v2 * uu
+        div = _d1(lambda z: flux(z, y)[0], x, h) + _d1(lambda z: flux(x, z)[1], y, h)
+        res = _d1(lambda s: o.exact(x, y, s), t, h) - div - f0 * o.exact(x, y, t) - o.time_factor(t) * o.coeffs(x, y)[6]
+        assert abs(res) <= 1e-8, (x, y, t, res)
+
+
+def test_bump_initial_field(orc):
+    """The batch workload's initial field: sin(pi z_xi) sin(pi z_eta) with z the
+    position in the computational box, or (1 + cos(xi)/2) sin(pi z_eta) when xi
+    is periodic."""
+    for p in (W.base(n_xi=7, n_eta=5, box=(0.0, 2.0, -1.0, 1.0), init="bump"),
+              W.base(n_xi=12, n_eta=5, periodic_xi=1, map="polar", map_p=(1.0, 2.0, 0, 0),
+                     box=(0.0, 2.0 * math.pi, 0.0, 1.0), init="bump")):
+        o = orc.Oracle(p)
+        U = o.init_field().reshape(o.nyp, o.nxp)
+        X, Y = o.node_coords()
+        x0, x1, y0, y1 = p["box"]
+        zy = (Y - y0) / (y1 - y0)
+        fx = (1.0 + 0.5 * np.cos(X)) if p["periodic_xi"] else np.sin(math.pi * (X - x0) / (x1 - x0))
+        np.testing.assert_allclose(U, fx * np.sin(math.pi * zy), rtol=0, atol=1e-15)

@@ -84,6 +84,11 @@ MUTATIONS = {
                                  "int bnd = (j == 0) || (!P->periodic_xi && (i == 0 || i == nx - 1));\n            if (!bnd) continue;"),
     "boundary_periodic_sides_set": ("int bnd = (j == 0 || j == ny - 1) || (!P->periodic_xi && (i == 0 || i == nx - 1));\n            if (!bnd) continue;",
                                     "int bnd = (j == 0 || j == ny - 1) || (i == 0 || i == nx - 1);\n            if (!bnd) continue;"),
+    "bump_periodic_factor": ("double fx = P->periodic_xi ? (1.0 + 0.5 * cos(xi)) : sin(M_PI * zx);",
+                             "double fx = P->periodic_xi ? (1.0 + 0.5 * sin(xi)) : sin(M_PI * zx);"),
+    "bump_eta_factor": ("val = fx * sin(M_PI * zy);", "val = fx * sin(M_PI * zy * 0.5);"),
+    "manufactured_solution_growth": ("case ORC_SOL_SINPROD_DECAY: return exp(-t) * sin(M_PI * x) * sin(M_PI * y);",
+                                     "case ORC_SOL_SINPROD_DECAY: return exp(t) * sin(M_PI * x) * sin(M_PI * y);"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }
