@@ -242,3 +242,22 @@ def test_bump_initial_field(orc):
         zy = (Y - y0) / (y1 - y0)
         fx = (1.0 + 0.5 * np.cos(X)) if p["periodic_xi"] else np.sin(math.pi * (X - x0) / (x1 - x0))
         np.testing.assert_allclose(U, fx * np.sin(math.pi * zy), rtol=0, atol=1e-15)
+
+
+def test_workload_fields_match_their_definitions(orc):
+    """The synthetic fields as documented for the workloads: the annulus
+    diffusivity d = 1 + sum_k c_k cos(k theta + phi_k) cos(k pi rho),
+    rho = (r - 1) / (2 - 1), and the Gaussian source factor exp(-(x^2 + y^2))."""
+    p = W.c5_surrogate_field(n_r=7, n_theta=16)
+    o = orc.Oracle(p)
+    c, ph = p["four"]["c"], p["four"]["phi"]
+    rng = np.random.default_rng(9)
+    for r, th in zip(rng.uniform(1.0, 2.0, 20), rng.uniform(-math.pi, math.pi, 20)):
+        x, y = r * math.cos(th), r * math.sin(th)
+        want = 1.0 + sum(c[k - 1] * math.cos(k * th + ph[k - 1]) * math.cos(k * math.pi * (r - 1.0))
+                         for k in (1, 2, 3))
+        assert o.physical(x, y)[0] == pytest.approx(want, rel=1e-14)
+    q = W.base(n_xi=5, n_eta=5, src="gauss_patch", src_amp=np.ones(16), time="sin", tc=math.pi)
+    og = orc.Oracle(q)
+    for x, y in _pts(10):
+        assert og.coeffs(x, y)[6] == pytest.approx(math.exp(-(x * x + y * y)), rel=1e-14)

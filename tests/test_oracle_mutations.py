@@ -89,6 +89,11 @@ MUTATIONS = {
     "bump_eta_factor": ("val = fx * sin(M_PI * zy);", "val = fx * sin(M_PI * zy * 0.5);"),
     "manufactured_solution_growth": ("case ORC_SOL_SINPROD_DECAY: return exp(-t) * sin(M_PI * x) * sin(M_PI * y);",
                                      "case ORC_SOL_SINPROD_DECAY: return exp(t) * sin(M_PI * x) * sin(M_PI * y);"),
+    "gauss_source_width": ("return exp(-(x * x + y * y));", "return exp(-0.5 * (x * x + y * y));"),
+    "fourier_radial_frequency": ("double B = cos(k * M_PI * rho), dB = -k * M_PI * sin(k * M_PI * rho) / (rb - ra);",
+                                 "double B = cos(k * M_PI * rho * 0.5), dB = -0.5 * k * M_PI * sin(k * M_PI * rho * 0.5) / (rb - ra);"),
+    "fourier_phase_sign": ("double A = cos(k * th + ph), dA = -k * sin(k * th + ph);",
+                           "double A = cos(k * th - ph), dA = -k * sin(k * th - ph);"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }
