@@ -58,10 +58,11 @@ def test_cosine_mode_amplification(j, l, K, dt_scale):
     np.testing.assert_allclose(got, rho ** K * w0, rtol=0, atol=1e-12)
 
 
-def _general_problem(mixed: bool):
+def _general_problem(mixed: bool, conv: str = "upwind"):
     """Heterogeneous tensor diffusion on a tanh-stretched grid with affine
-    velocity (upwind differences), reaction and an exponential-in-time source."""
-    return W.base(n_xi=6, n_eta=6, m_xi=7, m_eta=7, map="tanh", map_p=(1.5, 2.0, 0.0, 0.0),
+    velocity (upwind or central differences), reaction and an
+    exponential-in-time source."""
+    return W.base(n_xi=6, n_eta=6, m_xi=7, m_eta=7, map="tanh", map_p=(1.5, 2.0, 0.0, 0.0), conv=conv,
                   M=(1.0, 0.3 if mixed else 0.0, 0.6), d_aff=(0.02, 0.01, 0.005),
                   d_sin=(0.3, 1.0) if mixed else (0.0, 1.0),
                   va=(0.5, 0.4, 0.0), vb=(-0.3, 0.0, 0.2), f0=0.7,
@@ -101,9 +102,9 @@ def _exact_burst(o, p, L, r, T, tau, tc):
     return (scipy.linalg.expm(tau * A) @ z0)[:n]
 
 
-@pytest.mark.parametrize("mixed,order", [(False, 2.0), (True, 1.0)])
-def test_adi_converges_to_the_semidiscrete_solution(mixed, order):
-    p = _general_problem(mixed)
+@pytest.mark.parametrize("mixed,order,conv", [(False, 2.0, "upwind"), (True, 1.0, "upwind"), (False, 2.0, "central")])
+def test_adi_converges_to_the_semidiscrete_solution(mixed, order, conv):
+    p = _general_problem(mixed, conv)
     o = Oracle(p)
     n = o.mx * o.my
     dt_fe = Oracle(dict(p, micro="fe")).dt_micro()

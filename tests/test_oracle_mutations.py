@@ -94,6 +94,8 @@ MUTATIONS = {
                                  "double B = cos(k * M_PI * rho * 0.5), dB = -0.5 * k * M_PI * sin(k * M_PI * rho * 0.5) / (rb - ra);"),
     "fourier_phase_sign": ("double A = cos(k * th + ph), dA = -k * sin(k * th + ph);",
                            "double A = cos(k * th - ph), dA = -k * sin(k * th - ph);"),
+    "adi_xi_central_scale": ("if (P->conv == ORC_CONV_CENTRAL) ux = (uE - uW) / (2.0 * g->dx);\n        else ux = c[3]",
+                             "if (P->conv == ORC_CONV_CENTRAL) ux = (uE - uW) / g->dx;\n        else ux = c[3]"),
     "projection_tau": ("U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * (dU[p] / tau);",
                        "U[g.j * nx + g.i] = U[g.j * nx + g.i] + dtm * dU[p];"),
 }
