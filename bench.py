@@ -1,13 +1,21 @@
 """Benchmark of the patch-dynamics hot path on GB300.
 
-Workload: the 65 x 65 tanh-stretched heterogeneous tensor-diffusion CDR problem
-(11 x 11 micro points per patch, 20 forward-Euler micro steps per burst,
-200 macro steps, FP32 bursts with FP64 restriction and projection).  One bench
-step = one pd_step call over all 200 macro steps (lift -> burst -> restrict ->
-project per macro step, captured in a CUDA graph), with the macro field already
-resident in HBM.  The L2 is flushed (512 MB write) between timed steps.
+Default workload (the largest single-GPU configuration): 4096 independent,
+uneven constant-coefficient CDR instances (macro grids of 17..129 nodes per
+side, identity / tanh-stretched / annular maps, 5x5..11x11 micro points per
+patch, tensor diffusion with a cross term, K = 20 forward-Euler micro steps
+per burst), all stepped together by the batched work-queue kernels, FP32
+bursts with FP64 restriction and projection.  One bench step = one pd_step
+call of 10 macro steps over every instance (lift -> burst -> restrict ->
+project per macro step, captured in a CUDA graph) with the macro fields
+already resident in HBM (182 MB of FP64 fields, larger than the L2, which is
+also flushed between timed steps).  The same line carries the end-to-end
+figure (host fields copied in and out every step), the error against the FP64
+CPU oracle on sampled instances, the FP64 batch, and the 65x65 heterogeneous
+problem on the persistent dataflow kernel.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--workload c4|c2|c5|passes|adi|refresh]
 For N > 1 launch with torch.distributed.run: every rank runs an independent
 replica of the workload on its own GPU (no data-path collective; weak scaling).
 """
@@ -28,23 +36,36 @@ sys.path.insert(0, ROOT)
 
 METRIC = "patch point-updates/s (roofline frac), macro steps/s at fixed L2 err vs FP64"
 UNIT = "point-updates/s"
-FLOP_PER_UPDATE = 25.0        # algorithmic FP32 flops per point-update (9-point stencil + source)
-WORKLOAD = "tanh-stretched heterogeneous CDR, 65x65 macro grid, 11x11 micro, K=20, 200 macro steps"
+N_INST = 4096
+C4_MACRO = 10                 # macro steps per bench step of the batch workload
+C4_WORKLOAD = ("4096 uneven constant-coefficient CDR instances (N in {16,32,64,128}, m in {5,7,9,11}, "
+               "identity/tanh/annulus maps, rotated tensor D, K=20), 10 macro steps per step")
+C2_WORKLOAD = "tanh-stretched heterogeneous CDR, 65x65 macro grid, 11x11 micro, K=20, 200 macro steps"
 
-# DRAM traffic of one fused macro-step launch from an ncu capture of this
-# kernel source (sha256 of the kernel sources); null once the kernel changes.
+
+def flop_per_update(has_cross: bool) -> float:
+    """Algorithmic FP32 flops of one point-update of the 9-point micro stencil:
+    25 with the mixed-derivative (cross) term, 20 without it."""
+    return 25.0 if has_cross else 20.0
+
+
+# DRAM traffic of the dominant kernel from an ncu capture of this kernel
+# source (sha256 of the sources); null once the kernel changes.
 NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
 
 
-def kernel_sources_sha() -> str:
+def kernel_sources_sha(files=("pd_batch.cu", "pd_device.cuh", "pd_internal.h")) -> str:
     h = hashlib.sha256()
-    for f in ("pd_kernels.cu", "pd_internal.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2405_08764_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def peaks() -> dict:
+def peaks(device=None) -> dict:
+    """Measured HBM and BF16 peaks (MEASURED_PEAKS.json, else the fallback
+    figures) and the FP32 FMA peak from the device's SM count and the maximum
+    SM clock."""
     p = {"hbm_gbs": None, "sm_max_mhz": 2070.0, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -54,8 +75,19 @@ def peaks() -> dict:
     else:
         p["hbm_gbs"] = 6800.0
         p["bf16_tflops"] = 1900.0
-    # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop per clock at the maximum SM clock
-    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    n_sm, sm_src = 152, "GB300 SM count"
+    try:
+        import torch
+        if torch.cuda.is_available():
+            dev = torch.cuda.current_device() if device is None else device
+            n_sm, sm_src = torch.cuda.get_device_properties(dev).multi_processor_count, "device attribute"
+    except Exception:
+        pass
+    p["n_sm"] = n_sm
+    # FP32 FMA pipe: SMs x 128 lanes x 2 flop per clock at the maximum SM clock
+    p["fp32_tflops"] = n_sm * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    p["fp32_source"] = "%d SMs (%s) x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (
+        n_sm, sm_src, p["sm_max_mhz"], p["source"])
     return p
 
 
@@ -115,11 +147,84 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# --------------------------------------------------------------------------
+# workloads of the ranks
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def replica_batch(rank: int, ws: int, n_inst: int = N_INST) -> list:
+    """The batch of one rank: the 4096-instance workload itself on rank 0 (and
+    on one GPU); every other rank an independent batch of the same recipe
+    drawn from its own seeds (weak scaling, no data-path collective)."""
+    from paper_2405_08764_gb300 import workloads as W
+    seed0 = 4 if rank == 0 else 4 + n_inst * rank
+    return W.c4_batch(n_inst, seed0=seed0)
+
+
+def replica_workload(rank: int, ws: int) -> dict:
+    """The 65x65 heterogeneous problem of one rank: the problem itself on rank
+    0; other ranks the same problem with their own seeded per-patch source
+    amplitudes."""
+    from paper_2405_08764_gb300 import workloads as W
+    return W.bench_workload() if rank == 0 else W.c2_heterogeneous(seed=2 + rank)
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it); ms unchanged without a group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def batch_updates(probs: list, n_macro: int) -> int:
+    """Point-updates of n_macro macro steps over every instance, from the
+    workload parameters: patches x micro points x K."""
+    from paper_2405_08764_gb300 import workloads as W
+    return sum(W.n_patch(p) * p["m_xi"] * p["m_eta"] * p["k_micro"] for p in probs) * n_macro
+
+
+def accuracy_sample(probs: list) -> list:
+    """Instances checked against the oracle: the first of every (map, micro
+    size) pair, the first of the largest (N = 128, m = 11), the last one."""
+    sel = []
+    for mp in ("identity", "tanh", "polar"):
+        for m in (5, 7, 9, 11):
+            k = next((k for k, p in enumerate(probs) if p["map"] == mp and p["m_xi"] == m), None)
+            if k is not None:
+                sel.append(k)
+    k = next((k for k, p in enumerate(probs) if p["n_xi"] == 128 and p["m_xi"] == 11), None)
+    if k is not None:
+        sel.append(k)
+    sel.append(len(probs) - 1)
+    return sorted(set(sel))
+
+
+# --------------------------------------------------------------------------
+# CPU baselines (the oracle as it stands, on the host cores)
+
+
 def cpu_baseline(prob: dict, target_s: float = 12.0) -> dict:
-    """The CPU oracle as it stands on the host cores, on a bounded sample of the
-    workload: macro steps of the same problem from the initial field, in chunks
-    of 20, until about target_s seconds of CPU work have been done (one
-    untimed chunk first)."""
+    """The CPU oracle on a bounded sample of the 65x65 problem: macro steps from
+    the initial field in chunks of 20 until about target_s seconds of CPU work
+    (one untimed chunk first)."""
     import oracle
     o = oracle.Oracle(prob)
     U0 = o.init_field()
@@ -134,118 +239,212 @@ def cpu_baseline(prob: dict, target_s: float = 12.0) -> dict:
         o.step(U0, 0.0, dtm, chunk, dt)
         total += chunk
     el = time.perf_counter() - t
-    cores = oracle.num_threads()
-    return {"value": total * per_step / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d macro steps of the benchmark workload in chunks of %d from the initial field (%.1f s)"
+    return {"value": total * per_step / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d macro steps of the 65x65 problem in chunks of %d from the initial field (%.1f s)"
                       % (total, chunk, el)}
 
 
+class OracleBatch:
+    """The oracle over a fixed subset of the batch: each call advances every
+    instance of the subset by one macro step (at its own suggested step)."""
+
+    def __init__(self, probs: list):
+        import oracle
+        self.state = []
+        for p in probs:
+            o = oracle.Oracle(p)
+            self.state.append([o, o.init_field(), o.dt_macro(), o.dt_micro(), 0.0])
+        self.updates_per_round = sum(s[0].n_patch * s[0].mx * s[0].my * s[0].s.k_micro for s in self.state)
+
+    def round(self):
+        for s in self.state:
+            o, U, dtm, dt, t = s
+            s[1] = o.step(U, t, dtm, 1, dt)
+            s[4] = t + dtm
+
+
 def cpu_baseline_batch(probs: list, target_s: float = 12.0) -> dict:
-    """The CPU oracle on a fixed seeded subset of the batch workload: one macro
-    step of each instance in turn (each at its own suggested step) until about
-    target_s seconds of CPU work, reported per point-update."""
+    """The CPU oracle on the first 64 instances of the batch: rounds of one
+    macro step of each instance until about target_s seconds of CPU work (one
+    untimed round first), reported per point-update."""
     import oracle
-    orcs = [oracle.Oracle(p) for p in probs]
-    state = [(o, o.init_field(), 0.5 * o.dt_macro(), o.dt_micro()) for o in orcs]
-    state[0][0].step(state[0][1], 0.0, state[0][2], 1, state[0][3])
-    done = 0
-    k = 0
+    ob = OracleBatch(probs)
+    ob.round()
+    n = 0
     t = time.perf_counter()
-    while time.perf_counter() - t < target_s or k < len(state):
-        o, U, dtm, dt = state[k % len(state)]
-        o.step(U, 0.0, dtm, 1, dt)
-        done += o.n_patch * o.mx * o.my * o.s.k_micro
-        k += 1
+    while time.perf_counter() - t < target_s or n == 0:
+        ob.round()
+        n += 1
     el = time.perf_counter() - t
-    return {"value": done / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "%d macro steps over the first %d instances of the batch, one step each in turn (%.1f s)"
-                      % (k, len(state), el)}
-
-
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
-def replica_workload(rank: int, ws: int) -> dict:
-    """The benchmark workload of one rank: the workload itself on one GPU; with
-    several ranks every rank runs an independent replica with its own seeded
-    source amplitudes (weak scaling, no data-path collective)."""
-    from paper_2405_08764_gb300 import workloads as W
-    return W.bench_workload() if ws == 1 else W.c2_heterogeneous(seed=2 + rank)
-
-
-def max_over_ranks(ms: float, dist, device) -> float:
-    """The slowest rank's time (every rank gets it); ms unchanged without a group."""
-    if dist is None:
-        return ms
-    import torch
-    t = torch.tensor([ms], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return {"value": n * ob.updates_per_round / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d rounds of one macro step of each of the first %d instances of the batch (%.1f s)"
+                      % (n, len(probs), el)}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (the paper publishes no code),
+    timed as it stands on the host cores on a bounded sample of the same
+    workload; rank 0 only."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
-    from paper_2405_08764_gb300 import workloads as W
-    prob = W.bench_workload()
-    o = oracle.Oracle(prob)
-    U = o.init_field()
-    dtm, dt = 0.5 * o.dt_macro(), o.dt_micro()
-    per_macro = o.n_patch * o.mx * o.my * o.s.k_micro
-    n_sample = 20  # macro steps per reference step (bounded sample)
-    for _ in range(args.warmup):
-        o.step(U, 0.0, dtm, 1, dt)
-    times = []
+    if args.workload == "c2":
+        from paper_2405_08764_gb300 import workloads as W
+        prob = W.bench_workload()
+        o = oracle.Oracle(prob)
+        U = o.init_field()
+        dtm, dt = 0.5 * o.dt_macro(), o.dt_micro()
+        per_round = o.n_patch * o.mx * o.my * o.s.k_micro * 20
+
+        def one(s):
+            nonlocal U
+            U = o.step(U, s * 20 * dtm, dtm, 20, dt)
+        sample = "20 of the 200 macro steps of the 65x65 problem per step"
+        workload = C2_WORKLOAD
+    else:
+        ob = OracleBatch(replica_batch(0, 1)[:min(64, args.instances)])
+        per_round = ob.updates_per_round
+
+        def one(s):
+            ob.round()
+        sample = "one macro step of each of the first %d instances of the batch per step" % len(ob.state)
+        workload = C4_WORKLOAD
+    for s in range(args.warmup):
+        one(s)
+    el = 0.0
     for s in range(args.steps):
         t = time.perf_counter()
-        U = o.step(U, s * n_sample * dtm, dtm, n_sample, dt)
-        times.append(time.perf_counter() - t)
-    el = sum(times)
-    value = args.steps * n_sample * per_macro / el
+        one(args.warmup + s)
+        el += time.perf_counter() - t
+    value = args.steps * per_round / el
     cores = oracle.num_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "%d of 200 macro steps per step" % n_sample,
-                   "l2": "n/a (CPU)"},
+        "config": {"workload": workload, "sample": sample, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d macro steps per step, %d steps" % (n_sample, args.steps)},
+                         "sample": "%s, %d steps" % (sample, args.steps)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
+# --------------------------------------------------------------------------
+# the batch workload (default line)
+
+
+def _rel_l2(a, b) -> float:
+    import numpy as np
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def batch_oracle_error(g, probs, U0h, Uh, n_macro, sel) -> dict:
+    """Relative L2 distance of the GPU fields from the FP64 oracle after
+    n_macro macro steps (each instance at its suggested step) on the sampled
+    instances."""
+    import oracle
+    errs = {}
+    for k in sel:
+        i = g.info(k)
+        a, n = i["u_offset"], i["n_macro"]
+        o = oracle.Oracle(probs[k])
+        want = o.step(U0h[a:a + n], 0.0, o.dt_macro(), n_macro)
+        errs[k] = _rel_l2(Uh[a:a + n], want)
+    return {"max": max(errs.values()), "instances": len(errs),
+            "per_instance": {str(k): v for k, v in errs.items()}}
+
+
+def time_steps(g, U, U0, n_macro, steps, flush, stream):
+    """K bench steps of n_macro macro steps, CUDA events on the launching
+    stream around each, the field reset and the L2 flushed outside them."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s in range(steps):
+        U.copy_(U0)
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        g.step(U, 0.0, 0.0, n_macro)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def time_e2e(g, U0, n_macro, steps, stream):
+    """End to end through the public API: every step copies the host fields
+    (pinned) to the device, runs pd_step and copies the result back; one
+    untimed step first (graph capture for the new field pointer)."""
+    import torch
+    Uh = U0.cpu().pin_memory()
+    Uout = torch.empty_like(Uh).pin_memory()
+    Ud = torch.empty_like(U0)
+    Ud.copy_(Uh, non_blocking=True)
+    g.step(Ud, 0.0, 0.0, n_macro)
+    Uout.copy_(Ud, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        Ud.copy_(Uh, non_blocking=True)
+        g.step(Ud, 0.0, 0.0, n_macro)
+        Uout.copy_(Ud, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), U0.numel() * 8
+
+
+def batch_fp64(probs, n_macro, steps, sel, U0h) -> dict:
+    """The same batch with FP64 bursts (the parity precision): time per bench
+    step and error against the oracle."""
+    import torch
+    from paper_2405_08764_gb300.api import Grid
+    g = Grid(probs, prec="fp64")
+    U0 = g.init_field()
+    U = U0.clone()
+    g.step(U, 0.0, 0.0, n_macro)         # autotune + capture
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = time_steps(g, U, U0, n_macro, steps, flush, stream)
+    g.sync()
+    upd = batch_updates(probs, n_macro)
+    U.copy_(U0)
+    g.step(U, 0.0, 0.0, n_macro)
+    g.sync()
+    err = batch_oracle_error(g, probs, U0h, U.cpu().numpy(), n_macro, sel)
+    return {"value": upd * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "dtype": "f64", "l2_rel_err_vs_oracle": err["max"]}
+
+
 def run_batch(args):
-    """4096 uneven constant-coefficient instances (seed 4 + id), 100 macro steps,
-    one batched launch per macro step with the autotuned configuration."""
     import numpy as np
     import torch
 
-    from paper_2405_08764_gb300 import workloads as W
     from paper_2405_08764_gb300.api import Grid
 
-    torch.cuda.set_device(0)
-    probs = W.c4_batch(args.instances)
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    probs = replica_batch(rank, ws, args.instances)
+    n_macro = args.macro
     t = time.perf_counter()
     g = Grid(probs, prec=args.prec)
     setup_s = time.perf_counter() - t
-    n_macro = 100
-    updates = 0
-    for k in range(len(probs)):
-        i = g.info(k)
-        updates += i["n_patch"] * i["m_xi"] * i["m_eta"] * i["k_micro"] * n_macro
+    updates = batch_updates(probs, n_macro)
+    n_cross = sum(1 for k in range(len(probs)) if g.info(k)["has_cross"])
+    flop_step = sum(flop_per_update(g.info(k)["has_cross"]) * g.info(k)["n_patch"] * g.info(k)["m_xi"]
+                    * g.info(k)["m_eta"] * g.info(k)["k_micro"] for k in range(len(probs)))
     U0 = g.init_field()
     U = U0.clone()
+    field_bytes = U0.numel() * 8
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
     t = time.perf_counter()
     U.copy_(U0)
     g.step(U, 0.0, 0.0, n_macro)      # autotune + capture + one run
@@ -255,44 +454,245 @@ def run_batch(args):
         U.copy_(U0)
         g.step(U, 0.0, 0.0, n_macro)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stream = torch.cuda.current_stream()
-    sampler = ClockSampler(0)
+
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
+    g.set_timing(True)
     l0 = g.launches()
-    for s in range(args.steps):
+    ms = time_steps(g, U, U0, n_macro, args.steps, flush, stream)
+    launches = g.launches() - l0
+    kern_ms, kern_n = g.timing()
+    g.set_timing(False)
+    clocks = sampler.stop()
+    g.sync()
+    ms = max_over_ranks(ms, dist, "cuda")
+    if dist:
+        dist.barrier()
+    total_updates = sum_over_ranks(float(updates), dist, "cuda")
+    value = total_updates * args.steps / (ms / 1e3)
+    e2e_ms, nbytes = time_e2e(g, U0, n_macro, args.steps, stream)
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
+    e2e = total_updates * args.steps / (e2e_ms / 1e3)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    pk = peaks(local)
+    # the dominant kernels: the batched macro-step kernels of one macro step
+    # (per micro size, run concurrently); event time of the captured graph
+    # launches divided by their macro steps
+    per_macro_s = kern_ms / kern_n / 1e3 if kern_n else ms / 1e3 / (args.steps * n_macro)
+    achieved = flop_step / per_macro_s / 1e12
+    sha = kernel_sources_sha()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sources_sha256"] == sha else None
+    U.copy_(U0)
+    g.step(U, 0.0, 0.0, n_macro)
+    g.sync()
+    U0h, Uh = U0.cpu().numpy(), U.cpu().numpy()
+    sel = accuracy_sample(probs)
+    err32 = batch_oracle_error(g, probs, U0h, Uh, n_macro, sel)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": C4_WORKLOAD if len(probs) == N_INST else
+                   C4_WORKLOAD.replace("4096", str(len(probs))),
+                   "instances": len(probs), "macro_steps_per_step": n_macro,
+                   "point_updates_per_step": updates, "instances_with_cross_term": n_cross,
+                   "field_bytes": field_bytes, "setup_s": setup_s, "first_step_s": first_s,
+                   "l2": "inputs larger than L2 (182 MB of fields) and L2 flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "macro_steps_per_s": n_macro * args.steps / (ms / 1e3),
+        "l2_rel_err_vs_oracle": err32["max"],
+        "accuracy": {"vs": "FP64 CPU oracle, %d macro steps from the initial fields" % n_macro,
+                     "sampled_instances": err32["instances"], "max_rel_l2": err32["max"]},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / pk["fp32_tflops"], "traffic": traffic,
+                     "traffic_note": None if traffic is not None else
+                     "no DRAM capture of the current kernel source; the batch is ALU-bound (per macro step "
+                     "it reads and writes the FP64 fields, 2 x %.0f MB, and the 1-D metric tables)"
+                     % (field_bytes / 1e6),
+                     "kernel": "batch_kernel (work queue per micro size, one launch per micro size and macro step)",
+                     "flop_per_macro_step": flop_step,
+                     "flop_per_point_update": "25 with a cross term, 20 without (%d of %d instances have one)"
+                                              % (n_cross, len(probs)),
+                     "kernel_ms_per_macro_step": 1e3 * per_macro_s,
+                     "peak_source": pk["fp32_source"]},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if ws == 1 and not args.no_extras:
+        del g, U, U0, flush
+        torch.cuda.empty_cache()
+        line["fp64_batch"] = batch_fp64(probs, n_macro, max(1, min(2, args.steps)), sel, U0h)
+        torch.cuda.empty_cache()
+        line["c2"] = run_c2(args, extra=True)
+    if ws == 1 and not args.no_cpu_baseline:      # the host baseline is a one-GPU figure
+        line["cpu_baseline"] = cpu_baseline_batch(probs[:64])
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# --------------------------------------------------------------------------
+# the 65x65 heterogeneous problem (persistent dataflow kernel)
+
+
+def run_c2(args, extra: bool = False):
+    """The 65x65 tanh-stretched heterogeneous tensor-diffusion problem, 11x11
+    micro points, 200 macro steps per bench step on the persistent dataflow
+    kernel.  extra=True returns a summary dict for the batch line instead of
+    printing a line of its own."""
+    import numpy as np
+    import torch
+
+    from paper_2405_08764_gb300.api import Grid
+
+    ws, rank, local = dist_env()
+    if extra:
+        ws, rank = 1, 0
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prob = replica_workload(rank, ws)
+    g = Grid(prob, prec="fp32")
+    info = g.info()
+    n_macro = prob["n_macro"]
+    dtm = info["dt_macro_suggested"]
+    fpu = flop_per_update(info["has_cross"])
+    updates = info["n_patch"] * info["m_xi"] * info["m_eta"] * info["k_micro"] * n_macro
+    U0 = g.init_field()
+    U = U0.clone()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    steps = args.steps
+    for _ in range(args.warmup):
+        U.copy_(U0)
+        g.step(U, 0.0, dtm, n_macro)
+    g.sync()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if not extra:
+        sampler.start()
+        time.sleep(0.3)
+    g.set_timing(True)
+    l0 = g.launches()
+    for s in range(steps):
         U.copy_(U0)
         flush.fill_(float(s))
         ev[s][0].record(stream)
-        g.step(U, 0.0, 0.0, n_macro)
+        g.step(U, 0.0, dtm, n_macro)
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     launches = g.launches() - l0
-    clocks = sampler.stop()
+    kern_ms, kern_n = g.timing()
+    g.set_timing(False)
+    clocks = sampler.stop() if not extra else None
     g.sync()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    value = updates * args.steps / (ms / 1e3)
-    pk = peaks()
-    achieved = FLOP_PER_UPDATE * value / 1e12
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": "%d uneven constant-coefficient CDR instances (N in {16,32,64,128}, m in {5,7,9,11}, "
-                               "identity/tanh/annulus maps), K=20, 100 macro steps" % len(probs),
-                   "point_updates_per_step": updates, "setup_s": setup_s, "first_step_s": first_s,
-                   "l2": "flushed between timed steps (512 MB write)"},
-        "macro_steps_per_s": n_macro * args.steps / (ms / 1e3),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
-                     "frac": achieved / pk["fp32_tflops"], "traffic": None,
-                     "kernel": "batch_kernel (work queue, one launch per macro step)"},
-        "gpu_launches": launches, "clocks": clocks,
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
+    if dist:
+        dist.barrier()
+    value = ws * updates * steps / (ms / 1e3)
+
+    Uh = U0.cpu().pin_memory()
+    Uout = torch.empty_like(Uh).pin_memory()
+    Ud = torch.empty_like(U0)
+    Ud.copy_(Uh, non_blocking=True)
+    g.step(Ud, 0.0, dtm, n_macro)        # graph capture for the new field pointer
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(steps):
+        Ud.copy_(Uh, non_blocking=True)
+        g.step(Ud, 0.0, dtm, n_macro)
+        Uout.copy_(Ud, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    e2e = ws * updates * steps / (e2e_ms / 1e3)
+    nbytes = U0.numel() * 8
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # accuracy: FP32 and FP64 GPU results against the FP64 CPU oracle
+    import oracle
+    o = oracle.Oracle(prob)
+    want = o.step(U0.cpu().numpy(), 0.0, dtm, n_macro)
+    U.copy_(U0)
+    g.step(U, 0.0, dtm, n_macro)
+    g.sync()
+    g64 = Grid(prob, prec="fp64")
+    V = g64.init_field()
+    g64.step(V, 0.0, dtm, n_macro)
+    g64.sync()
+    err = {"fp32": _rel_l2(U.cpu().numpy(), want), "fp64": _rel_l2(V.cpu().numpy(), want)}
+
+    pk = peaks(local)
+    per_launch_updates = updates / n_macro
+    achieved = (fpu * per_launch_updates * kern_n / (kern_ms / 1e3)) / 1e12 if kern_ms > 0 else None
+    sha = kernel_sources_sha(("pd_persist.cu", "pd_device.cuh", "pd_internal.h"))
+    traffic = None
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+        "frac": (achieved / pk["fp32_tflops"]) if achieved else None, "traffic": traffic,
+        "traffic_note": "no DRAM capture of this kernel: ncu fails the cooperative launch before it runs; a cold "
+                        "launch reads the 30.7 MB of burst records once, later steps find them in L2",
+        "kernel": ("patch_persist_kernel<11,cross,tsrc,float> (cooperative, %d macro steps per launch)"
+                   % info["chunk_steps"] if info["exec_path"] == 2 else
+                   "patch_warp_kernel<11,cross,tsrc,float,fused> (one macro step per launch)"),
+        "flop_per_point_update": fpu,
+        "kernel_ms_per_macro_step": kern_ms / kern_n if kern_n else None,
+        "peak_source": pk["fp32_source"],
+        "sources_sha256": sha[:16],
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_batch(probs[:64])
+    if extra:
+        return {"workload": C2_WORKLOAD, "value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                "macro_steps_per_s": n_macro * steps / (ms / 1e3), "l2_rel_err_vs_oracle": err,
+                "roofline": roofline, "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                                              "d2h_bytes_per_step": nbytes}}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": C2_WORKLOAD, "macro_steps_per_step": n_macro, "n_patch": info["n_patch"],
+                   "point_updates_per_step": updates, "dt_macro": dtm,
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "macro_steps_per_s": n_macro * steps / (ms / 1e3),
+        "l2_rel_err_vs_oracle": err["fp32"],
+        "l2_rel_err_vs_oracle_fp64_path": err["fp64"],
+        "roofline": roofline,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(prob)
     print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
+
+
+# --------------------------------------------------------------------------
+# other workloads
 
 
 def run_surrogate(args):
@@ -355,8 +755,11 @@ def run_surrogate(args):
 
     res = {}
     fields = {}
-    for name, prec in (("plain_fp64", "fp64"), ("plain_fp32", "fp32")):
-        g = Grid(p, prec=prec)
+    # plain_k1: the plain scheme with bursts of one micro step (tau = dt_micro),
+    # i.e. the residual check's own estimator F1 run as the scheme
+    for name, prec, k in (("plain_fp64", "fp64", None), ("plain_fp32", "fp32", None),
+                          ("plain_k1_fp32", "fp32", 1), ("plain_k1_fp64", "fp64", 1)):
+        g = Grid(p if k is None else dict(p, k_micro=k), prec=prec)
         dtm = g.info()["dt_macro_suggested"]
         U = g.init_field()
         g.step(U.clone(), 0.0, dtm, 2)          # warm-up (graph capture for 2 steps)
@@ -405,6 +808,7 @@ def run_surrogate(args):
         "macro_steps_per_s": {k: n_macro / v for k, v in res.items()},
         "speedup_vs_plain_fp64": res["plain_fp64"] / res["surrogate"],
         "speedup_vs_plain_fp32": res["plain_fp32"] / res["surrogate"],
+        "speedup_vs_plain_k1_fp32": res["plain_k1_fp32"] / res["surrogate"],
         "l2_rel_vs_plain_fp64": err,
         "served_by_network": served,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
@@ -489,7 +893,7 @@ def run_passes(args):
     clocks = sampler.stop()
     upd = pts * K
     res["burst"]["point_updates_per_s"] = upd / (res["burst"]["ms"] / 1e3)
-    res["burst"]["frac_fp32"] = FLOP_PER_UPDATE * res["burst"]["point_updates_per_s"] / 1e12 / pk["fp32_tflops"]
+    res["burst"]["frac_fp32"] = flop_per_update(info["has_cross"]) * res["burst"]["point_updates_per_s"] / 1e12 / pk["fp32_tflops"]
     line = {
         "metric": "separate C-ABI passes: achieved HBM GB/s (lift, restrict, project), burst point-updates/s",
         "value": res["lift"]["GB_per_s"], "unit": "GB/s", "n_gpus": 1, "higher_is_better": True,
@@ -704,138 +1108,6 @@ def run_refresh(args):
     return 0
 
 
-def run_gpu(args):
-    import numpy as np
-    import torch
-
-    from paper_2405_08764_gb300 import workloads as W
-    from paper_2405_08764_gb300.api import Grid
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    prob = replica_workload(rank, ws)
-    g = Grid(prob, prec="fp32")
-    info = g.info()
-    n_macro = prob["n_macro"]
-    dtm = info["dt_macro_suggested"]
-    updates = info["n_patch"] * info["m_xi"] * info["m_eta"] * info["k_micro"] * n_macro
-    U0 = g.init_field()
-    U = U0.clone()
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    # warm-up: graph capture and first replays
-    for _ in range(args.warmup):
-        U.copy_(U0)
-        g.step(U, 0.0, dtm, n_macro)
-    g.sync()
-
-    # timed region: K steps, per-step CUDA events, L2 flushed between steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
-    g.set_timing(True)
-    l0 = g.launches()
-    for s in range(args.steps):
-        U.copy_(U0)
-        flush.fill_(float(s))
-        ev[s][0].record(stream)
-        g.step(U, 0.0, dtm, n_macro)
-        ev[s][1].record(stream)
-    torch.cuda.synchronize()
-    launches = g.launches() - l0
-    kern_ms, kern_n = g.timing()
-    g.set_timing(False)
-    time.sleep(0.3)
-    clocks = sampler.stop()
-    g.sync()
-    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
-    if dist:
-        dist.barrier()
-    value = ws * updates * args.steps / (ms / 1e3)
-
-    # end to end through the public API with host buffers: pinned H2D of the
-    # initial field, pd_step, D2H of the result, all inside the timed region
-    Uh = U0.cpu().pin_memory()
-    Uout = torch.empty_like(Uh).pin_memory()
-    Ud = torch.empty_like(U0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for s in range(args.steps):
-        Ud.copy_(Uh, non_blocking=True)
-        g.step(Ud, 0.0, dtm, n_macro)
-        Uout.copy_(Ud, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-    e2e = ws * updates * args.steps / (e2e_ms / 1e3)
-    nbytes = U0.numel() * 8
-
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return 0
-
-    # accuracy at this configuration: FP32 result against the FP64 path
-    g64 = Grid(prob, prec="fp64")
-    V = g64.init_field()
-    g64.step(V, 0.0, dtm, n_macro)
-    g64.sync()
-    a, b = U.cpu().numpy(), V.cpu().numpy()
-    l2 = float(np.linalg.norm(a - b) / np.linalg.norm(b))
-
-    pk = peaks()
-    per_launch_updates = updates / n_macro
-    achieved = (FLOP_PER_UPDATE * per_launch_updates * kern_n / (kern_ms / 1e3)) / 1e12 if kern_ms > 0 else None
-    sha = kernel_sources_sha()
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sources_sha256"] == sha else None
-    roofline = {
-        "bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
-        "frac": (achieved / pk["fp32_tflops"]) if achieved else None, "traffic": traffic,
-        "traffic_note": None if traffic is not None else
-        ("no DRAM capture of this kernel: ncu fails the cooperative launch before it runs; a cold launch "
-         "reads the 30.7 MB of burst records once, later steps find them in L2"),
-        "kernel": ("patch_persist_kernel<11,cross,tsrc,float> (cooperative, %d macro steps per launch)"
-                   % info["chunk_steps"] if info["exec_path"] == 2 else
-                   "patch_warp_kernel<11,cross,tsrc,float,fused> (one macro step per launch)"),
-        "flop_per_point_update": FLOP_PER_UPDATE,
-        "kernel_ms_per_macro_step": kern_ms / kern_n if kern_n else None,
-        "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (
-            pk["sm_max_mhz"], pk["source"]),
-    }
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "macro_steps_per_step": n_macro, "n_patch": info["n_patch"],
-                   "point_updates_per_step": updates, "dt_macro": dtm,
-                   "l2": "flushed between timed steps (512 MB write)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "macro_steps_per_s": n_macro * args.steps / (ms / 1e3),
-        "l2_rel_err_vs_fp64": l2,
-        "roofline": roofline,
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-        "gpu_launches": launches,
-        "clocks": clocks,
-    }
-    if not args.no_cpu_baseline and ws == 1:      # the host baseline is a one-GPU figure
-        line["cpu_baseline"] = cpu_baseline(prob)
-    print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    return 0
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -843,25 +1115,28 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "passes", "adi", "refresh"],
-                    help="c2: the benchmark workload (default); c4: the 4096-instance batch; "
+    ap.add_argument("--no-extras", action="store_true",
+                    help="c4: leave out the FP64 batch and the 65x65 problem from the line")
+    ap.add_argument("--workload", default="c4", choices=["c4", "c2", "c5", "passes", "adi", "refresh"],
+                    help="c4: the 4096-instance batch (default); c2: the 65x65 heterogeneous problem alone; "
                          "c5: the surrogate against the plain scheme on the 512x2048 annulus; "
                          "passes: the separate C-ABI passes on that annulus; "
                          "adi: ADI bursts at the paper's Section 4.1 patch settings; "
                          "refresh: edge-data refresh Q = 1, 2, 4, 10 on the annulus")
+    ap.add_argument("--macro", type=int, default=C4_MACRO, help="c4: macro steps per bench step")
     ap.add_argument("--adi-n", type=int, default=400, help="adi: macro intervals per side")
     ap.add_argument("--epochs", type=int, default=80, help="c5: training epochs")
     ap.add_argument("--c5-grid", default="511x2048", help="c5: radial intervals x angular nodes")
     ap.add_argument("--batch", type=int, default=2048, help="c5: training minibatch")
-    ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--instances", type=int, default=N_INST)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     import __graft_entry__
     __graft_entry__.build()
-    if args.workload == "c4":
-        return run_batch(args)
+    if args.workload == "c2":
+        return run_c2(args)
     if args.workload == "c5":
         return run_surrogate(args)
     if args.workload == "passes":
@@ -870,7 +1145,7 @@ def main():
         return run_adi(args)
     if args.workload == "refresh":
         return run_refresh(args)
-    return run_gpu(args)
+    return run_batch(args)
 
 
 if __name__ == "__main__":

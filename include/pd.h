@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define PD_ABI_VERSION 1
+#define PD_ABI_VERSION 2
 
 typedef enum {
     PD_OK = 0,
@@ -148,12 +148,17 @@ typedef struct {
                                      macro step, 2 persistent dataflow kernel, 3 batched
                                      work-queue kernel (several instances or table storage) */
     int chunk_steps;              /* macro steps per persistent launch (path 2) */
+    int has_cross;                /* 1 when beta (the mixed-derivative coefficient) is not
+                                     identically zero on this instance */
+    int has_tsrc;                 /* 1 when the source has a time factor */
 } pd_info;
 
 /* Create a grid of n_inst instances, descs[0..n_inst-1] (host array, copied);
  * instances may differ in every field except the precision.
  * `cuda_stream` is a cudaStream_t (NULL = default stream).  Allocates the
- * per-instance coefficient and scratch buffers on the current device.
+ * per-instance coefficient and scratch buffers on the current device, which
+ * becomes the grid's device: later calls on the grid make it current for
+ * their own work and restore the caller's current device before returning.
  * Errors: PD_EINVAL (bad descriptor), PD_ENOMEM, PD_ECUDA. */
 pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_stream, pd_grid** out);
 pd_status pd_destroy_grid(pd_grid* g);
@@ -263,17 +268,24 @@ pd_status pd_set_edge_refresh(pd_grid* g, int q);
  * tables on first use; this call instead carves both out of one fixed
  * 4 MiB device array per device (524288 doubles) that lives in the library.
  * Limits: a grid of one instance, per-point coefficient records (the default
- * for one instance), m_xi == m_eta in {3,5,7,9,11}; the need is
+ * for one instance), m_xi == m_eta in {3,5,7,9,11}, the forward-Euler outer
+ * step and fixed edge data (a grid set to Heun or AB2 by pd_set_integrator,
+ * or to q > 1 by pd_set_edge_refresh, is refused with PD_EINVAL rather than
+ * stepped differently from pd_step); forward-Euler and ADI bursts both run.
+ * The need is
  * roundup32(nxp*nyp) + n_macro*(k_micro + 3) doubles, and a larger request
  * is rejected with PD_EINVAL (take fewer macro steps per call).  Nothing in
  * the array has to start at zero: every step writes the whole next field and
  * the time table is written before it is read.  All calls on a device share
  * the array: two calls whose work overlaps in time (different streams,
  * grids or host threads without ordering between them) race and corrupt
- * each other's results; order them on one stream.  The first call on a
- * device looks up the array's address (set-up work in the CUDA runtime) and
- * should precede any stream capture.  Results equal pd_step's per-step
- * kernel path.  Errors: PD_EINVAL, PD_ESTATE, PD_ECUDA. */
+ * each other's results; order them on one stream.  Every call looks up the
+ * array's address in the current context of the grid's device (so a context
+ * created again after cudaDeviceReset is served correctly); the first lookup
+ * in a context loads the library's device code (set-up work in the CUDA
+ * runtime), so the first call on a device should precede any stream capture.
+ * The caller's current device is unchanged on return.  Results equal
+ * pd_step's per-step kernel path.  Errors: PD_EINVAL, PD_ESTATE, PD_ECUDA. */
 pd_status pd_step_noalloc(pd_grid* g, double* U_dev, double t0, double dt_macro, int n_macro);
 
 /* Coefficient storage (call before pd_set_coeffs): 0 auto (default: 1-D metric

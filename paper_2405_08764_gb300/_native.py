@@ -59,6 +59,7 @@ class Info(C.Structure):
         ("state_bytes", C.c_size_t), ("off_u0", C.c_size_t), ("off_r", C.c_size_t),
         ("off_w", C.c_size_t), ("off_edge", C.c_size_t), ("off_bias", C.c_size_t),
         ("edge_stride", C.c_int), ("exec_path", C.c_int), ("chunk_steps", C.c_int),
+        ("has_cross", C.c_int), ("has_tsrc", C.c_int),
     ]
 
 

@@ -7,7 +7,6 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -873,7 +872,7 @@ pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_strea
 pd_status pd_destroy_grid(pd_grid* g)
 {
     if (!g) return PD_EINVAL;
-    cudaSetDevice(g->device);
+    DeviceGuard dg(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
     for (auto& pr : g->tev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -914,7 +913,7 @@ pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
     if (c->n_four > 0 && !(c->four_rb > c->four_ra)) return fail(g, PD_EINVAL, "four_rb must exceed four_ra");
     if (c->src == PD_SRC_GAUSS_PATCH && !c->src_amp) return fail(g, PD_EINVAL, "GAUSS_PATCH needs src_amp");
     Inst& s = g->inst[inst];
-    cudaSetDevice(g->device);
+    DeviceGuard dg(g->device);
     if (c->src == PD_SRC_GAUSS_PATCH) {
         if (!s.amp) PD_CUDA(g, cudaMalloc(&s.amp, sizeof(double) * s.I.n_patch));
         PD_CUDA(g, cudaMemcpyAsync(s.amp, c->src_amp, sizeof(double) * s.I.n_patch, cudaMemcpyHostToDevice, g->stream));
@@ -1033,6 +1032,8 @@ pd_status pd_query(const pd_grid* gc, int inst, pd_info* o)
     else o->exec_path = !fused_supported(s.I) ? 0
                       : (g->persist && s.coef_set && s.I.micro == PD_MICRO_FE && persist_fits(s.I, s.d.prec)) ? 2 : 1;
     o->chunk_steps = o->exec_path == 2 ? persist_max_steps(s.I, s.d.prec) : 1;
+    o->has_cross = s.I.has_cross != 0;
+    o->has_tsrc = s.I.has_tsrc != 0;
     return PD_OK;
 }
 
@@ -1052,6 +1053,7 @@ pd_status pd_get_coeffs(pd_grid* g, int inst, double* out)
     Inst& s = g->inst[inst];
     if (!s.coef_set) return fail(g, PD_ESTATE, "coefficients not set");
     if (!out) return fail(g, PD_EINVAL, "null output");
+    DeviceGuard dg(g->device);
     if (s.I.coef_mode != COEF_RECORDS) PD_CUDA(g, launch_table_get_coeffs(s.I, out, g->stream));
     else PD_CUDA(g, launch_get_coeffs(s.I, s.d.prec, out, g->stream));
     g->launches += 1;
@@ -1066,6 +1068,7 @@ pd_status pd_init_field(pd_grid* g, int inst, int kind, const double* prm, int n
     if (!U) return fail(g, PD_EINVAL, "null field");
     if (kind < 0 || kind > 4) return fail(g, PD_EINVAL, "unknown init kind");
     if ((kind == PD_INIT_EXACT) && !s.coef_set) return fail(g, PD_ESTATE, "EXACT needs pd_set_coeffs");
+    DeviceGuard dg(g->device);
     double mu[8] = { 0 };
     if (kind == PD_INIT_BESSEL) {
         if (!prm || n_prm < 3 || prm[0] < 1 || prm[0] > 8 || n_prm < 3 + (int)prm[0])
@@ -1087,6 +1090,7 @@ pd_status pd_lift(pd_grid* g, const double* U, double t, void* state)
     if (((uintptr_t)state) & 255) return fail(g, PD_EINVAL, "state buffer must be 256-byte aligned");
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
+    DeviceGuard dg(g->device);
     for (auto& s : g->inst) {
         pd_info lay;
         layout(g, s, lay);
@@ -1104,6 +1108,7 @@ pd_status pd_micro_burst(pd_grid* g, void* state, double t, int k_steps)
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
     if (k_steps == 0) return PD_OK;
+    DeviceGuard dg(g->device);
     for (auto& s : g->inst)
         if (s.I.micro != PD_MICRO_FE) return fail(g, PD_EINVAL, "the ADI micro solver runs inside pd_step only");
     for (auto& s : g->inst) {
@@ -1121,6 +1126,7 @@ pd_status pd_restrict(pd_grid* g, const void* state, double* dU)
     if (!state || !dU) return fail(g, PD_EINVAL, "null pointer");
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
+    DeviceGuard dg(g->device);
     for (auto& s : g->inst) {
         pd_info lay;
         layout(g, s, lay);
@@ -1137,6 +1143,7 @@ pd_status pd_project(pd_grid* g, double* U, const double* dU, double t, double d
     if (!(dtm > 0)) return fail(g, PD_EINVAL, "dt_macro must be positive");
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
+    DeviceGuard dg(g->device);
     for (auto& s : g->inst) {
         PD_CUDA(g, launch_project(s.I, U + s.I.u_off, dU, t, dtm, g->stream));
         g->launches += 1;
@@ -1152,7 +1159,7 @@ pd_status pd_step(pd_grid* g, double* U, double t0, double dt_macro, int n_macro
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
     if (n_macro == 0) return PD_OK;
-    cudaSetDevice(g->device);
+    DeviceGuard dg(g->device);
     std::vector<double> dtm(g->inst.size());
     for (size_t k = 0; k < g->inst.size(); ++k) dtm[k] = dt_macro > 0 ? dt_macro : g->inst[k].dtm_sugg;
     if (g->q_refresh > 1) {
@@ -1242,6 +1249,7 @@ pd_status pd_autotune(pd_grid* g, int n_trial_steps, int* block, int* half_patch
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
     if (!use_batch(g) || !all_batch_supported(g)) return fail(g, PD_ESTATE, "autotuning applies to batched grids");
+    DeviceGuard dg(g->device);
     rc = batch_autotune(g, std::max(1, n_trial_steps));
     if (rc) return rc;
     if (block) *block = g->bt_block;
@@ -1341,6 +1349,7 @@ pd_status pd_get_timing(pd_grid* g, double* ms, long long* n)
 pd_status pd_sync(pd_grid* g)
 {
     if (!g) return PD_EINVAL;
+    DeviceGuard dg(g->device);
     PD_CUDA(g, cudaStreamSynchronize(g->stream));
     int h = 0;
     PD_CUDA(g, cudaMemcpy(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1371,6 +1380,7 @@ const char kMagic[8] = { 'P', 'D', 'C', 'K', 'P', 'T', '0', '1' };
 pd_status pd_save_checkpoint(pd_grid* g, const double* U, double t, long long step, const char* path)
 {
     if (!g || !U || !path) return fail(g, PD_EINVAL, "null argument");
+    DeviceGuard dg(g->device);
     std::vector<double> h((size_t)g->n_macro_total);
     PD_CUDA(g, cudaMemcpyAsync(h.data(), U, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
     PD_CUDA(g, cudaStreamSynchronize(g->stream));
@@ -1388,6 +1398,7 @@ pd_status pd_save_checkpoint(pd_grid* g, const double* U, double t, long long st
 pd_status pd_load_checkpoint(pd_grid* g, double* U, double* t, long long* step, const char* path)
 {
     if (!g || !U || !path) return fail(g, PD_EINVAL, "null argument");
+    DeviceGuard dg(g->device);
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(g, PD_EINVAL, std::string("cannot open ") + path);
     char mg[8];
@@ -1449,25 +1460,20 @@ void grid_count_launches(pd_grid* g, long long n)
 namespace {
 
 constexpr size_t kNoAllocDoubles = size_t(1) << 19;   // 4 MiB per device
-constexpr int kNoAllocDevices = 64;
 
 static __device__ __align__(256) double noalloc_scratch[kNoAllocDoubles];
 
-std::mutex noalloc_mu;
-double* noalloc_base[kNoAllocDevices] = {};
-
-// device address of the array on the grid's device, looked up once per device
+// Device address of the array in the current context of the grid's device
+// (the caller holds a DeviceGuard for it).  In host code the array's name is
+// only a host-side stand-in, so kernels get this address instead.  It is looked
+// up on every call rather than cached: a context torn down and created again
+// (cudaDeviceReset) loads the module at another address.  The first lookup in
+// a context loads the module (set-up work in the CUDA runtime).
 pd_status noalloc_scratch_on(pd_grid* g, double** out)
 {
-    std::lock_guard<std::mutex> lk(noalloc_mu);
-    if (g->device < 0 || g->device >= kNoAllocDevices) return fail(g, PD_EINVAL, "device ordinal out of range");
-    if (!noalloc_base[g->device]) {
-        PD_CUDA(g, cudaSetDevice(g->device));
-        void* p = nullptr;
-        PD_CUDA(g, cudaGetSymbolAddress(&p, noalloc_scratch));
-        noalloc_base[g->device] = static_cast<double*>(p);
-    }
-    *out = noalloc_base[g->device];
+    void* p = nullptr;
+    PD_CUDA(g, cudaGetSymbolAddress(&p, noalloc_scratch));
+    *out = static_cast<double*>(p);
     return PD_OK;
 }
 
@@ -1483,6 +1489,10 @@ pd_status pd_step_noalloc(pd_grid* g, double* U, double t0, double dt_macro, int
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
     if (g->inst.size() != 1) return fail(g, PD_EINVAL, "pd_step_noalloc takes a grid of one instance");
+    if (g->integrator != PD_INT_EULER)
+        return fail(g, PD_EINVAL, "pd_step_noalloc runs the forward-Euler outer step only (pd_set_integrator)");
+    if (g->q_refresh > 1)
+        return fail(g, PD_EINVAL, "pd_step_noalloc keeps the edge data fixed over a burst (pd_set_edge_refresh q = 1)");
     Inst& s = g->inst[0];
     const InstDev& I = s.I;
     if (I.coef_mode != COEF_RECORDS || !fused_supported(I))
@@ -1495,11 +1505,11 @@ pd_status pd_step_noalloc(pd_grid* g, double* U, double t0, double dt_macro, int
         return fail(g, PD_EINVAL, "pd_step_noalloc needs " + std::to_string(need) +
                                   " doubles of fixed scratch (field + n_macro time-table rows); the limit is " +
                                   std::to_string(kNoAllocDoubles) + ": take fewer macro steps per call");
+    if (n_macro == 0) return PD_OK;
+    DeviceGuard dg(g->device);
     double* base = nullptr;
     rc = noalloc_scratch_on(g, &base);
     if (rc) return rc;
-    if (n_macro == 0) return PD_OK;
-    PD_CUDA(g, cudaSetDevice(g->device));
     const double dtm = dt_macro > 0 ? dt_macro : s.dtm_sugg;
     double* tab = base + field;
     PD_CUDA(g, launch_time_table(I, t0, dtm, n_macro, tab, g->stream));

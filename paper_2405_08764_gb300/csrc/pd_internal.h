@@ -389,6 +389,24 @@ __device__ __forceinline__ double exact_solution(int sol, double x, double y, do
 
 enum ErrBits { ERR_NONFINITE = 1, ERR_JACOBIAN = 2, ERR_COEF = 4, ERR_TIMEOUT = 8 };
 
+// Makes `dev` the calling thread's current device for the lifetime of the
+// guard and restores the caller's device afterwards, so a host thread that
+// drives several devices finds its current device unchanged after any call.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) switched = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (switched) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // ---------------------------------------------------------------------------
 // host-side launch helpers (defined in the .cu files)
 struct StepLaunch {

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version_and_status_strings(lib):
     lib.pd_abi_version.restype = ctypes.c_int
-    assert lib.pd_abi_version() == 1
+    assert lib.pd_abi_version() == 2
     lib.pd_status_str.restype = ctypes.c_char_p
     lib.pd_status_str.argtypes = [ctypes.c_int]
     assert lib.pd_status_str(0) == b"ok"

@@ -102,8 +102,43 @@ def _bench(args, env_extra):
     return lines
 
 
+def _digest(probs):
+    h = hashlib.sha256()
+    for p in probs:
+        h.update(repr(sorted((k, v) for k, v in p.items() if k != "src_amp")).encode())
+    return h.hexdigest()
+
+
+def test_batch_replicas_keep_the_recipe_and_differ_by_rank():
+    import bench
+    from paper_2405_08764_gb300 import workloads as W
+    one = bench.replica_batch(0, 1)
+    assert len(one) == 4096
+    assert _digest(one) == _digest(W.c4_batch(4096))          # the one-GPU workload itself
+    assert _digest(bench.replica_batch(0, 2)) == _digest(one)   # rank 0 of a launch runs it too
+    r1 = bench.replica_batch(1, 2)
+    assert len(r1) == 4096 and _digest(r1) != _digest(one)
+    assert _digest(bench.replica_batch(1, 2)) == _digest(r1)
+    for p in r1:
+        assert p["n_xi"] in (16, 32, 64, 128) and p["m_xi"] in (5, 7, 9, 11) and p["k_micro"] == 20
+
+
+def test_batch_update_count_and_accuracy_sample():
+    import bench
+    from paper_2405_08764_gb300 import workloads as W
+    probs = W.c4_batch(64)
+    n = bench.batch_updates(probs, 3)
+    assert n == 3 * sum(W.n_patch(p) * p["m_xi"] ** 2 * 20 for p in probs)
+    sel = bench.accuracy_sample(probs)
+    assert sel == sorted(set(sel)) and sel[-1] == len(probs) - 1
+    assert {probs[k]["map"] for k in sel} == {"identity", "tanh", "polar"}
+    assert {probs[k]["m_xi"] for k in sel} == {5, 7, 9, 11}
+    assert bench.flop_per_update(True) == 25.0 and bench.flop_per_update(False) == 20.0
+
+
 def test_reference_arm_prints_one_contract_line_on_rank_0_only():
-    lines = _bench(["--impl", "reference", "--steps", "1", "--warmup", "3"], {"OMP_NUM_THREADS": "2"})
+    lines = _bench(["--impl", "reference", "--steps", "1", "--warmup", "3", "--instances", "6"],
+                   {"OMP_NUM_THREADS": "2"})
     assert len(lines) == 1
     d = lines[0]
     assert d["impl"] == "reference" and d["higher_is_better"] is True and d["value"] > 0
@@ -113,6 +148,10 @@ def test_reference_arm_prints_one_contract_line_on_rank_0_only():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["unit"] == d["e2e"]["unit"] == d["cpu_baseline"]["unit"]
     assert "workload" in d["config"]
+    assert "4096" in d["config"]["workload"]
     # other ranks of a torchrun launch exit without work
     assert _bench(["--impl", "reference", "--steps", "1", "--warmup", "3"],
                   {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+    # the 65x65 problem's reference line
+    c2 = _bench(["--impl", "reference", "--workload", "c2", "--steps", "1", "--warmup", "1"], {"OMP_NUM_THREADS": "2"})
+    assert len(c2) == 1 and "65x65" in c2[0]["config"]["workload"] and c2[0]["value"] > 0

@@ -264,6 +264,122 @@ def test_full_size_heterogeneous_workload_fp32(env, orc):
     assert err <= 1e-4, err
 
 
+def test_full_size_heterogeneous_workload_fp64(env, orc):
+    """The same full run in FP64 (per-step and persistent kernels alike run
+    the FP64 bursts) within the FP64 bound of the oracle."""
+    p = W.c2_heterogeneous()
+    got, want, g = _run_both(env, orc, p, "fp64", n=200)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= 1e-12, err
+
+
+def _literal_tol(o, p, dtm, n):
+    """FP64 bound against the literal recursion: the parity bound 1e-12 plus the
+    literal form's own cancellation.  The literal burst evolves u itself, so each
+    of its K forward-Euler updates rounds at |u| eps, and the restricted change
+    U1 - U0 that the step divides by tau keeps that absolute error; the macro
+    step multiplies it by dt_macro / tau.  Over n macro steps: n K (dt/tau) eps,
+    relative to |U| (a worst case: the roundings are not all aligned)."""
+    return 1e-12 + n * p["k_micro"] * (dtm / o.tau()) * 2.0 ** -52
+
+
+@pytest.mark.parametrize("name", ["c1", "c2s", "p411", "p412", "macro", "polar_aniso", "m3", "tiny"])
+def test_step_fp64_against_the_literal_recursion(env, orc, name):
+    """The GPU evaluates each burst in the split form (departure from the lift,
+    closed-form forcing); the oracle's literal form runs eq. (Computational_Problem)
+    on u itself with the explicit ghost points of the edge data, restricts u and
+    forms (U1 - U0)/tau as eq. (Time_Derivative) prints it.  The two meet within
+    the FP64 bound widened by the literal form's cancellation."""
+    p = CASES[name]
+    o = orc.Oracle(p)
+    dtm, n = _steps(p, o)
+    g = env(p, prec="fp64")
+    U = g.init_field()
+    U0 = U.cpu().numpy()
+    g.step(U, p.get("t0", 0.0), dtm, n)
+    g.sync()
+    want = o.step(U0, p.get("t0", 0.0), dtm, n, form="literal")
+    err = np.linalg.norm(U.cpu().numpy() - want) / np.linalg.norm(want)
+    assert err <= _literal_tol(o, p, dtm, n), (name, err, _literal_tol(o, p, dtm, n))
+
+
+def test_full_size_heterogeneous_workload_against_the_literal_recursion(env, orc):
+    """65 x 65, m = 11, 200 macro steps in FP64 against the oracle's literal
+    recursion (tau ~ dt_macro / 60 here, the regime where the literal quotient
+    cancels most)."""
+    p = W.c2_heterogeneous()
+    o = orc.Oracle(p)
+    dtm, _ = _steps(p, o)
+    g = env(p, prec="fp64")
+    U = g.init_field()
+    U0 = U.cpu().numpy()
+    g.step(U, 0.0, dtm, 200)
+    g.sync()
+    want = o.step(U0, 0.0, dtm, 200, form="literal")
+    err = np.linalg.norm(U.cpu().numpy() - want) / np.linalg.norm(want)
+    assert err <= _literal_tol(o, p, dtm, 200), err
+
+
+def test_batched_instances_against_the_literal_recursion(env, orc):
+    """Six uneven batched instances (work-queue kernel, metric tables) in FP64
+    against the literal recursion, each at its own suggested macro step."""
+    probs = [dict(W.c4_instance(i), n_xi=min(W.c4_instance(i)["n_xi"], 32),
+                  n_eta=min(W.c4_instance(i)["n_eta"], 32)) for i in range(6)]
+    g = env(probs, prec="fp64")
+    U = g.init_field()
+    U0 = U.cpu().numpy()
+    g.step(U, 0.0, 0.0, 6)
+    g.sync()
+    got = U.cpu().numpy()
+    for k, p in enumerate(probs):
+        i = g.info(k)
+        a, nn = i["u_offset"], i["n_macro"]
+        o = orc.Oracle(p)
+        want = o.step(U0[a:a + nn], 0.0, o.dt_macro(), 6, form="literal")
+        err = np.linalg.norm(got[a:a + nn] - want) / np.linalg.norm(want)
+        assert err <= _literal_tol(o, p, o.dt_macro(), 6), (k, p["map"], p["m_xi"], err)
+
+
+@pytest.mark.parametrize("field", ["burst", "mixed_signs"])
+def test_fp32_restriction_sum_error_is_bounded(env, field):
+    """The FP32 path sums the trapezoid average of the departure in FP32 (the
+    separate pass: four strided FMA chains and a two-level shuffle tree; the
+    fused kernels: column sums and a log2(m)-level tree), then forms dU in FP64.
+    Against the exact sum of the same FP32 values, the error of any summation
+    order with at most n additions on a path is bounded by
+    gamma_n * sum |weight * w| (gamma_n = n u / (1 - n u), u = 2^-24), and the
+    restricted change must stay within it for the departures of a real burst
+    and for a field of random signs."""
+    p = CASES["c2s"]
+    g = env(p, prec="fp32")
+    i = g.info()
+    mx, my = i["m_xi"], i["m_eta"]
+    U = g.init_field()
+    st = g.new_state()
+    g.lift(U, 0.0, st)
+    g.micro_burst(st, 0.0, p["k_micro"])
+    v = g.state_views(st)
+    if field == "mixed_signs":
+        rng = np.random.default_rng(7)
+        v["w"].copy_(torch.tensor(rng.normal(size=tuple(v["w"].shape)) * 1e-6, dtype=torch.float32))
+    dU = g.restrict(st).cpu().numpy()
+    w = v["w"].cpu().numpy().astype(np.float64)
+    bias = v["bias"].cpu().numpy()
+    tw = np.outer(np.where((np.arange(my) == 0) | (np.arange(my) == my - 1), 0.5, 1.0),
+                  np.where((np.arange(mx) == 0) | (np.arange(mx) == mx - 1), 0.5, 1.0))
+    inv_nn = 1.0 / ((mx - 1) * (my - 1))
+    exact = (w * tw).sum(axis=(1, 2)) * inv_nn + bias
+    mag = (np.abs(w) * tw).sum(axis=(1, 2)) * inv_nn
+    n_add = max(-(-mx * my // 4) + 2, mx + int(np.ceil(np.log2(mx)))) + 1
+    u = 2.0 ** -24
+    gamma = n_add * u / (1 - n_add * u)
+    assert np.all(np.abs(dU - exact) <= gamma * mag + 1e-300), np.max(np.abs(dU - exact) / (gamma * mag))
+    if field == "burst":
+        # departures of one sign inside a patch: the sum's relative error is far
+        # below the 1e-4 bound of the FP32 path
+        assert np.max(np.abs(dU - exact) / np.maximum(np.abs(exact - bias), 1e-300)) <= 1e-5
+
+
 def test_full_size_annulus_sampled_patches(env, orc):
     """128 x 512 annulus (m = 9): one macro step of dU on the GPU against the
     oracle on 300 sampled patches (including the periodic seam and both walls)."""
@@ -310,6 +426,39 @@ def test_checkpoint_roundtrip(env, orc, tmp_path):
     from paper_2405_08764_gb300 import _native as N
     with pytest.raises(N.PDError):
         g2.load_checkpoint(torch.zeros(g2.n_macro_total, dtype=torch.float64, device="cuda"), path)
+
+
+@pytest.mark.parametrize("name", ["c3s", "polar_aniso", "batch"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_resume_from_checkpoint_equals_uninterrupted_run(env, tmp_path, name, prec):
+    """n macro steps, a checkpoint, a fresh grid that loads it and m more steps
+    give bitwise the field of n + m uninterrupted steps.  The problems carry no
+    time-dependent source or boundary data, so both runs see the same time
+    levels exactly (with time dependence the resumed time origin t0 + n dt is
+    rounded once more).  Covers the persistent dataflow path (annulus), the
+    per-step fused path with a cross term (anisotropic annulus) and the batched
+    work queue (six uneven instances)."""
+    probs = [dict(W.c4_instance(i), n_xi=min(W.c4_instance(i)["n_xi"], 32),
+                  n_eta=min(W.c4_instance(i)["n_eta"], 32)) for i in range(6)] if name == "batch" else CASES[name]
+    n, m = 5, 4
+    dtm = 0.0 if name == "batch" else 0.5 * env(probs, prec="fp64").info()["dt_macro_suggested"]
+    ref = env(probs, prec=prec)
+    U = ref.init_field()
+    ref.step(U, 0.0, dtm, n + m)
+    ref.sync()
+    a = env(probs, prec=prec)
+    V = a.init_field()
+    a.step(V, 0.0, dtm, n)
+    path = str(tmp_path / "resume.bin")
+    a.save_checkpoint(V, n * dtm, n, path)
+    del a
+    b = env(probs, prec=prec)
+    W2 = torch.full_like(V, float("nan"))
+    t, s = b.load_checkpoint(W2, path)
+    assert s == n and t == n * dtm
+    b.step(W2, t, dtm, m)
+    b.sync()
+    assert torch.equal(W2, U), float((W2 - U).abs().max())
 
 
 def test_invalid_calls_are_rejected(env, orc):

@@ -14,6 +14,8 @@ CASES = {
     "c2_m11": W.c2_heterogeneous(n=24, m=11, n_macro=16),
     "c1_m7": W.c1_manufactured(n=12, m=7),
     "annulus_m9": W.c3_annulus(n_r=11, n_theta=26, m=9),
+    # Section 4.1 with the paper's ADI bursts (two nano steps per burst)
+    "paper411_adi": W.paper_cdr_adi(False, 0.1, 10, 2000),
 }
 
 
@@ -63,3 +65,23 @@ def test_rejects_requests_beyond_the_fixed_array(Grid):
     with pytest.raises(N.PDError) as e:
         h.step_noalloc(W2, 0.0, 0.0, 1)
     assert e.value.status == N.PD_EINVAL
+
+
+@pytest.mark.parametrize("setting", ["heun", "ab2", "q_refresh"])
+def test_refuses_grids_that_pd_step_would_step_differently(Grid, setting):
+    """A second-order outer integrator or an edge refresh changes what pd_step
+    computes; the fixed-scratch call runs neither, so it refuses such a grid
+    instead of silently taking forward-Euler steps with fixed edge data."""
+    from paper_2405_08764_gb300 import _native as N
+    p = CASES["c1_m7"]
+    if setting == "q_refresh":
+        g = Grid(dict(p, q_refresh=2), prec="fp64", persistent=False)
+    else:
+        g = Grid(p, prec="fp64", persistent=False, integrator=setting)
+    U = g.init_field()
+    before = U.clone()
+    with pytest.raises(N.PDError) as e:
+        g.step_noalloc(U, 0.0, 0.0, 2)
+    assert e.value.status == N.PD_EINVAL
+    g.sync()
+    assert torch.equal(U, before)
