@@ -106,6 +106,9 @@ struct pd_grid {
     InstDev* insts_dev = nullptr;
     BatchItem* items_dev = nullptr;
     int n_items = 0;
+    // micro-size classes of the batch: items [cls_beg[c], cls_beg[c] + cls_n[c])
+    // are the patch groups and boundary chunks of the instances with m = cls_m[c]
+    std::vector<int> cls_m, cls_beg, cls_n;
     bool batch_dirty = true;
     double* dtm_dev = nullptr;
     std::vector<double> dtm_host;
@@ -537,19 +540,30 @@ pd_status prepare_batch(pd_grid* g)
         s.I.ppw = g->bt_half ? std::max(1, (P + 1) / 2) : P;
         host[k] = s.I;
     }
-    // patch groups, costliest micro size first so the tail of the queue holds small items
-    std::vector<size_t> order(n);
-    for (size_t k = 0; k < n; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return g->inst[x].I.mx > g->inst[y].I.mx; });
-    for (size_t k : order) {
-        const InstDev& I = g->inst[k].I;
-        int wpr = (I.ncols + I.ppw - 1) / I.ppw;
-        for (int jr = 0; jr < I.nrows; ++jr)
-            for (int wc = 0; wc < wpr; ++wc) items.push_back(BatchItem{ (int)k, 0, jr, wc });
-    }
-    for (size_t k = 0; k < n; ++k) {
-        int chunks = (g->inst[k].I.n_bnd + 31) / 32;
-        for (int c = 0; c < chunks; ++c) items.push_back(BatchItem{ (int)k, 1, c, 0 });
+    // one class per micro size (largest first); in each class the patch groups,
+    // then the boundary chunks of the class's instances
+    std::vector<int> sizes;
+    for (size_t k = 0; k < n; ++k)
+        if (std::find(sizes.begin(), sizes.end(), g->inst[k].I.mx) == sizes.end()) sizes.push_back(g->inst[k].I.mx);
+    std::sort(sizes.rbegin(), sizes.rend());
+    g->cls_m.clear(); g->cls_beg.clear(); g->cls_n.clear();
+    for (int m : sizes) {
+        const int beg = (int)items.size();
+        for (size_t k = 0; k < n; ++k) {
+            const InstDev& I = g->inst[k].I;
+            if (I.mx != m) continue;
+            int wpr = (I.ncols + I.ppw - 1) / I.ppw;
+            for (int jr = 0; jr < I.nrows; ++jr)
+                for (int wc = 0; wc < wpr; ++wc) items.push_back(BatchItem{ (int)k, 0, jr, wc });
+        }
+        for (size_t k = 0; k < n; ++k) {
+            if (g->inst[k].I.mx != m) continue;
+            int chunks = (g->inst[k].I.n_bnd + 31) / 32;
+            for (int c = 0; c < chunks; ++c) items.push_back(BatchItem{ (int)k, 1, c, 0 });
+        }
+        g->cls_m.push_back(m);
+        g->cls_beg.push_back(beg);
+        g->cls_n.push_back((int)items.size() - beg);
     }
     if (!g->insts_dev) PD_CUDA(g, cudaMalloc(&g->insts_dev, sizeof(InstDev) * n));
     PD_CUDA(g, cudaMemcpy(g->insts_dev, host.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice));
@@ -584,10 +598,13 @@ pd_status batch_buffers(pd_grid* g, int n_macro, const std::vector<double>& dtm)
         PD_CUDA(g, cudaMemcpy(g->dtm_dev, dtm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
         g->dtm_host = dtm;
     }
-    if ((size_t)n_macro > g->counters_n) {
+    // one work-queue counter per macro step and micro-size class (at most the
+    // five batched micro sizes, so the classes may be rebuilt afterwards)
+    const size_t n_counters = (size_t)n_macro * 5;
+    if (n_counters > g->counters_n) {
         if (g->counters) { cudaStreamSynchronize(g->stream); cudaFree(g->counters); }
-        PD_CUDA(g, cudaMalloc(&g->counters, sizeof(int) * n_macro));
-        g->counters_n = n_macro;
+        PD_CUDA(g, cudaMalloc(&g->counters, sizeof(int) * n_counters));
+        g->counters_n = n_counters;
         for (auto& kv : g->gcache) { cudaGraphExecDestroy(kv.second.exec); cudaGraphDestroy(kv.second.graph); }
         g->gcache.clear();
     }
@@ -621,31 +638,38 @@ pd_status batch_time_tables(pd_grid* g, double t0, int n_macro, const std::vecto
     return PD_OK;
 }
 
-int batch_grid(const pd_grid* g, int block)
+int batch_grid(const pd_grid* g, int block, int M)
 {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
-    int per = batch_blocks_per_sm(g->inst[0].d.prec, batch_tsrc(g), block);
+    int per = batch_blocks_per_sm(g->inst[0].d.prec, batch_tsrc(g), M, block);
     return std::max(1, per) * nsm;
 }
 
+// n_macro macro steps; every step launches one kernel per micro-size class
+// (each sized to fill the device, its warps pulling that class's items)
 pd_status enqueue_batch(pd_grid* g, double* U, int n_macro, cudaStream_t st, int& n_launch, bool tables)
 {
-    PD_CUDA(g, cudaMemsetAsync(g->counters, 0, sizeof(int) * n_macro, st));
+    const int ncls = (int)g->cls_m.size();
+    PD_CUDA(g, cudaMemsetAsync(g->counters, 0, sizeof(int) * (size_t)n_macro * ncls, st));
     int block = g->bt_block;
-    int grid = batch_grid(g, block);
+    std::vector<int> grid(ncls);
+    for (int c = 0; c < ncls; ++c) grid[c] = batch_grid(g, block, g->cls_m[c]);
     for (int t = 0; t < n_macro; ++t) {
-        BatchArgs a;
-        a.insts = g->insts_dev; a.items = g->items_dev; a.n_items = g->n_items;
-        a.counter = g->counters + t;
-        a.Ubase = U; a.Sbase = g->U_scratch; a.parity = t & 1;
-        a.dtm = g->dtm_dev;
-        a.tab = tables ? g->tab : nullptr;
-        a.tab_off = tables ? g->tab_off_dev : nullptr;
-        a.step = t;
-        cudaError_t e = launch_batch(g->inst[0].d.prec, batch_tsrc(g), a, block, grid, st);
-        if (e != cudaSuccess) return cuda_fail(g, e, "batched step");
-        n_launch += 1;
+        for (int c = 0; c < ncls; ++c) {
+            if (g->cls_n[c] == 0) continue;
+            BatchArgs a;
+            a.insts = g->insts_dev; a.items = g->items_dev + g->cls_beg[c]; a.n_items = g->cls_n[c];
+            a.counter = g->counters + (size_t)t * ncls + c;
+            a.Ubase = U; a.Sbase = g->U_scratch; a.parity = t & 1;
+            a.dtm = g->dtm_dev;
+            a.tab = tables ? g->tab : nullptr;
+            a.tab_off = tables ? g->tab_off_dev : nullptr;
+            a.step = t;
+            cudaError_t e = launch_batch(g->inst[0].d.prec, batch_tsrc(g), g->cls_m[c], a, block, grid[c], st);
+            if (e != cudaSuccess) return cuda_fail(g, e, "batched step");
+            n_launch += 1;
+        }
     }
     if (n_macro & 1) {
         cudaError_t e = cudaMemcpyAsync(U, g->U_scratch, sizeof(double) * g->n_macro_total, cudaMemcpyDeviceToDevice, st);

@@ -1,15 +1,31 @@
 // Batched macro step over many independent instances of uneven sizes.
 //
-// One launch per macro step covers every instance of the grid.  The work is a
-// list of items (a patch group = up to 32 / m patches of one patch row of one
-// instance, or a chunk of 32 boundary nodes), sorted by cost on the host; the
-// warps of a persistent-size grid pull items from a device counter (one atomic
-// per item), so instances of different micro sizes and macro grids balance
-// across the GPU.  A patch group runs the whole macro step in registers: lift,
-// K forward-Euler micro steps, trapezoid restriction, projective update.  The
-// transformed coefficients come from the instance's 1-D metric tables (constant
-// K, v, f on separable or polar maps) or from its per-point records, and the
-// stencil weights and closed-form forcing are formed on the fly.
+// Every macro step launches one kernel per micro size m over the instances
+// with that size.  The work is a list of items (a patch group = up to 32 / m
+// patches of one patch row of one instance, or a chunk of 32 boundary nodes);
+// the warps of a persistent-size grid pull items from a device counter (one
+// atomic per item), so instances of different macro grids balance across the
+// GPU.  A patch group runs the whole macro step of eq. (Time_Derivative) and
+// eq. (Extrapolation): lift, K forward-Euler micro steps, trapezoid
+// restriction, projective update.
+//
+// Each item runs in four phases:
+//   1. the nine monomial coefficients of each patch's interpolant from the
+//      FP64 macro field (FP64 stencil differences), staged in shared memory;
+//   2. the burst record of every micro point of the group -- the six
+//      dt-scaled stencil weights with the mirror ghosts of the departure folded
+//      in, the forcing dt r of the lifted field (burst_forcing) and dt G --
+//      computed by all 32 lanes over the group's points in a rolled loop and
+//      written to shared memory.  The transformed coefficients come from the
+//      instance's 1-D metric tables (constant K, v, f on separable or polar
+//      maps) or from its per-point records;
+//   3. the K micro steps with lane a of patch q holding micro column a in
+//      registers (records loaded from shared memory once);
+//   4. the trapezoid sum (FP32 column sums and a segmented shuffle tree) and
+//      the FP64 increment dt_macro / tau * dU.
+// Staging the records keeps the register footprint of the per-point set-up out
+// of the burst, so each micro size runs at the occupancy its burst allows, and
+// spreads the set-up of the larger sizes over lanes the burst leaves idle.
 #include "pd_device.cuh"
 
 #include <math.h>
@@ -18,10 +34,118 @@ namespace pd {
 
 namespace {
 
-template <int M, bool TSRC, typename real>
-__device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it, const BatchArgs& A, int lane)
+// Shared-memory stage of one warp: per patch the FP64 values c20, c02, U(0,0)
+// (4 doubles, one pad) and the nine interpolant coefficients in the working
+// precision (12, three pads); per micro point two 4-vectors of the record:
+// plane 0 = (cE, cW, cN, cS), plane 1 = (cX, cC, dt r, dt G), both in point
+// order ((q M + b) M + a) so that lanes of consecutive columns read
+// consecutive 16-byte entries; per patch edge point the weights its ghost
+// terms need.
+template <int M, typename real>
+struct WarpStage {
+    static constexpr int P = 32 / M;
+    static constexpr int NPT = P * M * M;
+    static constexpr size_t fp64_off = 0;
+    static constexpr size_t cv_off = fp64_off + (size_t)P * 4 * sizeof(double);
+    static constexpr size_t rec0_off = cv_off + (size_t)P * 12 * sizeof(real);
+    static constexpr size_t rec1_off = rec0_off + (size_t)NPT * 4 * sizeof(real);
+    // per patch, side (W, E, S, N) and position along it: the dt-scaled stencil
+    // weight toward the ghost and the cross weight, before the mirror folding
+    static constexpr size_t side_off = rec1_off + (size_t)NPT * 4 * sizeof(real);
+    // a record of zeros (8 values) for the lanes that hold no micro column
+    static constexpr size_t zero_off = side_off + (size_t)P * 4 * M * 2 * sizeof(real);
+    static constexpr size_t bytes = zero_off + 8 * sizeof(real);
+    static_assert(cv_off % 16 == 0 && rec0_off % 16 == 0 && rec1_off % 16 == 0 && side_off % 16 == 0 &&
+                  zero_off % 16 == 0, "16-byte aligned planes");
+};
+
+template <typename real>
+__device__ __forceinline__ void store_vec4_shared(real* p, real x, real y, real z, real w)
 {
-    const int P = I.ppw;                      // patches per warp chosen for this instance
+    if constexpr (sizeof(real) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(x, y, z, w);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(x, y);
+        reinterpret_cast<double2*>(p)[1] = make_double2(z, w);
+    }
+}
+
+// Slot k (0..8) of the 3x3 stencil around node (i, j) as in stencil_slot, with
+// the three stencil points and weights formed by selects instead of a switch,
+// so lanes forming different slots do not diverge: v = wB U_B + (U_A + sC U_C).
+__device__ __forceinline__ double stencil_slot_sel(const InstDev& I, const double* __restrict__ Uc, int i, int j,
+                                                   int k)
+{
+    const bool x2 = k < 3;                    // second xi-differences at eta offsets -1, 0, 1
+    const bool x1 = (k >= 3) && (k < 6);      // first xi-differences at eta offsets -1, 0, 1
+    const int eo = x2 ? k - 1 : (x1 ? k - 4 : 0);
+    const int ia = x2 ? -1 : (x1 ? 1 : 0);
+    const int ja = (x2 || x1) ? eo : (k == 6 ? 1 : (k == 7 ? -1 : 0));
+    const int ic = -ia;
+    const int jc = (x2 || x1) ? eo : -ja;
+    const int jb = x2 ? eo : 0;
+    const double wB = (x2 || k == 7) ? -2.0 : 0.0;
+    const double sC = (x1 || k == 6) ? -1.0 : (k == 8 ? 0.0 : 1.0);
+    const double A = __ldg(Uc + (long long)(j + ja) * I.nxp + wrap_col(I, i + ia));
+    const double B = __ldg(Uc + (long long)(j + jb) * I.nxp + i);
+    const double C = __ldg(Uc + (long long)(j + jc) * I.nxp + wrap_col(I, i + ic));
+    return fma(wB, B, fma(sC, C, A));
+}
+
+// Phase 1: slot s of the 3x3 stencil (one FP64 difference) by lane qbase + s % M
+// in register s / M, the coefficient k combined from three slots (two fma, one
+// multiply) by lane qbase + k % M, then written to the patch's shared entry.
+template <int M, typename real>
+__device__ __forceinline__ void stage_coeffs(const InstDev& I, const double* __restrict__ Uc, int i, int j, int a,
+                                             int qbase, bool writer, real* cvq, double* dq)
+{
+    constexpr int NC = (9 + M - 1) / M;
+    double x1[NC];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) x1[r] = stencil_slot_sel(I, Uc, i, j, min(a + r * M, 8));
+    auto gather = [&](int s) -> double {
+        const int ln = (qbase + s % M) & 31;
+        double v = __shfl_sync(kFull, x1[0], ln);
+#pragma unroll
+        for (int rr = 1; rr < NC; ++rr) {
+            const double w = __shfl_sync(kFull, x1[rr], ln);
+            if (s / M == rr) v = w;
+        }
+        return v;
+    };
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+        const int k = min(a + r * M, 8);
+        const double P = gather(I.c2slot[k][0]), Q = gather(I.c2slot[k][1]), R = gather(I.c2slot[k][2]);
+        const double ck = fma(I.c2w[k][1], R, fma(I.c2w[k][0], Q, P)) * I.c2w[k][2];
+        if (writer && a + r * M < 9) {
+            cvq[k] = (real)ck;
+            if (k == 3) dq[0] = ck;
+            if (k == 5) dq[1] = ck;
+            if (k == 8) dq[2] = x1[r];     // slot 8 is U(0, 0)
+        }
+    }
+}
+
+// d/dxi and d/deta of (P - u0) at an edge, the parts of the Neumann data of
+// eq. (edge) that the quadratic lift does not carry (see edge_gap_xi/_eta)
+template <typename real>
+__device__ __forceinline__ real gap_xi(real c21, real c12, real c22, real s, real t)
+{
+    return t * (real(2) * c21 * s + c12 * t + real(2) * c22 * s * t);
+}
+template <typename real>
+__device__ __forceinline__ real gap_eta(real c21, real c12, real c22, real s, real t)
+{
+    return s * (c21 * s + real(2) * c12 * t + real(2) * c22 * s * t);
+}
+
+template <int M, bool TSRC, typename real>
+__device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it, const BatchArgs& A, int lane,
+                                           unsigned char* stage)
+{
+    using S = WarpStage<M, real>;
+    const int P = I.ppw;                      // patches per warp chosen for this instance (<= 32 / M)
     const int jr = it.jr;
     const int ic0 = it.wc * P;
     const int q = lane / M;
@@ -30,56 +154,161 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     const bool active = (q < P) && (ic < I.ncols);
     const int icl = active ? ic : (I.ncols - 1);
     const int i = I.i0 + icl, j = 1 + jr;
-    const int qbase = (q < P ? q : P - 1) * M;
+    const int qc = q < P ? q : P - 1;
+    const int qbase = qc * M;
+
+    double* fp64_s = reinterpret_cast<double*>(stage + S::fp64_off);
+    real* cv_s = reinterpret_cast<real*>(stage + S::cv_off);
+    real* rec0 = reinterpret_cast<real*>(stage + S::rec0_off);
+    real* rec1 = reinterpret_cast<real*>(stage + S::rec1_off);
 
     const double* Uc = (A.parity ? A.Sbase : A.Ubase) + I.u_off;
     double* Un = (A.parity ? A.Ubase : A.Sbase) + I.u_off;
 
-    real cv[9];
-    double c20, c02, u00;
-    macro_coeffs<M, real, false>(I, Uc, i, j, a, qbase, I.lw, I.c2slot, I.c2w, cv, c20, c02, u00);
-    double bias = 0.0;
-    if (I.restrict_mode == PD_RESTRICT_MACRO) bias = (I.dx * I.dx * c20 + I.dy * I.dy * c02) * (1.0 / 6.0);
-    Poly<real> c = { cv[0], cv[1], cv[2], cv[3], cv[4], cv[5], cv[6], cv[7], cv[8] };
+    // ---- phase 1: interpolant coefficients (FP64 stencil) -> shared
+    __syncwarp();                             // the previous item's readers are done
+    stage_coeffs<M, real>(I, Uc, i, j, a, qbase, q < P, cv_s + qc * 12, fp64_s + qc * 4);
+    __syncwarp();
 
-    const double* trow = (A.tab && (TSRC || I.sol != PD_SOL_NONE)) ? A.tab + A.tab_off[it.inst] + (long long)A.step * (I.K + kTabExtra) : nullptr;
-    const real sT = (TSRC && trow) ? (real)trow[I.K] : real(0);
+    // ---- phase 2: burst records of the group's points, all lanes.  (a) every
+    // point: weights and the forcing of the lift without ghost terms; (b) one
+    // pass per patch side (uniform across the warp): the ghost-point terms of
+    // the points on that side added to their forcing.
+    const double* trow = (A.tab && (TSRC || I.sol != PD_SOL_NONE))
+                             ? A.tab + A.tab_off[it.inst] + (long long)A.step * (I.K + kTabExtra) : nullptr;
+    {
+        const real sT = (TSRC && trow) ? (real)trow[I.K] : real(0);
+        const RealConsts<real> kc = real_consts<real>(I);
+        real hx, hy;
+        if constexpr (sizeof(real) == 4) { hx = I.kf[13]; hy = I.kf[14]; }
+        else { hx = I.hx; hy = I.hy; }
+        const real dx = kc.dx, dy = kc.dy;
+        const real s0 = real(-0.5) * hx, t0 = real(-0.5) * hy;
+        const real dt = sizeof(real) == 4 ? (real)I.kf[15] : (real)I.dt;
+        const real* rec = static_cast<const real*>(I.rec);
+        const long long rowstride = (long long)I.ncols * M;
+        real* side = reinterpret_cast<real*>(stage + S::side_off);
+        const int npt = P * M * M;
+#pragma unroll 1
+        for (int pt = lane; pt < npt; pt += 32) {
+            const int pq = pt / (M * M);
+            const int rem = pt - pq * (M * M);
+            const int pb = rem / M;
+            const int pa = rem - pb * M;
+            const int pic = ic0 + pq;
+            real e = real(0), ww = real(0), n = real(0), sw = real(0), x = real(0), cc = real(0), R = real(0),
+                 Gd = real(0);
+            real dW = real(0), dE = real(0), dS = real(0), dN = real(0), dX = real(0);
+            if (pic < I.ncols) {
+                const real* c9 = cv_s + pq * 12;
+                real C0, c10, c01, c20, c11, c02, c21, c12;
+                load_vec4_shared<real>(c9, C0, c10, c01, c20);
+                load_vec4_shared<real>(c9 + 4, c11, c02, c21, c12);
+                real co[6], G = real(0);
+                if (I.coef_mode != COEF_RECORDS) {
+                    table_coeffs_k<real>(I, kc, pic, pa, jr, pb, co);
+                } else {
+                    const real* pr = rec + ((long long)jr * M * rowstride + (long long)pb * rowstride +
+                                            (long long)pic * M + pa) * 8;
+                    for (int k = 0; k < 6; ++k) co[k] = pr[k];
+                    G = pr[6];
+                }
+                const PointW<real> pw = point_weights_k<real>(I, kc, co[0], co[1], co[2], co[3], co[4], co[5]);
+                // forcing of the quadratic lift (burst_forcing without its ghost terms)
+                const real sa = s0 + real(pa) * dx, tb = t0 + real(pb) * dy;
+                const real u0 = C0 + sa * (c10 + sa * c20 + tb * c11) + tb * (c01 + tb * c02);
+                const real ux = c10 + real(2) * c20 * (sa + pw.ox) + c11 * tb;
+                const real uy = c01 + real(2) * c02 * (tb + pw.oy) + c11 * sa;
+                const real r = real(2) * c20 * co[0] + c11 * co[1] + real(2) * c02 * co[2] - co[3] * ux - co[4] * uy +
+                               co[5] * u0 + sT * G;
+                e = dt * pw.wE; ww = dt * pw.wW; n = dt * pw.wN; sw = dt * pw.wS; x = dt * pw.wX;
+                dW = ww; dE = e; dS = sw; dN = n; dX = x;
+                cc = real(1) + dt * pw.wC;
+                if (pa == 0) { e += ww; ww = real(0); }
+                if (pa == M - 1) { ww += e; e = real(0); }
+                if (pb == 0) { n += sw; sw = real(0); }
+                if (pb == M - 1) { sw += n; n = real(0); }
+                if (pa == 0 || pa == M - 1 || pb == 0 || pb == M - 1) x = real(0);
+                R = dt * r;
+                Gd = dt * G;
+            }
+            store_vec4_shared<real>(rec0 + (size_t)pt * 4, e, ww, n, sw);
+            store_vec4_shared<real>(rec1 + (size_t)pt * 4, x, cc, R, Gd);
+            real* sq = side + (size_t)pq * 8 * M;
+            if (pa == 0) { sq[2 * pb] = dW; sq[2 * pb + 1] = dX; }
+            if (pa == M - 1) { sq[2 * (M + pb)] = dE; sq[2 * (M + pb) + 1] = dX; }
+            if (pb == 0) { sq[2 * (2 * M + pa)] = dS; sq[2 * (2 * M + pa) + 1] = dX; }
+            if (pb == M - 1) { sq[2 * (3 * M + pa)] = dN; sq[2 * (3 * M + pa) + 1] = dX; }
+        }
+        __syncwarp();
+        // ghost terms: a ghost neighbour (a', b') outside the patch adds
+        // weight * (ghost value - lift there) (ghost_offset); the diagonal
+        // ghosts of the cross term are taken by the W/E pass when a' is outside,
+        // else by the S/N pass.
+        const real sL = s0, sR = -s0, tB = t0, tT = -t0;
+        const real s1 = s0 + dx, sM2 = -s0 - dx;              // s(1), s(M - 2)
+#pragma unroll 1
+        for (int sd = 0; sd < 4; ++sd) {
+#pragma unroll 1
+            for (int e = lane; e < P * M; e += 32) {
+                const int pq = e / M;
+                const int p = e - pq * M;
+                if (ic0 + pq >= I.ncols) continue;
+                const real* c9 = cv_s + pq * 12;
+                const real c21 = c9[6], c12 = c9[7], c22 = c9[8];
+                const real* sq = side + (size_t)pq * 8 * M + 2 * (sd * M + p);
+                const real wg = sq[0], wx = sq[1];
+                const real lo = p >= 1 ? real(1) : real(0), hi = p <= M - 2 ? real(1) : real(0);
+                real g;
+                int pt;
+                if (sd < 2) {
+                    // W (a = 0) / E (a = M - 1): ghosts at a' = -1 / M, rows b - 1, b, b + 1
+                    const real sg = sd == 0 ? real(-1) : real(1);
+                    const real se = sd == 0 ? sL : sR;
+                    const real sin_ = sd == 0 ? s1 : sM2;          // s(a_in) for the eta part of a corner ghost
+                    const real tb = t0 + real(p) * dy;
+                    const real gm = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb);
+                    const real gdn = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb - dy) -
+                                     (real(1) - lo) * real(2) * dy * gap_eta(c21, c12, c22, sin_, tB);
+                    const real gup = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb + dy) +
+                                     (real(1) - hi) * real(2) * dy * gap_eta(c21, c12, c22, sin_, tT);
+                    // W: +wX go(-1, b-1) - wX go(-1, b+1); E: +wX go(M, b+1) - wX go(M, b-1)
+                    g = wg * gm + sg * wx * (gup - gdn);
+                    pt = (pq * M + p) * M + (sd == 0 ? 0 : M - 1);
+                } else {
+                    // S (b = 0) / N (b = M - 1): ghosts at b' = -1 / M, columns a - 1, a, a + 1 inside the patch
+                    const real sg = sd == 2 ? real(-1) : real(1);
+                    const real te = sd == 2 ? tB : tT;
+                    const real sa = s0 + real(p) * dx;
+                    const real gm = sg * real(2) * dy * gap_eta(c21, c12, c22, sa, te);
+                    const real gl = sg * real(2) * dy * gap_eta(c21, c12, c22, sa - dx, te);
+                    const real gr = sg * real(2) * dy * gap_eta(c21, c12, c22, sa + dx, te);
+                    // S: +wX go(a-1, -1) - wX go(a+1, -1); N: +wX go(a+1, M) - wX go(a-1, M)
+                    g = wg * gm + sg * wx * (hi * gr - lo * gl);
+                    pt = (pq * M + (sd == 2 ? 0 : M - 1)) * M + p;
+                }
+                rec1[(size_t)pt * 4 + 2] += g;
+            }
+            __syncwarp();
+        }
+    }
 
-    const RealConsts<real> kc = real_consts<real>(I);
-    PatchGeo<real> g;
-    if constexpr (sizeof(real) == 4) { g.hx = I.kf[13]; g.hy = I.kf[14]; }
-    else { g.hx = I.hx; g.hy = I.hy; }
-    g.dx = kc.dx; g.dy = kc.dy;
-    g.nx = M - 1; g.ny = M - 1;
-    const real dt = sizeof(real) == 4 ? (real)I.kf[15] : (real)I.dt;
-    const real* rec = static_cast<const real*>(I.rec);
-    const long long rowstride = (long long)I.ncols * M;
-    const long long base = (long long)jr * M * rowstride + (long long)icl * M + a;
-
+    // ---- phase 3: K micro steps, lane (q, a) holding micro column a of patch q
+    // a patch past the end of its row has zero records; a lane past the last
+    // patch of the group reads the zero record for every row
     real w[M], Rr[M], cE[M], cW[M], cN[M], cS[M], cC[M], cX[M], Gs[M];
+    const real* z = reinterpret_cast<const real*>(stage + S::zero_off);
+    const real* r0p = q < P ? rec0 + ((size_t)(qc * M) * M + a) * 4 : z;
+    const real* r1p = q < P ? rec1 + ((size_t)(qc * M) * M + a) * 4 : z + 4;
+    const int rs = q < P ? M * 4 : 0;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
-        real co[6], G = real(0);
-        if (I.coef_mode != COEF_RECORDS) {
-            table_coeffs_k<real>(I, kc, icl, a, jr, b, co);
-        } else {
-            const real* pr = rec + (base + b * rowstride) * 8;
-            for (int k = 0; k < 6; ++k) co[k] = pr[k];
-            G = pr[6];
-        }
-        PointW<real> pw = point_weights_k<real>(I, kc, co[0], co[1], co[2], co[3], co[4], co[5]);
-        real r = burst_forcing<real>(c, g, a, b, co[0], co[1], co[2], co[3], co[4], co[5], G, sT, pw);
-        real e = dt * pw.wE, ww = dt * pw.wW, n = dt * pw.wN, s = dt * pw.wS, x = dt * pw.wX;
-        real cc = real(1) + dt * pw.wC;
-        if (a == 0) { e += ww; ww = real(0); }
-        if (a == M - 1) { ww += e; e = real(0); }
-        if (b == 0) { n += s; s = real(0); }
-        if (b == M - 1) { s += n; n = real(0); }
-        if (a == 0 || a == M - 1 || b == 0 || b == M - 1) x = real(0);
-        if (!active) { e = ww = n = s = x = cc = r = G = real(0); }
+        real e, ww, n, s, x, cc, R, Gd;
+        load_vec4_shared<real>(r0p + b * rs, e, ww, n, s);
+        load_vec4_shared<real>(r1p + b * rs, x, cc, R, Gd);
         cE[b] = e; cW[b] = ww; cN[b] = n; cS[b] = s; cX[b] = x; cC[b] = cc;
-        Rr[b] = dt * r;
-        Gs[b] = dt * G;
+        Rr[b] = R;
+        Gs[b] = Gd;
         w[b] = real(0);
     }
 
@@ -87,6 +316,7 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     if (TSRC && trow) burst_steps<M, true, true, real>(w, cE, cW, cN, cS, cC, cX, Gs, Rr, trow, I.K);
     else burst_steps<M, true, false, real>(w, cE, cW, cN, cS, cC, cX, Gs, Rr, trow, I.K);
 
+    // ---- phase 4: restriction and projective update
     real col = real(0.5) * (w[0] + w[M - 1]);
 #pragma unroll
     for (int b = 1; b < M - 1; ++b) col += w[b];
@@ -98,10 +328,13 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
         if (a + off < M) col += o;
     }
     if (active && a == 0) {
+        const double* dq = fp64_s + qc * 4;
+        double bias = 0.0;
+        if (I.restrict_mode == PD_RESTRICT_MACRO) bias = (I.dx * I.dx * dq[0] + I.dy * I.dy * dq[1]) * (1.0 / 6.0);
         double bias_scale = A.dtm[it.inst] * I.inv_tau;
         double inc = fma((double)col, bias_scale * I.inv_nn, bias * bias_scale);
         if (!isfinite(inc)) atomicOr(I.err, ERR_NONFINITE);
-        Un[(long long)j * I.nxp + i] = u00 + inc;
+        Un[(long long)j * I.nxp + i] = dq[2] + inc;
     }
 }
 
@@ -120,11 +353,25 @@ __device__ __forceinline__ void boundary_item(const InstDev& I, const BatchItem&
     Un[(long long)ij.y * I.nxp + ij.x] = v;
 }
 
-// at most 128 threads per block and 170 registers per thread: three blocks per SM
-template <bool TSRC, typename real>
-__global__ void __launch_bounds__(128, 3) batch_kernel(const BatchArgs A)
+// Resident blocks per SM requested from the compiler for each micro size: the
+// burst keeps about 9 M values per lane (departure, forcing, six weights, source
+// factor), so the small micro sizes run at a higher occupancy than the largest.
+template <int M, typename real>
+struct BatchBounds {
+    static constexpr int min_blocks = sizeof(real) == 4 ? (M <= 5 ? 8 : M <= 7 ? 6 : M <= 9 ? 5 : 4)
+                                                        : (M <= 5 ? 4 : M <= 7 ? 3 : 2);
+};
+
+// One micro size per kernel: the items of this launch are the patch groups of
+// the instances with m = M and those instances' boundary chunks.
+template <int M, bool TSRC, typename real>
+__global__ void __launch_bounds__(128, BatchBounds<M, real>::min_blocks) batch_kernel(const BatchArgs A)
 {
+    extern __shared__ __align__(16) unsigned char batch_smem[];
+    unsigned char* stage = batch_smem + (size_t)(threadIdx.x >> 5) * WarpStage<M, real>::bytes;
     const int lane = threadIdx.x & 31;
+    if (lane < 8) reinterpret_cast<real*>(stage + WarpStage<M, real>::zero_off)[lane] = real(0);
+    __syncwarp();
     for (;;) {
         int idx = 0;
         if (lane == 0) idx = atomicAdd(A.counter, 1);
@@ -133,43 +380,78 @@ __global__ void __launch_bounds__(128, 3) batch_kernel(const BatchArgs A)
         const BatchItem it = A.items[idx];
         const InstDev& I = A.insts[it.inst];
         if (it.kind == 1) { boundary_item(I, it, A, lane); continue; }
-        switch (I.mx) {
-        case 3: patch_item<3, TSRC, real>(I, it, A, lane); break;
-        case 5: patch_item<5, TSRC, real>(I, it, A, lane); break;
-        case 7: patch_item<7, TSRC, real>(I, it, A, lane); break;
-        case 9: patch_item<9, TSRC, real>(I, it, A, lane); break;
-        case 11: patch_item<11, TSRC, real>(I, it, A, lane); break;
-        default: break;
-        }
+        patch_item<M, TSRC, real>(I, it, A, lane, stage);
+    }
+}
+
+template <int M, bool TSRC, typename real>
+size_t smem_bytes(int block)
+{
+    return (size_t)(block / 32) * WarpStage<M, real>::bytes;
+}
+
+template <int M, bool TSRC, typename real>
+cudaError_t launch_m(const BatchArgs& a, int block, int grid, cudaStream_t st)
+{
+    const size_t smem = smem_bytes<M, TSRC, real>(block);
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    batch_kernel<M, TSRC, real><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int M, bool TSRC, typename real>
+int occupancy_m(int block)
+{
+    const size_t smem = smem_bytes<M, TSRC, real>(block);
+    if (cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<M, TSRC, real>, block, smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <bool TSRC, typename real>
+cudaError_t launch_tr(int M, const BatchArgs& a, int block, int grid, cudaStream_t st)
+{
+    switch (M) {
+    case 3: return launch_m<3, TSRC, real>(a, block, grid, st);
+    case 5: return launch_m<5, TSRC, real>(a, block, grid, st);
+    case 7: return launch_m<7, TSRC, real>(a, block, grid, st);
+    case 9: return launch_m<9, TSRC, real>(a, block, grid, st);
+    case 11: return launch_m<11, TSRC, real>(a, block, grid, st);
+    default: return cudaErrorInvalidValue;
     }
 }
 
 template <bool TSRC, typename real>
-int occupancy(int block)
+int occupancy_tr(int M, int block)
 {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<TSRC, real>, block, 0) != cudaSuccess) return 0;
-    return nb;
+    switch (M) {
+    case 3: return occupancy_m<3, TSRC, real>(block);
+    case 5: return occupancy_m<5, TSRC, real>(block);
+    case 7: return occupancy_m<7, TSRC, real>(block);
+    case 9: return occupancy_m<9, TSRC, real>(block);
+    case 11: return occupancy_m<11, TSRC, real>(block);
+    default: return 0;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_batch(int prec, bool tsrc, const BatchArgs& a, int block, int grid, cudaStream_t st)
+cudaError_t launch_batch(int prec, bool tsrc, int M, const BatchArgs& a, int block, int grid, cudaStream_t st)
 {
-    if (prec == PD_FP32) {
-        if (tsrc) batch_kernel<true, float><<<grid, block, 0, st>>>(a);
-        else batch_kernel<false, float><<<grid, block, 0, st>>>(a);
-    } else {
-        if (tsrc) batch_kernel<true, double><<<grid, block, 0, st>>>(a);
-        else batch_kernel<false, double><<<grid, block, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    if (prec == PD_FP32) return tsrc ? launch_tr<true, float>(M, a, block, grid, st) : launch_tr<false, float>(M, a, block, grid, st);
+    return tsrc ? launch_tr<true, double>(M, a, block, grid, st) : launch_tr<false, double>(M, a, block, grid, st);
 }
 
-int batch_blocks_per_sm(int prec, bool tsrc, int block)
+int batch_blocks_per_sm(int prec, bool tsrc, int M, int block)
 {
-    if (prec == PD_FP32) return tsrc ? occupancy<true, float>(block) : occupancy<false, float>(block);
-    return tsrc ? occupancy<true, double>(block) : occupancy<false, double>(block);
+    if (prec == PD_FP32) return tsrc ? occupancy_tr<true, float>(M, block) : occupancy_tr<false, float>(M, block);
+    return tsrc ? occupancy_tr<true, double>(M, block) : occupancy_tr<false, double>(M, block);
 }
 
 }  // namespace pd

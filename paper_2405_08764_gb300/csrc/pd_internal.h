@@ -522,8 +522,9 @@ struct BatchArgs {
     const long long* tab_off;  // per-instance offset of the table of this pd_step
     int step;                  // macro step index within the pd_step call
 };
-cudaError_t launch_batch(int prec, bool tsrc, const BatchArgs& a, int block, int grid, cudaStream_t st);
-int batch_blocks_per_sm(int prec, bool tsrc, int block);
+// one launch covers the items of the instances with micro size M (M x M patches)
+cudaError_t launch_batch(int prec, bool tsrc, int M, const BatchArgs& a, int block, int grid, cudaStream_t st);
+int batch_blocks_per_sm(int prec, bool tsrc, int M, int block);
 cudaError_t launch_batch_time_tables(const InstDev* insts, int n_inst, const double* dtm, double t0, int n_macro,
                                      const long long* tab_off, double* tab, long long total, cudaStream_t st);
 int persist_item_warps(const InstDev& I);
