@@ -111,6 +111,7 @@ struct pd_grid {
     std::vector<int> cls_m, cls_beg, cls_n;
     bool batch_dirty = true;
     double* dtm_dev = nullptr;
+    double2* scale_dev = nullptr;    // per instance (dtm inv_tau inv_nn, dtm inv_tau)
     std::vector<double> dtm_host;
     long long* tab_off_dev = nullptr;
     int* counters = nullptr;
@@ -531,6 +532,7 @@ pd_status prepare_batch(pd_grid* g)
 {
     if (!g->batch_dirty) return PD_OK;
     PD_CUDA(g, cudaStreamSynchronize(g->stream));   // no kernel may still read the old tables
+    g->dtm_host.clear();                            // tau may have changed: rebuild the update scales
     size_t n = g->inst.size();
     std::vector<InstDev> host(n);
     std::vector<BatchItem> items;
@@ -593,9 +595,16 @@ pd_status batch_buffers(pd_grid* g, int n_macro, const std::vector<double>& dtm)
 {
     size_t n = g->inst.size();
     if (!g->dtm_dev) PD_CUDA(g, cudaMalloc(&g->dtm_dev, sizeof(double) * n));
+    if (!g->scale_dev) PD_CUDA(g, cudaMalloc(&g->scale_dev, sizeof(double2) * n));
     if (g->dtm_host != dtm) {
+        std::vector<double2> sc(n);
+        for (size_t k = 0; k < n; ++k) {
+            const double bs = dtm[k] * g->inst[k].I.inv_tau;
+            sc[k] = make_double2(bs * g->inst[k].I.inv_nn, bs);
+        }
         PD_CUDA(g, cudaStreamSynchronize(g->stream));
         PD_CUDA(g, cudaMemcpy(g->dtm_dev, dtm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        PD_CUDA(g, cudaMemcpy(g->scale_dev, sc.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
         g->dtm_host = dtm;
     }
     // one work-queue counter per macro step and micro-size class (at most the
@@ -663,6 +672,7 @@ pd_status enqueue_batch(pd_grid* g, double* U, int n_macro, cudaStream_t st, int
             a.counter = g->counters + (size_t)t * ncls + c;
             a.Ubase = U; a.Sbase = g->U_scratch; a.parity = t & 1;
             a.dtm = g->dtm_dev;
+            a.scale = g->scale_dev;
             a.tab = tables ? g->tab : nullptr;
             a.tab_off = tables ? g->tab_off_dev : nullptr;
             a.step = t;
@@ -906,7 +916,7 @@ pd_status pd_destroy_grid(pd_grid* g)
     cudaFree(g->S2); cudaFree(g->dUa); cudaFree(g->dUb);
     cudaFree(g->Dq); cudaFree(g->dRa); cudaFree(g->dRb); cudaFree(g->dRz);
     cudaFree(g->state); cudaFree(g->dU); cudaFree(g->flags);
-    cudaFree(g->insts_dev); cudaFree(g->items_dev); cudaFree(g->dtm_dev); cudaFree(g->tab_off_dev); cudaFree(g->counters);
+    cudaFree(g->insts_dev); cudaFree(g->items_dev); cudaFree(g->dtm_dev); cudaFree(g->scale_dev); cudaFree(g->tab_off_dev); cudaFree(g->counters);
     if (g->cap) cudaStreamDestroy(g->cap);
     delete g;
     return PD_OK;

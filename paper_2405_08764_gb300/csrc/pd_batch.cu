@@ -52,11 +52,13 @@ struct WarpStage {
     // per patch, side (W, E, S, N) and position along it: the dt-scaled stencil
     // weight toward the ghost and the cross weight, before the mirror folding
     static constexpr size_t side_off = rec1_off + (size_t)NPT * 4 * sizeof(real);
+    // separable maps: per patch and micro row the row factors of the record (12 values)
+    static constexpr size_t row_off = side_off + (size_t)P * 4 * M * 2 * sizeof(real);
     // a record of zeros (8 values) for the lanes that hold no micro column
-    static constexpr size_t zero_off = side_off + (size_t)P * 4 * M * 2 * sizeof(real);
+    static constexpr size_t zero_off = row_off + (size_t)P * M * 12 * sizeof(real);
     static constexpr size_t bytes = zero_off + 8 * sizeof(real);
     static_assert(cv_off % 16 == 0 && rec0_off % 16 == 0 && rec1_off % 16 == 0 && side_off % 16 == 0 &&
-                  zero_off % 16 == 0, "16-byte aligned planes");
+                  row_off % 16 == 0 && zero_off % 16 == 0, "16-byte aligned planes");
 };
 
 template <typename real>
@@ -177,6 +179,8 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     const double* trow = (A.tab && (TSRC || I.sol != PD_SOL_NONE))
                              ? A.tab + A.tab_off[it.inst] + (long long)A.step * (I.K + kTabExtra) : nullptr;
     {
+        // instance constants in registers for the whole item (read once from
+        // the instance record, never inside the point loops)
         const real sT = (TSRC && trow) ? (real)trow[I.K] : real(0);
         const RealConsts<real> kc = real_consts<real>(I);
         real hx, hy;
@@ -184,61 +188,230 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
         else { hx = I.hx; hy = I.hy; }
         const real dx = kc.dx, dy = kc.dy;
         const real s0 = real(-0.5) * hx, t0 = real(-0.5) * hy;
+        const real hdx = real(0.5) * dx, hdy = real(0.5) * dy;
         const real dt = sizeof(real) == 4 ? (real)I.kf[15] : (real)I.dt;
-        const real* rec = static_cast<const real*>(I.rec);
-        const long long rowstride = (long long)I.ncols * M;
+        const int mode = I.coef_mode;
+        const bool central = I.conv == PD_CONV_CENTRAL;
+        const int nvalid = min(P, I.ncols - ic0);             // patches of the group inside the row
+        const real K11 = kc.K11, K12 = kc.K12, K22 = kc.K22, v1 = kc.v1, v2 = kc.v2, f0 = kc.f0;
+        const real idx = kc.idx, idy = kc.idy, idx2 = kc.idx2, idy2 = kc.idy2, i4dxdy = kc.i4dxdy;
+        // this item's entries of the 1-D tables: columns ic0 .. ic0 + P - 1, row jr
+        const real* colt = mode != COEF_RECORDS ? kc.col + (size_t)ic0 * M * 2 : nullptr;
+        const real* rowt = mode != COEF_RECORDS ? kc.row + (size_t)jr * M * 4 : nullptr;
+        const real* rect = mode == COEF_RECORDS
+                               ? static_cast<const real*>(I.rec) + ((size_t)jr * M * I.ncols + (size_t)ic0) * M * 8
+                               : nullptr;
+        const int recrow = I.ncols * M * 8;                   // one micro row of the patch row, in values
         real* side = reinterpret_cast<real*>(stage + S::side_off);
         const int npt = P * M * M;
-#pragma unroll 1
-        for (int pt = lane; pt < npt; pt += 32) {
-            const int pq = pt / (M * M);
-            const int rem = pt - pq * (M * M);
-            const int pb = rem / M;
-            const int pa = rem - pb * M;
-            const int pic = ic0 + pq;
-            real e = real(0), ww = real(0), n = real(0), sw = real(0), x = real(0), cc = real(0), R = real(0),
-                 Gd = real(0);
-            real dW = real(0), dE = real(0), dS = real(0), dN = real(0), dX = real(0);
-            if (pic < I.ncols) {
-                const real* c9 = cv_s + pq * 12;
-                real C0, c10, c01, c20, c11, c02, c21, c12;
-                load_vec4_shared<real>(c9, C0, c10, c01, c20);
-                load_vec4_shared<real>(c9 + 4, c11, c02, c21, c12);
-                real co[6], G = real(0);
-                if (I.coef_mode != COEF_RECORDS) {
-                    table_coeffs_k<real>(I, kc, pic, pa, jr, pb, co);
+        if (mode == COEF_SEPARABLE) {
+            // Separable map x = X(xi), y = Y(eta) with constant K, v, f: alpha, nu
+            // and the xi-weights depend on the column only, gamma, omega and the
+            // eta-weights on the row only, beta = 2 K12 X'^-1 Y'^-1 is a product,
+            // and the forcing splits as r = X_a + Y_b + c11 Z_ab with
+            //   X_a = 2 c20 alpha - nu (c10 + 2 c20 (s + ox)) + f (c10 s + c20 s^2),
+            //   Y_b = 2 c02 gamma - omega (c01 + 2 c02 (t + oy)) + f (C0 + c01 t + c02 t^2),
+            //   Z_ab = beta - nu t - omega s + f s t.
+            // Row factors per (patch, micro row) first, one lane each:
+            real* rowq = reinterpret_cast<real*>(stage + S::row_off);
+            for (int e = lane; e < P * M; e += 32) {
+                const int pq = e / M;
+                const int pb = e - pq * M;
+                const real* rt = rowt + pb * 4;
+                const real ib = rt[0], ib2 = rt[1];
+                const real ga = K22 * ib * ib;
+                const real om = v2 * ib + K22 * ib2;
+                const real gy = ga * idy2;
+                real wN, wS, wCr, oy;
+                if (central) {
+                    const real ho = real(0.5) * om * idy;
+                    wN = gy - ho; wS = gy + ho; wCr = -real(2) * gy; oy = real(0);
                 } else {
-                    const real* pr = rec + ((long long)jr * M * rowstride + (long long)pb * rowstride +
-                                            (long long)pic * M + pa) * 8;
-                    for (int k = 0; k < 6; ++k) co[k] = pr[k];
-                    G = pr[6];
+                    const real oyv = om * idy;
+                    const bool po = om > real(0);
+                    wS = po ? gy + oyv : gy;
+                    wN = po ? gy : gy - oyv;
+                    wCr = po ? -real(2) * gy - oyv : -real(2) * gy + oyv;
+                    oy = po ? -hdy : hdy;
                 }
-                const PointW<real> pw = point_weights_k<real>(I, kc, co[0], co[1], co[2], co[3], co[4], co[5]);
-                // forcing of the quadratic lift (burst_forcing without its ghost terms)
+                const real nu_ = dt * wN, su = dt * wS;
+                const real nf = pb == 0 ? nu_ + su : (pb == M - 1 ? real(0) : nu_);
+                const real sf = pb == M - 1 ? su + nu_ : (pb == 0 ? real(0) : su);
+                const real crow = real(1) + dt * (wCr + f0);
+                const real tb = t0 + real(pb) * dy;
+                const real* c9 = cv_s + pq * 12;
+                const real C0 = c9[0], c01 = c9[2], c02 = c9[5];
+                const real Yb = real(2) * c02 * ga - om * (c01 + real(2) * c02 * (tb + oy)) +
+                                f0 * (C0 + tb * (c01 + tb * c02));
+                real* o = rowq + e * 12;
+                store_vec4_shared<real>(o, nf, sf, crow, ib);
+                store_vec4_shared<real>(o + 4, tb, om, Yb, nu_);
+                store_vec4_shared<real>(o + 8, su, real(0), real(0), real(0));
+            }
+            __syncwarp();
+            // then each lane (q, a) holding a column walks down its micro rows
+            if (q < nvalid) {
+                const real* ct = colt + (q * M + a) * 2;
+                const real ia = ct[0], ia2 = ct[1];
+                const real al = K11 * ia * ia;
+                const real nu = v1 * ia + K11 * ia2;
+                const real ax = al * idx2;
+                real wE, wW, wCc, ox;
+                if (central) {
+                    const real hn = real(0.5) * nu * idx;
+                    wE = ax - hn; wW = ax + hn; wCc = -real(2) * ax; ox = real(0);
+                } else {
+                    const real nx = nu * idx;
+                    const bool pn = nu > real(0);
+                    wW = pn ? ax + nx : ax;
+                    wE = pn ? ax : ax - nx;
+                    wCc = pn ? -real(2) * ax - nx : -real(2) * ax + nx;
+                    ox = pn ? -hdx : hdx;
+                }
+                const real eu = dt * wE, wu = dt * wW, ccol = dt * wCc;
+                const real ef = a == 0 ? eu + wu : (a == M - 1 ? real(0) : eu);
+                const real wf = a == M - 1 ? wu + eu : (a == 0 ? real(0) : wu);
+                const real b2 = real(2) * K12 * ia;                   // beta / (1 / Y')
+                const real xu = dt * b2 * i4dxdy;                     // unfolded cross weight / (1 / Y')
+                const real xin = (a == 0 || a == M - 1) ? real(0) : xu;
+                const real sa = s0 + real(a) * dx;
+                const real* c9 = cv_s + q * 12;
+                const real c10 = c9[1], c20 = c9[3], c11 = c9[4];
+                const real Xa = real(2) * c20 * al - nu * (c10 + real(2) * c20 * (sa + ox)) + f0 * (sa * (c10 + sa * c20));
+                const real fs = f0 * sa;
+                const real* rq = rowq + q * M * 12;
+                real* sq = side + q * 8 * M;
+#pragma unroll 1
+                for (int b = 0; b < M; ++b) {
+                    real nf, sf, crow, ib, tb, om, Yb, nu_, su, p1, p2, p3;
+                    load_vec4_shared<real>(rq + b * 12, nf, sf, crow, ib);
+                    load_vec4_shared<real>(rq + b * 12 + 4, tb, om, Yb, nu_);
+                    load_vec4_shared<real>(rq + b * 12 + 8, su, p1, p2, p3);
+                    real Z = b2 * ib;
+                    Z = fma(-nu, tb, Z);
+                    Z = fma(-om, sa, Z);
+                    Z = fma(fs, tb, Z);
+                    const real r = (Xa + Yb) + c11 * Z;
+                    const bool redge = b == 0 || b == M - 1;
+                    const real x = redge ? real(0) : xin * ib;
+                    const int pt = (q * M + b) * M + a;
+                    store_vec4_shared<real>(rec0 + pt * 4, ef, wf, nf, sf);
+                    store_vec4_shared<real>(rec1 + pt * 4, x, ccol + crow, dt * r, real(0));
+                    const real xs = xu * ib;                          // unfolded dt * wX at (a, b)
+                    if (a == 0) { sq[2 * b] = wu; sq[2 * b + 1] = xs; }
+                    if (a == M - 1) { sq[2 * (M + b)] = eu; sq[2 * (M + b) + 1] = xs; }
+                    if (b == 0) { sq[2 * (2 * M + a)] = su; sq[2 * (2 * M + a) + 1] = xs; }
+                    if (b == M - 1) { sq[2 * (3 * M + a)] = nu_; sq[2 * (3 * M + a) + 1] = xs; }
+                }
+            } else if (q < P) {
+                // patches past the end of the row: zero records
+#pragma unroll 1
+                for (int b = 0; b < M; ++b) {
+                    const int pt = (q * M + b) * M + a;
+                    store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
+                    store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
+                }
+            }
+        } else {
+            // general point: record of micro point (pa, pb) of patch pq from its
+            // transformed coefficients, written at pt; weights and the forcing of
+            // the quadratic lift as point_weights_k and burst_forcing (without its
+            // ghost terms), the upwind choice by selects
+            auto emit = [&](int pt, int pq, int pa, int pb, real al, real be, real ga, real nu, real om, real ph,
+                            real G) {
+                const real* c9 = cv_s + pq * 12;
+                real C0, c10, c01, c20, c11, c02, c21_, c12_;
+                load_vec4_shared<real>(c9, C0, c10, c01, c20);
+                load_vec4_shared<real>(c9 + 4, c11, c02, c21_, c12_);
+                const real ax = al * idx2, gy = ga * idy2;
+                real wE, wW, wN, wS, ox, oy;
+                real wC = -real(2) * ax - real(2) * gy + ph;
+                const real wX = be * i4dxdy;
+                if (central) {
+                    const real hn = real(0.5) * nu * idx, ho = real(0.5) * om * idy;
+                    wE = ax - hn; wW = ax + hn; wN = gy - ho; wS = gy + ho;
+                    ox = real(0); oy = real(0);
+                } else {
+                    const real nx = nu * idx, oyv = om * idy;
+                    const bool pn = nu > real(0), po = om > real(0);
+                    wW = pn ? ax + nx : ax;
+                    wE = pn ? ax : ax - nx;
+                    wC = pn ? wC - nx : wC + nx;
+                    ox = pn ? -hdx : hdx;
+                    wS = po ? gy + oyv : gy;
+                    wN = po ? gy : gy - oyv;
+                    wC = po ? wC - oyv : wC + oyv;
+                    oy = po ? -hdy : hdy;
+                }
                 const real sa = s0 + real(pa) * dx, tb = t0 + real(pb) * dy;
                 const real u0 = C0 + sa * (c10 + sa * c20 + tb * c11) + tb * (c01 + tb * c02);
-                const real ux = c10 + real(2) * c20 * (sa + pw.ox) + c11 * tb;
-                const real uy = c01 + real(2) * c02 * (tb + pw.oy) + c11 * sa;
-                const real r = real(2) * c20 * co[0] + c11 * co[1] + real(2) * c02 * co[2] - co[3] * ux - co[4] * uy +
-                               co[5] * u0 + sT * G;
-                e = dt * pw.wE; ww = dt * pw.wW; n = dt * pw.wN; sw = dt * pw.wS; x = dt * pw.wX;
-                dW = ww; dE = e; dS = sw; dN = n; dX = x;
-                cc = real(1) + dt * pw.wC;
-                if (pa == 0) { e += ww; ww = real(0); }
-                if (pa == M - 1) { ww += e; e = real(0); }
-                if (pb == 0) { n += sw; sw = real(0); }
-                if (pb == M - 1) { sw += n; n = real(0); }
-                if (pa == 0 || pa == M - 1 || pb == 0 || pb == M - 1) x = real(0);
-                R = dt * r;
-                Gd = dt * G;
+                const real ux = c10 + real(2) * c20 * (sa + ox) + c11 * tb;
+                const real uy = c01 + real(2) * c02 * (tb + oy) + c11 * sa;
+                const real r = real(2) * c20 * al + c11 * be + real(2) * c02 * ga - nu * ux - om * uy + ph * u0 + sT * G;
+                const real dE = dt * wE, dW = dt * wW, dN = dt * wN, dS = dt * wS, dX = dt * wX;
+                const bool aw = pa == 0, ae = pa == M - 1, bs = pb == 0, bn = pb == M - 1;
+                const real e = aw ? dE + dW : (ae ? real(0) : dE);
+                const real ww = ae ? dW + dE : (aw ? real(0) : dW);
+                const real n = bs ? dN + dS : (bn ? real(0) : dN);
+                const real sw = bn ? dS + dN : (bs ? real(0) : dS);
+                const real x = (aw || ae || bs || bn) ? real(0) : dX;
+                store_vec4_shared<real>(rec0 + pt * 4, e, ww, n, sw);
+                store_vec4_shared<real>(rec1 + pt * 4, x, real(1) + dt * wC, dt * r, dt * G);
+                real* sq = side + pq * 8 * M;
+                if (aw) { sq[2 * pb] = dW; sq[2 * pb + 1] = dX; }
+                if (ae) { sq[2 * (M + pb)] = dE; sq[2 * (M + pb) + 1] = dX; }
+                if (bs) { sq[2 * (2 * M + pa)] = dS; sq[2 * (2 * M + pa) + 1] = dX; }
+                if (bn) { sq[2 * (3 * M + pa)] = dN; sq[2 * (3 * M + pa) + 1] = dX; }
+            };
+            if (mode == COEF_POLAR) {
+                // polar map: each lane (q, a) forms the angular factors of its column
+                // once (table_coeffs' A, B, C, B', velocity projections) and walks
+                // down its micro rows with the radial factors (same for all lanes)
+                if (q < nvalid) {
+                    const real* ct = colt + (q * M + a) * 2;
+                    const real sn = ct[0], co = ct[1];
+                    const real ss = sn * sn, c2 = co * co, sc = sn * co;
+                    const real Av = ss * K11 - real(2) * sc * K12 + c2 * K22;
+                    const real Bv = sc * (K22 - K11) + (c2 - ss) * K12;
+                    const real Cv = c2 * K11 + real(2) * sc * K12 + ss * K22;
+                    const real Bp = (c2 - ss) * (K22 - K11) - real(4) * sc * K12;
+                    const real V1 = -sn * v1 + co * v2, V2 = co * v1 + sn * v2;
+#pragma unroll 1
+                    for (int b = 0; b < M; ++b) {
+                        const real* rt = rowt + b * 4;
+                        const real iR = rt[0], iRp = rt[1], qq = rt[2];
+                        const real al = Av * iR * iR;
+                        const real be = real(2) * Bv * iR * iRp;
+                        const real ga = Cv * iRp * iRp;
+                        const real nu = V1 * iR + real(2) * Bv * iR * iR;
+                        const real om = V2 * iRp - (Bp + Cv * (real(1) - qq)) * iR * iRp;
+                        emit((q * M + b) * M + a, q, a, b, al, be, ga, nu, om, f0, real(0));
+                    }
+                } else if (q < P) {
+#pragma unroll 1
+                    for (int b = 0; b < M; ++b) {
+                        const int pt = (q * M + b) * M + a;
+                        store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
+                        store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
+                    }
+                }
+            } else {
+                // per-point coefficient records: every lane takes points of the group in turn
+#pragma unroll 1
+                for (int pt = lane; pt < npt; pt += 32) {
+                    const int pq = pt / (M * M);
+                    const int rem = pt - pq * (M * M);
+                    const int pb = rem / M;
+                    const int pa = rem - pb * M;
+                    if (pq < nvalid) {
+                        const real* pr = rect + pb * recrow + (pq * M + pa) * 8;
+                        emit(pt, pq, pa, pb, pr[0], pr[1], pr[2], pr[3], pr[4], pr[5], pr[6]);
+                    } else {
+                        store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
+                        store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
+                    }
+                }
             }
-            store_vec4_shared<real>(rec0 + (size_t)pt * 4, e, ww, n, sw);
-            store_vec4_shared<real>(rec1 + (size_t)pt * 4, x, cc, R, Gd);
-            real* sq = side + (size_t)pq * 8 * M;
-            if (pa == 0) { sq[2 * pb] = dW; sq[2 * pb + 1] = dX; }
-            if (pa == M - 1) { sq[2 * (M + pb)] = dE; sq[2 * (M + pb) + 1] = dX; }
-            if (pb == 0) { sq[2 * (2 * M + pa)] = dS; sq[2 * (2 * M + pa) + 1] = dX; }
-            if (pb == M - 1) { sq[2 * (3 * M + pa)] = dN; sq[2 * (3 * M + pa) + 1] = dX; }
         }
         __syncwarp();
         // ghost terms: a ghost neighbour (a', b') outside the patch adds
@@ -253,7 +426,7 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
             for (int e = lane; e < P * M; e += 32) {
                 const int pq = e / M;
                 const int p = e - pq * M;
-                if (ic0 + pq >= I.ncols) continue;
+                if (pq >= nvalid) continue;
                 const real* c9 = cv_s + pq * 12;
                 const real c21 = c9[6], c12 = c9[7], c22 = c9[8];
                 const real* sq = side + (size_t)pq * 8 * M + 2 * (sd * M + p);
@@ -329,10 +502,10 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     }
     if (active && a == 0) {
         const double* dq = fp64_s + qc * 4;
+        const double2 sc = A.scale[it.inst];
         double bias = 0.0;
         if (I.restrict_mode == PD_RESTRICT_MACRO) bias = (I.dx * I.dx * dq[0] + I.dy * I.dy * dq[1]) * (1.0 / 6.0);
-        double bias_scale = A.dtm[it.inst] * I.inv_tau;
-        double inc = fma((double)col, bias_scale * I.inv_nn, bias * bias_scale);
+        double inc = fma((double)col, sc.x, bias * sc.y);
         if (!isfinite(inc)) atomicOr(I.err, ERR_NONFINITE);
         Un[(long long)j * I.nxp + i] = dq[2] + inc;
     }
@@ -372,15 +545,27 @@ __global__ void __launch_bounds__(128, BatchBounds<M, real>::min_blocks) batch_k
     const int lane = threadIdx.x & 31;
     if (lane < 8) reinterpret_cast<real*>(stage + WarpStage<M, real>::zero_off)[lane] = real(0);
     __syncwarp();
-    for (;;) {
-        int idx = 0;
-        if (lane == 0) idx = atomicAdd(A.counter, 1);
-        idx = __shfl_sync(kFull, idx, 0);
-        if (idx >= A.n_items) break;
-        const BatchItem it = A.items[idx];
+    // the next item's index, record and the head of its instance record are
+    // requested while the current item runs
+    auto fetch = [&]() -> int {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(A.counter, 1);
+        return __shfl_sync(kFull, v, 0);
+    };
+    int idx = fetch();
+    BatchItem it = idx < A.n_items ? A.items[idx] : BatchItem{ 0, 0, 0, 0 };
+    while (idx < A.n_items) {
+        const int nidx = fetch();
+        const BatchItem nit = nidx < A.n_items ? A.items[nidx] : BatchItem{ 0, 0, 0, 0 };
+        if (nidx < A.n_items && lane < 4) {
+            const char* p = reinterpret_cast<const char*>(A.insts + nit.inst) + lane * 128;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+        }
         const InstDev& I = A.insts[it.inst];
-        if (it.kind == 1) { boundary_item(I, it, A, lane); continue; }
-        patch_item<M, TSRC, real>(I, it, A, lane, stage);
+        if (it.kind == 1) boundary_item(I, it, A, lane);
+        else patch_item<M, TSRC, real>(I, it, A, lane, stage);
+        idx = nidx;
+        it = nit;
     }
 }
 

@@ -518,6 +518,7 @@ struct BatchArgs {
     double* Sbase;             // scratch field
     int parity;                // step parity: reads Ubase if 0
     const double* dtm;         // per-instance macro step
+    const double2* scale;      // per instance: (dtm / (tau (m_xi - 1)(m_eta - 1)), dtm / tau), formed on the host
     const double* tab;         // per-instance time tables (nullable)
     const long long* tab_off;  // per-instance offset of the table of this pd_step
     int step;                  // macro step index within the pd_step call
