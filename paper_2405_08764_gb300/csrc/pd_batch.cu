@@ -312,6 +312,95 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                     store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
                 }
             }
+        } else if (mode == COEF_POLAR) {
+            // Polar map x = R cos xi, y = R sin xi with constant K, v, f: each
+            // coefficient of table_coeffs is a sum of products of an angular factor
+            // (the lane's micro column) and a radial factor (the micro row, shared by
+            // all lanes), so the angular part is formed once per lane.  Radial factors
+            // per micro row first, one lane each:
+            real* rowq = reinterpret_cast<real*>(stage + S::row_off);
+            if (lane < M) {
+                const real* rt = rowt + lane * 4;
+                const real iR = rt[0], iRp = rt[1], qq = rt[2];
+                const real iRR = iR * iRp;
+                real* o = rowq + lane * 8;
+                store_vec4_shared<real>(o, iR, iRp, iR * iR, iRR);
+                store_vec4_shared<real>(o + 4, iRp * iRp, (real(1) - qq) * iRR, t0 + real(lane) * dy, real(0));
+            }
+            __syncwarp();
+            if (q < nvalid) {
+                const real* ct = colt + (q * M + a) * 2;
+                const real sn = ct[0], co = ct[1];
+                const real ss = sn * sn, c2 = co * co, sc = sn * co;
+                const real Av = ss * K11 - real(2) * sc * K12 + c2 * K22;
+                const real Bv = sc * (K22 - K11) + (c2 - ss) * K12;
+                const real Cv = c2 * K11 + real(2) * sc * K12 + ss * K22;
+                const real Bp = (c2 - ss) * (K22 - K11) - real(4) * sc * K12;
+                const real V1 = -sn * v1 + co * v2, V2 = co * v1 + sn * v2;
+                const real Bv2 = real(2) * Bv;
+                const real* c9 = cv_s + q * 12;
+                real C0, c10, c01, c20, c11, c02, c21_, c12_;
+                load_vec4_shared<real>(c9, C0, c10, c01, c20);
+                load_vec4_shared<real>(c9 + 4, c11, c02, c21_, c12_);
+                const real sa = s0 + real(a) * dx;
+                const real uxa = c10 + real(2) * c20 * sa;               // d/dxi of the lift at (s, 0)
+                const real U0a = C0 + sa * (c10 + sa * c20);
+                const real c20dx = c20 * dx, c02dy = c02 * dy;
+                const bool aw = a == 0, ae = a == M - 1;
+                real* sq = side + q * 8 * M;
+#pragma unroll 1
+                for (int b = 0; b < M; ++b) {
+                    real iR, iRp, iR2, iRR, iRp2, omq, tb, pad;
+                    load_vec4_shared<real>(rowq + b * 8, iR, iRp, iR2, iRR);
+                    load_vec4_shared<real>(rowq + b * 8 + 4, iRp2, omq, tb, pad);
+                    const real al = Av * iR2, be = Bv2 * iRR, ga = Cv * iRp2;
+                    const real nu = V1 * iR + Bv2 * iR2;
+                    const real om = V2 * iRp - Bp * iRR - Cv * omq;
+                    const real ax = al * idx2, gy = ga * idy2;
+                    real wC = -real(2) * ax - real(2) * gy + f0;
+                    const real wX = be * i4dxdy;
+                    real wE, wW, wN, wS, ox2, oy2;                        // ox2 = 2 c20 ox, oy2 = 2 c02 oy
+                    if (central) {
+                        const real hn = real(0.5) * nu * idx, ho = real(0.5) * om * idy;
+                        wE = ax - hn; wW = ax + hn; wN = gy - ho; wS = gy + ho;
+                        ox2 = real(0); oy2 = real(0);
+                    } else {
+                        const real nx = nu * idx, oyv = om * idy;
+                        const bool pn = nu > real(0), po = om > real(0);
+                        wW = pn ? ax + nx : ax;
+                        wE = pn ? ax : ax - nx;
+                        wC = pn ? wC - nx : wC + nx;
+                        ox2 = pn ? -c20dx : c20dx;
+                        wS = po ? gy + oyv : gy;
+                        wN = po ? gy : gy - oyv;
+                        wC = po ? wC - oyv : wC + oyv;
+                        oy2 = po ? -c02dy : c02dy;
+                    }
+                    const real ux = uxa + ox2 + c11 * tb;
+                    const real uy = c01 + real(2) * c02 * tb + oy2 + c11 * sa;
+                    const real u0 = U0a + tb * (c11 * sa + c01 + c02 * tb);
+                    const real r = real(2) * c20 * al + c11 * be + real(2) * c02 * ga - nu * ux - om * uy + f0 * u0;
+                    const real dE = dt * wE, dW = dt * wW, dN = dt * wN, dS = dt * wS, dX = dt * wX;
+                    const bool bs = b == 0, bn = b == M - 1;
+                    const int pt = (q * M + b) * M + a;
+                    store_vec4_shared<real>(rec0 + pt * 4, aw ? dE + dW : (ae ? real(0) : dE),
+                                            ae ? dW + dE : (aw ? real(0) : dW), bs ? dN + dS : (bn ? real(0) : dN),
+                                            bn ? dS + dN : (bs ? real(0) : dS));
+                    store_vec4_shared<real>(rec1 + pt * 4, (aw || ae || bs || bn) ? real(0) : dX, real(1) + dt * wC,
+                                            dt * r, real(0));
+                    if (aw) { sq[2 * b] = dW; sq[2 * b + 1] = dX; }
+                    if (ae) { sq[2 * (M + b)] = dE; sq[2 * (M + b) + 1] = dX; }
+                    if (bs) { sq[2 * (2 * M + a)] = dS; sq[2 * (2 * M + a) + 1] = dX; }
+                    if (bn) { sq[2 * (3 * M + a)] = dN; sq[2 * (3 * M + a) + 1] = dX; }
+                }
+            } else if (q < P) {
+#pragma unroll 1
+                for (int b = 0; b < M; ++b) {
+                    const int pt = (q * M + b) * M + a;
+                    store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
+                    store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
+                }
+            }
         } else {
             // general point: record of micro point (pa, pb) of patch pq from its
             // transformed coefficients, written at pt; weights and the forcing of
@@ -363,39 +452,7 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                 if (bs) { sq[2 * (2 * M + pa)] = dS; sq[2 * (2 * M + pa) + 1] = dX; }
                 if (bn) { sq[2 * (3 * M + pa)] = dN; sq[2 * (3 * M + pa) + 1] = dX; }
             };
-            if (mode == COEF_POLAR) {
-                // polar map: each lane (q, a) forms the angular factors of its column
-                // once (table_coeffs' A, B, C, B', velocity projections) and walks
-                // down its micro rows with the radial factors (same for all lanes)
-                if (q < nvalid) {
-                    const real* ct = colt + (q * M + a) * 2;
-                    const real sn = ct[0], co = ct[1];
-                    const real ss = sn * sn, c2 = co * co, sc = sn * co;
-                    const real Av = ss * K11 - real(2) * sc * K12 + c2 * K22;
-                    const real Bv = sc * (K22 - K11) + (c2 - ss) * K12;
-                    const real Cv = c2 * K11 + real(2) * sc * K12 + ss * K22;
-                    const real Bp = (c2 - ss) * (K22 - K11) - real(4) * sc * K12;
-                    const real V1 = -sn * v1 + co * v2, V2 = co * v1 + sn * v2;
-#pragma unroll 1
-                    for (int b = 0; b < M; ++b) {
-                        const real* rt = rowt + b * 4;
-                        const real iR = rt[0], iRp = rt[1], qq = rt[2];
-                        const real al = Av * iR * iR;
-                        const real be = real(2) * Bv * iR * iRp;
-                        const real ga = Cv * iRp * iRp;
-                        const real nu = V1 * iR + real(2) * Bv * iR * iR;
-                        const real om = V2 * iRp - (Bp + Cv * (real(1) - qq)) * iR * iRp;
-                        emit((q * M + b) * M + a, q, a, b, al, be, ga, nu, om, f0, real(0));
-                    }
-                } else if (q < P) {
-#pragma unroll 1
-                    for (int b = 0; b < M; ++b) {
-                        const int pt = (q * M + b) * M + a;
-                        store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
-                        store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
-                    }
-                }
-            } else {
+            {
                 // per-point coefficient records: every lane takes points of the group in turn
 #pragma unroll 1
                 for (int pt = lane; pt < npt; pt += 32) {
