@@ -772,6 +772,11 @@ def run_surrogate(args):
     W_ = g.init_field()
     s.step(W_, 0.0, dtm, 2)                      # warm-up
     U = g.init_field()
+    # the method without the network: every patch takes the one-step estimate F1
+    W1 = g.init_field()
+    s.step_f1(W1.clone(), 0.0, dtm, 2)           # warm-up
+    res["f1_only"] = timed(lambda: s.step_f1(W1, 0.0, dtm, n_macro))
+    fields["f1_only"] = W1
     st0, fb0 = s.counts()
     sampler = ClockSampler(0)
     sampler.start()
@@ -809,6 +814,7 @@ def run_surrogate(args):
         "speedup_vs_plain_fp64": res["plain_fp64"] / res["surrogate"],
         "speedup_vs_plain_fp32": res["plain_fp32"] / res["surrogate"],
         "speedup_vs_plain_k1_fp32": res["plain_k1_fp32"] / res["surrogate"],
+        "speedup_vs_f1_only": res["f1_only"] / res["surrogate"],
         "l2_rel_vs_plain_fp64": err,
         "served_by_network": served,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",

@@ -156,6 +156,14 @@ pd_status pd_surrogate_evaluate(pd_surrogate* s, const double* U_dev, double t, 
  * burst otherwise (eps < 0: every patch takes the burst). */
 pd_status pd_surrogate_step(pd_surrogate* s, double* U_dev, double t0, double dt_macro, int n_macro, double eps);
 
+/* The same macro steps without the network: every patch's F is the check's
+ * estimate F1, the restricted change of a burst of one micro step over that
+ * step (eq. (Time_Derivative) with tau = dt_micro; Section 4.1.1's Table 3
+ * and Section 4.2's Table 6 show F insensitive to tau), evaluated in closed
+ * form from the per-patch one-step basis.  The baseline that shows what the
+ * network gains.  Errors: PD_EINVAL, PD_ECUDA. */
+pd_status pd_surrogate_step_f1(pd_surrogate* s, double* U_dev, double t0, double dt_macro, int n_macro);
+
 /* V = U + rel_sigma max|U| z on the interior nodes (boundary rows and, on
  * non-periodic grids, boundary columns copied): grid-scale perturbations for
  * training data.  z = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller) with

@@ -122,6 +122,7 @@ SIGNATURES = {
     "pd_surrogate_targets": (C.c_int, [_VP, _VP, C.c_double, _VP, _VP]),
     "pd_surrogate_evaluate": (C.c_int, [_VP, _VP, C.c_double, _VP, _VP, _VP]),
     "pd_surrogate_step": (C.c_int, [_VP, _VP, C.c_double, C.c_double, C.c_int, C.c_double]),
+    "pd_surrogate_step_f1": (C.c_int, [_VP, _VP, C.c_double, C.c_double, C.c_int]),
     "pd_surrogate_counts": (C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "pd_surrogate_perturb": (C.c_int, [_VP, _VP, C.c_double, C.c_ulonglong, _VP]),
 }

@@ -405,6 +405,13 @@ class Surrogate:
         N.check(self.L.pd_surrogate_step(self.h, self._p(U), float(t0), float(dt_macro), int(n_macro), float(eps)),
                 self.grid.h)
 
+    def step_f1(self, U: torch.Tensor, t0: float, dt_macro: float, n_macro: int):
+        """The same macro steps with every patch's F taken from the one-micro-step
+        estimate F1 (no network)."""
+        self._pre()
+        N.check(self.L.pd_surrogate_step_f1(self.h, self._p(U), float(t0), float(dt_macro), int(n_macro)),
+                self.grid.h)
+
     def perturb(self, U: torch.Tensor, rel_sigma: float, seed: int, out: torch.Tensor = None) -> torch.Tensor:
         """U plus seeded grid-scale noise of relative size rel_sigma on the interior nodes"""
         V = torch.empty_like(U) if out is None else out

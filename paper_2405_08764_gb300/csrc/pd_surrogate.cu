@@ -199,6 +199,27 @@ check_kernel(int n, const float* __restrict__ yhat, const double* __restrict__ s
     if (fb) list[base_s + cnt_s[warp] + __popc(b & ((1u << lane) - 1u))] = p;
 }
 
+// The scheme with bursts of one micro step (tau = dt): per patch the restricted
+// change of one forward-Euler step from the lift, exactly the check's estimate
+// F1 = sum_q T1_q U_q + s(T) T1_9 over the 3x3 stencil (never clamped for a
+// patch), written as dU = F1 tau, the change the projection divides by tau.
+// One patch per thread.
+__global__ void f1_step_kernel(const InstDev I, const double* __restrict__ U, const double* __restrict__ T1,
+                               const double* __restrict__ sT, double tau, double* __restrict__ dU)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= I.n_patch) return;
+    const int i = I.i0 + p % I.ncols, j = 1 + p / I.ncols;
+    const double* t = T1 + (long long)p * 10;
+    double f = *sT * t[9];
+    for (int pp = -1; pp <= 1; ++pp) {
+        int c = i + pp;
+        if (I.periodic) c = c < 0 ? c + I.nxp : (c >= I.nxp ? c - I.nxp : c);
+        for (int qq = -1; qq <= 1; ++qq) f = fma(t[(pp + 1) * 3 + qq + 1], U[(long long)(j + qq) * I.nxp + c], f);
+    }
+    dU[p] = f * tau;
+}
+
 __global__ void maxabs_kernel(long long n, const double* __restrict__ U, unsigned long long* __restrict__ out)
 {
     double v = 0.0;
@@ -466,6 +487,29 @@ pd_status pd_surrogate_step(pd_surrogate* s, double* U, double t0, double dt_mac
     }
     grid_count_launches(s->g, nl);
     s->patch_steps += (long long)s->n * n_macro;
+    return PD_OK;
+}
+
+pd_status pd_surrogate_step_f1(pd_surrogate* s, double* U, double t0, double dt_macro, int n_macro)
+{
+    if (!s) return PD_EINVAL;
+    if (!U || n_macro < 0) return sfail(s, PD_EINVAL, "null field or negative step count");
+    if (n_macro == 0) return PD_OK;
+    pd_status rc = ensure_tables(s, n_macro);
+    if (rc) return rc;
+    const InstDev& I = s->ga.I;
+    cudaStream_t st = s->ga.stream;
+    const double dtm = dt_macro > 0 ? dt_macro : s->ga.dtm_sugg;
+    const int strideK = I.K + kTabExtra;
+    SCUDA(s, launch_time_table(I, t0, dtm, n_macro, s->tabK, st));
+    for (int k = 0; k < n_macro; ++k) {
+        const double t = t0 + k * dtm;
+        const double* row = s->tabK + (size_t)k * strideK;
+        f1_step_kernel<<<blocks(s->n, 128), 128, 0, st>>>(I, U, s->T1, row + I.K, I.K * I.dt, s->dUf);
+        SCUDA(s, cudaGetLastError());
+        SCUDA(s, launch_project(I, U, s->dUf, t, dtm, st));
+    }
+    grid_count_launches(s->g, 1 + 2LL * n_macro);
     return PD_OK;
 }
 

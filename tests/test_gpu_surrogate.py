@@ -270,3 +270,43 @@ def test_full_size_annulus_sampled_patches(api):
     expect = dtm * np.where(r <= eps, Fh[sel], FK[sel])
     scale = dtm * max(np.abs(Fh[sel]).max(), np.abs(FK[sel]).max())
     np.testing.assert_allclose(d[clear], expect[clear], rtol=0, atol=1e-6 * scale)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_one_step_scheme_matches_oracle_with_one_micro_step(api, prec, tol):
+    """pd_surrogate_step_f1 (every patch takes the check estimate F1, no network)
+    is the plain scheme with bursts of one micro step: the oracle's step with
+    K = 1 at the same micro step, Dirichlet data and projection."""
+    p = _small()
+    g = api.Grid(p, prec=prec)
+    s = api.Surrogate(g, _net(api))
+    dt, dtm = g.info()["dt_micro"], g.info()["dt_macro_suggested"]
+    U = g.init_field()
+    U0 = U.cpu().numpy()
+    s.step_f1(U, 0.0, dtm, 6)
+    g.sync()
+    want = Oracle(dict(p, k_micro=1)).step(U0, 0.0, dtm, 6, dt)
+    err = np.linalg.norm(U.cpu().numpy() - want) / np.linalg.norm(want)
+    assert err <= tol, err
+
+
+def test_one_step_scheme_is_within_the_check_tolerance_of_the_burst(api):
+    """Section 4's tau-insensitivity on the surrogate workload: over 20 macro
+    steps the scheme without the network at one micro step per burst moves the
+    field by the same change as the K-step scheme to within the 1e-3 tolerance
+    the surrogate is held to (1.5e-4 here), so F1 -- the estimate the residual
+    check compares the network with -- is itself an admissible answer, and the
+    network's gain is measured against it (bench.py --workload c5: f1_only)."""
+    p = _small()
+    g = api.Grid(p, prec="fp64")
+    s = api.Surrogate(g, _net(api))
+    dtm = g.info()["dt_macro_suggested"]
+    U0 = g.init_field()
+    A, B = U0.clone(), U0.clone()
+    g.step(A, 0.0, dtm, 20)
+    s.step_f1(B, 0.0, dtm, 20)
+    g.sync()
+    a, b, u0 = A.cpu().numpy(), B.cpu().numpy(), U0.cpu().numpy()
+    rel = np.linalg.norm(a - b) / np.linalg.norm(a - u0)
+    assert rel <= 1e-3, rel
+    assert rel > 1e-8, rel          # the two schemes are distinct: K = 20 bursts are not K = 1
