@@ -51,7 +51,10 @@ def flop_per_update(has_cross: bool) -> float:
 
 # DRAM traffic of the dominant kernel from an ncu capture of this kernel
 # source (sha256 of the sources); null once the kernel changes.
-NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+# For the batch: the four per-size launches of one macro step of the 4096-instance
+# batch (profiles/batch_kernel_c4.md).
+NCU_TRAFFIC = {"sources_sha256": "77ac4aeb5dcd06b29f0c98503fdffdec2bb4705e9721fc1a279fc0c088ba2bba",
+               "bytes_per_launch": 462.6e6}
 
 
 def kernel_sources_sha(files=("pd_batch.cu", "pd_device.cuh", "pd_internal.h")) -> str:
@@ -463,7 +466,9 @@ def run_batch(args):
     time.sleep(0.3)
     g.set_timing(True)
     l0 = g.launches()
+    torch.cuda.nvtx.range_push("timed")          # profilers can restrict a capture to this range
     ms = time_steps(g, U, U0, n_macro, args.steps, flush, stream)
+    torch.cuda.nvtx.range_pop()
     launches = g.launches() - l0
     kern_ms, kern_n = g.timing()
     g.set_timing(False)
@@ -513,10 +518,12 @@ def run_batch(args):
                      "sampled_instances": err32["instances"], "max_rel_l2": err32["max"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                      "frac": achieved / pk["fp32_tflops"], "traffic": traffic,
-                     "traffic_note": None if traffic is not None else
-                     "no DRAM capture of the current kernel source; the batch is ALU-bound (per macro step "
-                     "it reads and writes the FP64 fields, 2 x %.0f MB, and the 1-D metric tables)"
-                     % (field_bytes / 1e6),
+                     "traffic_note": ("dram read + write of the four per-size launches of one macro step "
+                                      "(the unit of achieved), one ncu capture of this kernel source on the "
+                                      "4096-instance batch" if traffic is not None else
+                                      "no DRAM capture of the current kernel source; the batch is ALU-bound "
+                                      "(per macro step it reads and writes the FP64 fields, 2 x %.0f MB, and "
+                                      "the 1-D metric tables)" % (field_bytes / 1e6)),
                      "kernel": "batch_kernel (work queue per micro size, one launch per micro size and macro step)",
                      "flop_per_macro_step": flop_step,
                      "flop_per_point_update": "25 with a cross term, 20 without (%d of %d instances have one)"

@@ -827,6 +827,7 @@ long long pd_launch_count(const pd_grid* g) { return g ? g->launches : 0; }
 
 pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_stream, pd_grid** out)
 {
+    NvtxRange nvtx_range("pd_create_grid");
     if (!descs || n_inst < 1 || !out) return PD_EINVAL;
     *out = nullptr;
     pd_grid* g = new pd_grid();
@@ -905,6 +906,7 @@ pd_status pd_create_grid(const pd_grid_desc* descs, int n_inst, void* cuda_strea
 
 pd_status pd_destroy_grid(pd_grid* g)
 {
+    NvtxRange nvtx_range("pd_destroy_grid");
     if (!g) return PD_EINVAL;
     DeviceGuard dg(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
@@ -938,6 +940,7 @@ pd_status pd_set_graph_mode(pd_grid* g, int enabled)
 
 pd_status pd_set_coeffs(pd_grid* g, int inst, const pd_coeff_desc* c)
 {
+    NvtxRange nvtx_range("pd_set_coeffs");
     pd_status rc = check_inst(g, inst);
     if (rc) return rc;
     if (!c) return fail(g, PD_EINVAL, "null coefficient descriptor");
@@ -1082,6 +1085,7 @@ pd_status pd_sizes(const pd_grid* g, long long* nm, long long* np, size_t* sb)
 
 pd_status pd_get_coeffs(pd_grid* g, int inst, double* out)
 {
+    NvtxRange nvtx_range("pd_get_coeffs");
     pd_status rc = check_inst(g, inst);
     if (rc) return rc;
     Inst& s = g->inst[inst];
@@ -1096,6 +1100,7 @@ pd_status pd_get_coeffs(pd_grid* g, int inst, double* out)
 
 pd_status pd_init_field(pd_grid* g, int inst, int kind, const double* prm, int n_prm, double t, double* U)
 {
+    NvtxRange nvtx_range("pd_init_field");
     pd_status rc = check_inst(g, inst);
     if (rc) return rc;
     Inst& s = g->inst[inst];
@@ -1119,6 +1124,7 @@ pd_status pd_init_field(pd_grid* g, int inst, int kind, const double* prm, int n
 
 pd_status pd_lift(pd_grid* g, const double* U, double t, void* state)
 {
+    NvtxRange nvtx_range("pd_lift");
     if (!g) return PD_EINVAL;
     if (!U || !state) return fail(g, PD_EINVAL, "null pointer");
     if (((uintptr_t)state) & 255) return fail(g, PD_EINVAL, "state buffer must be 256-byte aligned");
@@ -1136,6 +1142,7 @@ pd_status pd_lift(pd_grid* g, const double* U, double t, void* state)
 
 pd_status pd_micro_burst(pd_grid* g, void* state, double t, int k_steps)
 {
+    NvtxRange nvtx_range("pd_micro_burst");
     if (!g) return PD_EINVAL;
     if (!state) return fail(g, PD_EINVAL, "null state");
     if (k_steps < 0 || k_steps > kMaxK) return fail(g, PD_EINVAL, "k_steps must be in [0, 4096]");
@@ -1156,6 +1163,7 @@ pd_status pd_micro_burst(pd_grid* g, void* state, double t, int k_steps)
 
 pd_status pd_restrict(pd_grid* g, const void* state, double* dU)
 {
+    NvtxRange nvtx_range("pd_restrict");
     if (!g) return PD_EINVAL;
     if (!state || !dU) return fail(g, PD_EINVAL, "null pointer");
     pd_status rc = all_coeffs_set(g);
@@ -1172,6 +1180,7 @@ pd_status pd_restrict(pd_grid* g, const void* state, double* dU)
 
 pd_status pd_project(pd_grid* g, double* U, const double* dU, double t, double dtm)
 {
+    NvtxRange nvtx_range("pd_project");
     if (!g) return PD_EINVAL;
     if (!U || !dU) return fail(g, PD_EINVAL, "null pointer");
     if (!(dtm > 0)) return fail(g, PD_EINVAL, "dt_macro must be positive");
@@ -1187,6 +1196,7 @@ pd_status pd_project(pd_grid* g, double* U, const double* dU, double t, double d
 
 pd_status pd_step(pd_grid* g, double* U, double t0, double dt_macro, int n_macro)
 {
+    NvtxRange nvtx_range("pd_step");
     if (!g) return PD_EINVAL;
     if (!U) return fail(g, PD_EINVAL, "null field");
     if (n_macro < 0) return fail(g, PD_EINVAL, "n_macro must be >= 0");
@@ -1279,6 +1289,7 @@ pd_status pd_set_coeff_storage(pd_grid* g, int mode)
 
 pd_status pd_autotune(pd_grid* g, int n_trial_steps, int* block, int* half_patches)
 {
+    NvtxRange nvtx_range("pd_autotune");
     if (!g) return PD_EINVAL;
     pd_status rc = all_coeffs_set(g);
     if (rc) return rc;
@@ -1382,6 +1393,7 @@ pd_status pd_get_timing(pd_grid* g, double* ms, long long* n)
 
 pd_status pd_sync(pd_grid* g)
 {
+    NvtxRange nvtx_range("pd_sync");
     if (!g) return PD_EINVAL;
     DeviceGuard dg(g->device);
     PD_CUDA(g, cudaStreamSynchronize(g->stream));
@@ -1413,6 +1425,7 @@ const char kMagic[8] = { 'P', 'D', 'C', 'K', 'P', 'T', '0', '1' };
 
 pd_status pd_save_checkpoint(pd_grid* g, const double* U, double t, long long step, const char* path)
 {
+    NvtxRange nvtx_range("pd_save_checkpoint");
     if (!g || !U || !path) return fail(g, PD_EINVAL, "null argument");
     DeviceGuard dg(g->device);
     std::vector<double> h((size_t)g->n_macro_total);
@@ -1431,6 +1444,7 @@ pd_status pd_save_checkpoint(pd_grid* g, const double* U, double t, long long st
 
 pd_status pd_load_checkpoint(pd_grid* g, double* U, double* t, long long* step, const char* path)
 {
+    NvtxRange nvtx_range("pd_load_checkpoint");
     if (!g || !U || !path) return fail(g, PD_EINVAL, "null argument");
     DeviceGuard dg(g->device);
     FILE* f = std::fopen(path, "rb");
@@ -1517,6 +1531,7 @@ extern "C" {
 
 pd_status pd_step_noalloc(pd_grid* g, double* U, double t0, double dt_macro, int n_macro)
 {
+    NvtxRange nvtx_range("pd_step_noalloc");
     if (!g) return PD_EINVAL;
     if (!U) return fail(g, PD_EINVAL, "null field");
     if (n_macro < 0) return fail(g, PD_EINVAL, "n_macro must be >= 0");

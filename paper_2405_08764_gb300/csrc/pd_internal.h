@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "pd.h"
@@ -388,6 +389,16 @@ __device__ __forceinline__ double exact_solution(int sol, double x, double y, do
 }
 
 enum ErrBits { ERR_NONFINITE = 1, ERR_JACOBIAN = 2, ERR_COEF = 4, ERR_TIMEOUT = 8 };
+
+// An NVTX range named after a C-ABI call for the lifetime of the object, so
+// profilers show each call's kernels under it (header-only NVTX: inert when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Makes `dev` the calling thread's current device for the lifetime of the
 // guard and restores the caller's device afterwards, so a host thread that

@@ -3,6 +3,7 @@
 // GELU backward, split-K gradient accumulation, the final 256 -> 1 layer),
 // plus the elementwise training kernels (minibatch gather, loss and head
 // backward, bias gradients, Adam) and the C ABI of include/pd_surrogate.h.
+#include "pd_internal.h"
 #include "pd_surrogate.h"
 #include "pd_tc.cuh"
 
@@ -1297,6 +1298,7 @@ pd_status pd_mlp_pack(pd_mlp* m, const float* X, const float* y, long long n, ui
 
 pd_status pd_mlp_forward(pd_mlp* m, const uint16_t* X, long long n, float* y)
 {
+    pd::NvtxRange nvtx_range("pd_mlp_forward");
     if (!m) return PD_EINVAL;
     if (n == 0) return PD_OK;
     if (!X || !y || n < 0) return mfail(m, PD_EINVAL, "null argument");
@@ -1365,6 +1367,7 @@ pd_status pd_mlp_adam_step(pd_mlp* m, float lr)
 pd_status pd_mlp_train(pd_mlp* m, const uint16_t* X, const float* T, long long n, int batch, int epochs, float lr_max,
                        unsigned long long seed, float* loss_hist)
 {
+    pd::NvtxRange nvtx_range("pd_mlp_train");
     if (!m) return PD_EINVAL;
     if (!X || !T) return mfail(m, PD_EINVAL, "null argument");
     if (batch < 128 || batch % 128 || batch > m->cap) return mfail(m, PD_EINVAL, "batch must be a multiple of 128 and <= max_batch");

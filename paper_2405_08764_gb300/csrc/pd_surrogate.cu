@@ -388,6 +388,7 @@ pd_status pd_surrogate_destroy(pd_surrogate* s)
 
 pd_status pd_surrogate_features(pd_surrogate* s, const double* U, uint16_t* X, double* scale, float* Xraw, double* Rs)
 {
+    NvtxRange nvtx_range("pd_surrogate_features");
     if (!s) return PD_EINVAL;
     if (!U) return sfail(s, PD_EINVAL, "null field");
     if (X || scale) {
@@ -404,6 +405,7 @@ pd_status pd_surrogate_features(pd_surrogate* s, const double* U, uint16_t* X, d
 
 pd_status pd_surrogate_targets(pd_surrogate* s, const double* U, double t, const double* Rs, float* y)
 {
+    NvtxRange nvtx_range("pd_surrogate_targets");
     if (!s) return PD_EINVAL;
     if (!U || !Rs || !y) return sfail(s, PD_EINVAL, "null argument");
     pd_status rc = ensure_tables(s, 1);
@@ -420,6 +422,7 @@ pd_status pd_surrogate_targets(pd_surrogate* s, const double* U, double t, const
 
 pd_status pd_surrogate_evaluate(pd_surrogate* s, const double* U, double t, double* F_hat, double* F1, double* F)
 {
+    NvtxRange nvtx_range("pd_surrogate_evaluate");
     if (!s) return PD_EINVAL;
     if (!U) return sfail(s, PD_EINVAL, "null field");
     pd_status rc = ensure_tables(s, 1);
@@ -451,6 +454,7 @@ pd_status pd_surrogate_evaluate(pd_surrogate* s, const double* U, double t, doub
 
 pd_status pd_surrogate_step(pd_surrogate* s, double* U, double t0, double dt_macro, int n_macro, double eps)
 {
+    NvtxRange nvtx_range("pd_surrogate_step");
     if (!s) return PD_EINVAL;
     if (!U || n_macro < 0) return sfail(s, PD_EINVAL, "null field or negative step count");
     if (n_macro == 0) return PD_OK;
@@ -492,6 +496,7 @@ pd_status pd_surrogate_step(pd_surrogate* s, double* U, double t0, double dt_mac
 
 pd_status pd_surrogate_step_f1(pd_surrogate* s, double* U, double t0, double dt_macro, int n_macro)
 {
+    NvtxRange nvtx_range("pd_surrogate_step_f1");
     if (!s) return PD_EINVAL;
     if (!U || n_macro < 0) return sfail(s, PD_EINVAL, "null field or negative step count");
     if (n_macro == 0) return PD_OK;
