@@ -142,6 +142,46 @@ __device__ __forceinline__ real gap_eta(real c21, real c12, real c22, real s, re
     return s * (c21 * s + real(2) * c12 * t + real(2) * c22 * s * t);
 }
 
+// Ghost-neighbour terms (dt-scaled) of micro point (a, b), the part of
+// burst_forcing that only edge points have, from the point's unfolded
+// dt-scaled weights toward the ghosts (dW at a = 0, dE at a = M - 1, dS at
+// b = 0, dN at b = M - 1) and dX.  A ghost neighbour (a', b') adds
+// weight * (ghost value - lift there); the diagonal ghosts of the cross term go
+// with the W/E side when a' is outside the patch, else with the S/N side.  The
+// Neumann gaps are polynomials along each edge: on xi = se, gap_xi = A1 t + A2
+// t^2 with A1 = 2 c21 se, A2 = c12 + 2 c22 se, so the W/E terms of row t need
+// only gap(t) and gap(t + dy) - gap(t - dy) = 2 dy (A1 + 2 A2 t).
+template <int M, typename real>
+__device__ __forceinline__ real ghost_terms(int a, int b, real dW, real dE, real dS, real dN, real dX, real c21,
+                                            real c12, real c22, real s0, real t0, real dx, real dy)
+{
+    real g = real(0);
+    const bool aw = a == 0, ae = a == M - 1, bs = b == 0, bn = b == M - 1;
+    if (aw || ae) {
+        const real tb = t0 + real(b) * dy;
+        const real sgx = aw ? real(-1) : real(1);
+        const real se = aw ? s0 : -s0;
+        const real sin_ = aw ? s0 + dx : -s0 - dx;          // s of the column next to the edge
+        const real Kx = sgx * real(2) * dx;
+        const real A1 = real(2) * c21 * se, A2 = c12 + real(2) * c22 * se;
+        real dif = Kx * real(2) * dy * (A1 + real(2) * A2 * tb);
+        if (bs) dif += real(2) * dy * gap_eta(c21, c12, c22, sin_, t0);
+        if (bn) dif += real(2) * dy * gap_eta(c21, c12, c22, sin_, -t0);
+        g += (aw ? dW : dE) * (Kx * tb * (A1 + A2 * tb)) + sgx * dX * dif;
+    }
+    if (bs || bn) {
+        const real sa = s0 + real(a) * dx;
+        const real sgy = bs ? real(-1) : real(1);
+        const real te = bs ? t0 : -t0;
+        const real Ky = sgy * real(2) * dy;
+        const real gm = Ky * gap_eta(c21, c12, c22, sa, te);
+        const real gl = a >= 1 ? Ky * gap_eta(c21, c12, c22, sa - dx, te) : real(0);
+        const real gr = a <= M - 2 ? Ky * gap_eta(c21, c12, c22, sa + dx, te) : real(0);
+        g += (bs ? dS : dN) * gm + sgy * dX * (gr - gl);
+    }
+    return g;
+}
+
 template <int M, bool TSRC, typename real>
 __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it, const BatchArgs& A, int lane,
                                            unsigned char* stage)
@@ -279,8 +319,8 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                 const real c10 = c9[1], c20 = c9[3], c11 = c9[4];
                 const real Xa = real(2) * c20 * al - nu * (c10 + real(2) * c20 * (sa + ox)) + f0 * (sa * (c10 + sa * c20));
                 const real fs = f0 * sa;
+                const real c21 = c9[6], c12 = c9[7], c22 = c9[8];
                 const real* rq = rowq + q * M * 12;
-                real* sq = side + q * 8 * M;
 #pragma unroll 1
                 for (int b = 0; b < M; ++b) {
                     real nf, sf, crow, ib, tb, om, Yb, nu_, su, p1, p2, p3;
@@ -295,13 +335,10 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                     const bool redge = b == 0 || b == M - 1;
                     const real x = redge ? real(0) : xin * ib;
                     const int pt = (q * M + b) * M + a;
+                    // unfolded dt wX at (a, b) = xu ib
+                    const real g = ghost_terms<M, real>(a, b, wu, eu, su, nu_, xu * ib, c21, c12, c22, s0, t0, dx, dy);
                     store_vec4_shared<real>(rec0 + pt * 4, ef, wf, nf, sf);
-                    store_vec4_shared<real>(rec1 + pt * 4, x, ccol + crow, dt * r, real(0));
-                    const real xs = xu * ib;                          // unfolded dt * wX at (a, b)
-                    if (a == 0) { sq[2 * b] = wu; sq[2 * b + 1] = xs; }
-                    if (a == M - 1) { sq[2 * (M + b)] = eu; sq[2 * (M + b) + 1] = xs; }
-                    if (b == 0) { sq[2 * (2 * M + a)] = su; sq[2 * (2 * M + a) + 1] = xs; }
-                    if (b == M - 1) { sq[2 * (3 * M + a)] = nu_; sq[2 * (3 * M + a) + 1] = xs; }
+                    store_vec4_shared<real>(rec1 + pt * 4, x, ccol + crow, dt * r + g, real(0));
                 }
             } else if (q < P) {
                 // patches past the end of the row: zero records
@@ -347,7 +384,7 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                 const real U0a = C0 + sa * (c10 + sa * c20);
                 const real c20dx = c20 * dx, c02dy = c02 * dy;
                 const bool aw = a == 0, ae = a == M - 1;
-                real* sq = side + q * 8 * M;
+                const real c22 = c9[8];
 #pragma unroll 1
                 for (int b = 0; b < M; ++b) {
                     real iR, iRp, iR2, iRR, iRp2, omq, tb, pad;
@@ -383,15 +420,12 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                     const real dE = dt * wE, dW = dt * wW, dN = dt * wN, dS = dt * wS, dX = dt * wX;
                     const bool bs = b == 0, bn = b == M - 1;
                     const int pt = (q * M + b) * M + a;
+                    const real g = ghost_terms<M, real>(a, b, dW, dE, dS, dN, dX, c21_, c12_, c22, s0, t0, dx, dy);
                     store_vec4_shared<real>(rec0 + pt * 4, aw ? dE + dW : (ae ? real(0) : dE),
                                             ae ? dW + dE : (aw ? real(0) : dW), bs ? dN + dS : (bn ? real(0) : dN),
                                             bn ? dS + dN : (bs ? real(0) : dS));
                     store_vec4_shared<real>(rec1 + pt * 4, (aw || ae || bs || bn) ? real(0) : dX, real(1) + dt * wC,
-                                            dt * r, real(0));
-                    if (aw) { sq[2 * b] = dW; sq[2 * b + 1] = dX; }
-                    if (ae) { sq[2 * (M + b)] = dE; sq[2 * (M + b) + 1] = dX; }
-                    if (bs) { sq[2 * (2 * M + a)] = dS; sq[2 * (2 * M + a) + 1] = dX; }
-                    if (bn) { sq[2 * (3 * M + a)] = dN; sq[2 * (3 * M + a) + 1] = dX; }
+                                            dt * r + g, real(0));
                 }
             } else if (q < P) {
 #pragma unroll 1
@@ -478,7 +512,7 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
         const real sL = s0, sR = -s0, tB = t0, tT = -t0;
         const real s1 = s0 + dx, sM2 = -s0 - dx;              // s(1), s(M - 2)
 #pragma unroll 1
-        for (int sd = 0; sd < 4; ++sd) {
+        for (int sd = 0; sd < (mode == COEF_RECORDS ? 4 : 0); ++sd) {
 #pragma unroll 1
             for (int e = lane; e < P * M; e += 32) {
                 const int pq = e / M;
