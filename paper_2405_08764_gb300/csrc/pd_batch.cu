@@ -284,9 +284,10 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                 const real Yb = real(2) * c02 * ga - om * (c01 + real(2) * c02 * (tb + oy)) +
                                 f0 * (C0 + tb * (c01 + tb * c02));
                 real* o = rowq + e * 12;
+                // unfolded dt wS of the bottom row, dt wN of the top row (their ghost terms)
+                const real wsn = pb == 0 ? su : (pb == M - 1 ? nu_ : real(0));
                 store_vec4_shared<real>(o, nf, sf, crow, ib);
-                store_vec4_shared<real>(o + 4, tb, om, Yb, nu_);
-                store_vec4_shared<real>(o + 8, su, real(0), real(0), real(0));
+                store_vec4_shared<real>(o + 4, tb, om, Yb, wsn);
             }
             __syncwarp();
             // then each lane (q, a) holding a column walks down its micro rows
@@ -323,10 +324,9 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                 const real* rq = rowq + q * M * 12;
 #pragma unroll 1
                 for (int b = 0; b < M; ++b) {
-                    real nf, sf, crow, ib, tb, om, Yb, nu_, su, p1, p2, p3;
+                    real nf, sf, crow, ib, tb, om, Yb, wsn;
                     load_vec4_shared<real>(rq + b * 12, nf, sf, crow, ib);
-                    load_vec4_shared<real>(rq + b * 12 + 4, tb, om, Yb, nu_);
-                    load_vec4_shared<real>(rq + b * 12 + 8, su, p1, p2, p3);
+                    load_vec4_shared<real>(rq + b * 12 + 4, tb, om, Yb, wsn);
                     real Z = b2 * ib;
                     Z = fma(-nu, tb, Z);
                     Z = fma(-om, sa, Z);
@@ -336,7 +336,7 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                     const real x = redge ? real(0) : xin * ib;
                     const int pt = (q * M + b) * M + a;
                     // unfolded dt wX at (a, b) = xu ib
-                    const real g = ghost_terms<M, real>(a, b, wu, eu, su, nu_, xu * ib, c21, c12, c22, s0, t0, dx, dy);
+                    const real g = ghost_terms<M, real>(a, b, wu, eu, wsn, wsn, xu * ib, c21, c12, c22, s0, t0, dx, dy);
                     store_vec4_shared<real>(rec0 + pt * 4, ef, wf, nf, sf);
                     store_vec4_shared<real>(rec1 + pt * 4, x, ccol + crow, dt * r + g, real(0));
                 }
