@@ -119,11 +119,21 @@ __device__ __forceinline__ void stage_coeffs(const InstDev& I, const double* __r
     for (int r = 0; r < NC; ++r) {
         const int k = min(a + r * M, 8);
         const double P = gather(I.c2slot[k][0]), Q = gather(I.c2slot[k][1]), R = gather(I.c2slot[k][2]);
-        const double ck = fma(I.c2w[k][1], R, fma(I.c2w[k][0], Q, P)) * I.c2w[k][2];
-        if (writer && a + r * M < 9) {
-            cvq[k] = (real)ck;
-            if (k == 3) dq[0] = ck;
-            if (k == 5) dq[1] = ck;
+        // the combination of differences needs FP64 (it cancels); its scale is
+        // applied in the working precision (one FP64 multiply less per round on
+        // the FP32 path), in FP64 only where the MACRO reference bias reads c20, c02
+        const double cp = fma(I.c2w[k][1], R, fma(I.c2w[k][0], Q, P));
+        const bool writes = writer && a + r * M < 9;
+        if constexpr (sizeof(real) == 4) {
+            if (writes) cvq[k] = (real)cp * I.c2sf[k];
+        } else {
+            if (writes) cvq[k] = cp * I.c2w[k][2];
+        }
+        if (writes) {
+            if (I.restrict_mode == PD_RESTRICT_MACRO) {
+                if (k == 3) dq[0] = cp * I.c2w[k][2];
+                if (k == 5) dq[1] = cp * I.c2w[k][2];
+            }
             if (k == 8) dq[2] = x1[r];     // slot 8 is U(0, 0)
         }
     }
@@ -597,7 +607,8 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
         double bias = 0.0;
         if (I.restrict_mode == PD_RESTRICT_MACRO) bias = (I.dx * I.dx * dq[0] + I.dy * I.dy * dq[1]) * (1.0 / 6.0);
         double inc = fma((double)col, sc.x, bias * sc.y);
-        if (!isfinite(inc)) atomicOr(I.err, ERR_NONFINITE);
+        // a non-finite restricted change shows in the working-precision sum already
+        if (!isfinite(col) || !isfinite(bias)) atomicOr(I.err, ERR_NONFINITE);
         Un[(long long)j * I.nxp + i] = dq[2] + inc;
     }
 }

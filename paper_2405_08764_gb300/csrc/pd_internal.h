@@ -67,6 +67,7 @@ struct InstDev {
     // double -> float conversion issues on the slow FP64 pipe): K11, K12, K22,
     // v1, v2, f0, 1/dx, 1/dy, 1/dx^2, 1/dy^2, 1/(4 dx dy), dx, dy, hx, hy, dt
     float kf[16];
+    float c2sf[9];               // FP32 copies of the interpolant scales c2w[k][2]
     const void* arec_c;          // ADI line records, eta lines (8 per point, see pd_adi.cu)
     const void* arec_r;          // ADI line records, xi lines (8 per point, patch-transposed)
 };
@@ -79,6 +80,7 @@ inline void fill_float_consts(InstDev& I)
     const double v[16] = { I.K11, I.K12, I.K22, I.v1, I.v2, I.f0, I.inv_dx, I.inv_dy, I.inv_dx2, I.inv_dy2,
                            I.inv_4dxdy, I.dx, I.dy, I.hx, I.hy, I.dt };
     for (int k = 0; k < 16; ++k) I.kf[k] = (float)v[k];
+    for (int k = 0; k < 9; ++k) I.c2sf[k] = (float)I.c2w[k][2];
 }
 
 // Transformed coefficients (alpha, beta, gamma, nu, omega, phi) for constant K, v,

@@ -202,3 +202,19 @@ def test_full_size_batch_sampled_instances(Grid, orc):
         want = o.step(U0[a:a + i["n_macro"]], 0.0, o.dt_macro(), 3)
         err = np.linalg.norm(got[a:a + i["n_macro"]] - want) / np.linalg.norm(want)
         assert err <= 1e-4, (k, probs[k]["map"], probs[k]["n_xi"], probs[k]["m_xi"], err)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_batched_macro_reference_matches_oracle(Grid, orc, prec, tol):
+    """The printed restriction reference U0 = U_ij (MACRO) on the batched path:
+    the interpolant's c20, c02 enter the reference offset in FP64."""
+    probs = [dict(p, restrict="macro") for p in _c4_subset(6)]
+    g = Grid(probs, prec=prec)
+    U = g.init_field()
+    g.step(U, 0.0, 0.0, 5)
+    g.sync()
+    got = _split(g, U)
+    want = _oracle_runs(orc, probs, 5)
+    for k, (a, b) in enumerate(zip(got, want)):
+        err = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert err <= tol, (k, probs[k]["map"], probs[k]["m_xi"], err)
