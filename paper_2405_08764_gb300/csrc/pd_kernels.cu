@@ -530,26 +530,35 @@ restrict_kernel(const InstDev I, const real* __restrict__ w, const double* __res
     real* tw = tile + (size_t)ppb * mm;                       // [mm] weights
     for (int t = threadIdx.x; t < mm; t += blockDim.x) {
         const int b = t / I.mx, a = t - b * I.mx;
-        tw[t] = real(((a == 0 || a == I.mx - 1) ? 0.5 : 1.0) * ((b == 0 || b == I.my - 1) ? 0.5 : 1.0));
+        const real wa = (a == 0 || a == I.mx - 1) ? real(0.5) : real(1);
+        tw[t] = (b == 0 || b == I.my - 1) ? real(0.5) * wa : wa;
     }
     const int p0 = blockIdx.x * ppb;
     const int np = min(ppb, I.n_patch - p0);
+    // the bias of this thread's patch, requested before the staging loads
+    const int q = threadIdx.x >> 2, sub = threadIdx.x & 3;
+    const long long pg = (long long)I.p_off + p0 + q;
+    const double bq = (q < np && sub == 0) ? __ldg(bias + pg) : 0.0;
     const real* src = w + I.pt_off + (long long)p0 * mm;
     const int n = np * mm;
     constexpr int V = 16 / sizeof(real);
     if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(tile) & 15) == 0) {
+        // every 16-byte piece of the block's patches requested at once, straight
+        // into shared memory (no registers held while the loads are in flight)
         const int nv = n / V;
         const uint4* s4 = reinterpret_cast<const uint4*>(src);
         uint4* t4 = reinterpret_cast<uint4*>(tile);
-#pragma unroll 4
-        for (int e = threadIdx.x; e < nv; e += blockDim.x) t4[e] = s4[e];
+        for (int e = threadIdx.x; e < nv; e += blockDim.x) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(t4 + e);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(s4 + e) : "memory");
+        }
         for (int e = nv * V + threadIdx.x; e < n; e += blockDim.x) tile[e] = src[e];
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
 #pragma unroll 4
         for (int e = threadIdx.x; e < n; e += blockDim.x) tile[e] = src[e];
     }
     __syncthreads();
-    const int q = threadIdx.x >> 2, sub = threadIdx.x & 3;
     real acc = real(0);
     if (q < np) {
         const real* x = tile + q * mm;
@@ -558,8 +567,7 @@ restrict_kernel(const InstDev I, const real* __restrict__ w, const double* __res
     acc += __shfl_xor_sync(FULL, acc, 1);
     acc += __shfl_xor_sync(FULL, acc, 2);
     if (q < np && sub == 0) {
-        const long long pg = (long long)I.p_off + p0 + q;
-        double v = fma((double)acc, I.inv_nn, bias[pg]);
+        double v = fma((double)acc, I.inv_nn, bq);
         if (!isfinite(v)) atomicOr(I.err, ERR_NONFINITE);
         dU[pg] = v;
     }
@@ -567,20 +575,46 @@ restrict_kernel(const InstDev I, const real* __restrict__ w, const double* __res
 
 // eq. (Extrapolation) on interior nodes + Dirichlet data at t + dt_macro
 // (scale = dt_macro / tau, formed on the host: no FP64 division per node)
-__global__ void project_kernel(const InstDev I, double* __restrict__ U, const double* __restrict__ dU,
-                               double t_next, double scale)
+// Grid rows y (strided by gridDim.y): y < nrows is patch row jr = y, blockIdx.x a
+// chunk of kProjectPer * blockDim.x of its columns; the rows after those hold
+// chunks of the boundary nodes.  Each thread issues the loads of all its nodes
+// before the first update, so it keeps kProjectPer loads of U and dU in flight.
+// Dirichlet data at one boundary node, out of line: inlined, the FP64 solution
+// code is if-converted into the interior path of every warp
+__device__ __noinline__ void project_boundary_node(const InstDev& I, double* __restrict__ U, int q, double t_next)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < I.n_patch) {
-        int i, j, ic, jr;
-        patch_ij(I, k, i, j, ic, jr);
-        long long node = (long long)j * I.nxp + i;
-        U[node] = fma(scale, dU[(long long)I.p_off + k], U[node]);
-    } else if (k < I.n_patch + I.n_bnd) {
-        int q = k - I.n_patch;
-        int2 ij = I.bnd_ij[q];
-        double2 xy = I.bnd_xy[q];
-        U[(long long)ij.y * I.nxp + ij.x] = exact_solution(I.sol, xy.x, xy.y, t_next);
+    const int2 ij = I.bnd_ij[q];
+    const double2 xy = I.bnd_xy[q];
+    U[(long long)ij.y * I.nxp + ij.x] = exact_solution(I.sol, xy.x, xy.y, t_next);
+}
+
+constexpr int kProjectPer = 4;
+constexpr int kProjectBlock = 128;
+
+__global__ void __launch_bounds__(kProjectBlock)
+project_kernel(const InstDev I, double* __restrict__ U, const double* __restrict__ dU, double t_next, double scale,
+               int n_rows_total)
+{
+    for (int jr = blockIdx.y; jr < n_rows_total; jr += gridDim.y) {
+        if (jr < I.nrows) {
+            const int c0 = blockIdx.x * (kProjectPer * kProjectBlock) + threadIdx.x;
+            double* row = U + (long long)(1 + jr) * I.nxp + I.i0;
+            const double* drow = dU + (long long)I.p_off + (long long)jr * I.ncols;
+            double u[kProjectPer], d[kProjectPer];
+#pragma unroll
+            for (int k = 0; k < kProjectPer; ++k) {
+                const int ic = c0 + k * kProjectBlock;
+                if (ic < I.ncols) { u[k] = row[ic]; d[k] = __ldg(drow + ic); }
+            }
+#pragma unroll
+            for (int k = 0; k < kProjectPer; ++k) {
+                const int ic = c0 + k * kProjectBlock;
+                if (ic < I.ncols) row[ic] = fma(scale, d[k], u[k]);
+            }
+        } else {
+            const int q = ((jr - I.nrows) * gridDim.x + blockIdx.x) * kProjectBlock + threadIdx.x;
+            if (q < I.n_bnd) project_boundary_node(I, U, q, t_next);
+        }
     }
 }
 
@@ -864,8 +898,12 @@ cudaError_t launch_ab2(const InstDev& I, double* U, const double* dUn, const dou
 
 cudaError_t launch_project(const InstDev& I, double* U, const double* dU, double t, double dtm, cudaStream_t st)
 {
-    int n = I.n_patch + I.n_bnd;
-    project_kernel<<<(n + 127) / 128, 128, 0, st>>>(I, U, dU, t + dtm, dtm * I.inv_tau);
+    const unsigned gx = (unsigned)((I.ncols + kProjectPer * kProjectBlock - 1) / (kProjectPer * kProjectBlock));
+    const unsigned bnd_rows = (unsigned)(((long long)I.n_bnd + (long long)gx * kProjectBlock - 1) / ((long long)gx * kProjectBlock));
+    const int rows = I.nrows + (int)bnd_rows;
+    if (rows == 0) return cudaSuccess;
+    project_kernel<<<dim3(gx, (unsigned)std::min(rows, 65535)), kProjectBlock, 0, st>>>(I, U, dU, t + dtm,
+                                                                                      dtm * I.inv_tau, rows);
     return cudaGetLastError();
 }
 
