@@ -192,6 +192,155 @@ __device__ __forceinline__ real ghost_terms(int a, int b, real dW, real dE, real
     return g;
 }
 
+// Burst records of a patch group whose instance has per-point coefficient
+// records (heterogeneous coefficients): out of line, so that the table-mode
+// set-up the uniform instances run is compiled without this path's registers.
+template <typename real>
+struct RecSetup {
+    const real* cv_s;
+    real* rec0;
+    real* rec1;
+    real* side;
+    const real* rect;
+    real idx, idy, idx2, idy2, i4dxdy, hdx, hdy, s0, t0, dx, dy, sT, dt;
+    int recrow, nvalid;
+    bool central;
+};
+
+template <int M, typename real>
+__device__ __noinline__ void records_setup(const RecSetup<real> k, int lane)
+{
+    constexpr int P = 32 / M;
+    constexpr int npt = P * M * M;
+    const real* cv_s = k.cv_s;
+    real* rec0 = k.rec0;
+    real* rec1 = k.rec1;
+    real* side = k.side;
+    const real* rect = k.rect;
+    const real idx = k.idx, idy = k.idy, idx2 = k.idx2, idy2 = k.idy2, i4dxdy = k.i4dxdy;
+    const real hdx = k.hdx, hdy = k.hdy, s0 = k.s0, t0 = k.t0, dx = k.dx, dy = k.dy, sT = k.sT, dt = k.dt;
+    const int recrow = k.recrow, nvalid = k.nvalid;
+    const bool central = k.central;
+    // general point: record of micro point (pa, pb) of patch pq from its
+    // transformed coefficients, written at pt; weights and the forcing of
+    // the quadratic lift as point_weights_k and burst_forcing (without its
+    // ghost terms), the upwind choice by selects
+    auto emit = [&](int pt, int pq, int pa, int pb, real al, real be, real ga, real nu, real om, real ph,
+                    real G) {
+        const real* c9 = cv_s + pq * 12;
+        real C0, c10, c01, c20, c11, c02, c21_, c12_;
+        load_vec4_shared<real>(c9, C0, c10, c01, c20);
+        load_vec4_shared<real>(c9 + 4, c11, c02, c21_, c12_);
+        const real ax = al * idx2, gy = ga * idy2;
+        real wE, wW, wN, wS, ox, oy;
+        real wC = -real(2) * ax - real(2) * gy + ph;
+        const real wX = be * i4dxdy;
+        if (central) {
+            const real hn = real(0.5) * nu * idx, ho = real(0.5) * om * idy;
+            wE = ax - hn; wW = ax + hn; wN = gy - ho; wS = gy + ho;
+            ox = real(0); oy = real(0);
+        } else {
+            const real nx = nu * idx, oyv = om * idy;
+            const bool pn = nu > real(0), po = om > real(0);
+            wW = pn ? ax + nx : ax;
+            wE = pn ? ax : ax - nx;
+            wC = pn ? wC - nx : wC + nx;
+            ox = pn ? -hdx : hdx;
+            wS = po ? gy + oyv : gy;
+            wN = po ? gy : gy - oyv;
+            wC = po ? wC - oyv : wC + oyv;
+            oy = po ? -hdy : hdy;
+        }
+        const real sa = s0 + real(pa) * dx, tb = t0 + real(pb) * dy;
+        const real u0 = C0 + sa * (c10 + sa * c20 + tb * c11) + tb * (c01 + tb * c02);
+        const real ux = c10 + real(2) * c20 * (sa + ox) + c11 * tb;
+        const real uy = c01 + real(2) * c02 * (tb + oy) + c11 * sa;
+        const real r = real(2) * c20 * al + c11 * be + real(2) * c02 * ga - nu * ux - om * uy + ph * u0 + sT * G;
+        const real dE = dt * wE, dW = dt * wW, dN = dt * wN, dS = dt * wS, dX = dt * wX;
+        const bool aw = pa == 0, ae = pa == M - 1, bs = pb == 0, bn = pb == M - 1;
+        const real e = aw ? dE + dW : (ae ? real(0) : dE);
+        const real ww = ae ? dW + dE : (aw ? real(0) : dW);
+        const real n = bs ? dN + dS : (bn ? real(0) : dN);
+        const real sw = bn ? dS + dN : (bs ? real(0) : dS);
+        const real x = (aw || ae || bs || bn) ? real(0) : dX;
+        store_vec4_shared<real>(rec0 + pt * 4, e, ww, n, sw);
+        store_vec4_shared<real>(rec1 + pt * 4, x, real(1) + dt * wC, dt * r, dt * G);
+        real* sq = side + pq * 8 * M;
+        if (aw) { sq[2 * pb] = dW; sq[2 * pb + 1] = dX; }
+        if (ae) { sq[2 * (M + pb)] = dE; sq[2 * (M + pb) + 1] = dX; }
+        if (bs) { sq[2 * (2 * M + pa)] = dS; sq[2 * (2 * M + pa) + 1] = dX; }
+        if (bn) { sq[2 * (3 * M + pa)] = dN; sq[2 * (3 * M + pa) + 1] = dX; }
+    };
+    {
+        // per-point coefficient records: every lane takes points of the group in turn
+#pragma unroll 1
+        for (int pt = lane; pt < npt; pt += 32) {
+            const int pq = pt / (M * M);
+            const int rem = pt - pq * (M * M);
+            const int pb = rem / M;
+            const int pa = rem - pb * M;
+            if (pq < nvalid) {
+                const real* pr = rect + pb * recrow + (pq * M + pa) * 8;
+                emit(pt, pq, pa, pb, pr[0], pr[1], pr[2], pr[3], pr[4], pr[5], pr[6]);
+            } else {
+                store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
+                store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
+            }
+        }
+    }
+    __syncwarp();
+    // ghost terms: a ghost neighbour (a', b') outside the patch adds
+    // weight * (ghost value - lift there) (ghost_offset); the diagonal
+    // ghosts of the cross term are taken by the W/E pass when a' is outside,
+    // else by the S/N pass.
+    const real sL = s0, sR = -s0, tB = t0, tT = -t0;
+    const real s1 = s0 + dx, sM2 = -s0 - dx;              // s(1), s(M - 2)
+#pragma unroll 1
+    for (int sd = 0; sd < 4; ++sd) {
+#pragma unroll 1
+        for (int e = lane; e < P * M; e += 32) {
+            const int pq = e / M;
+            const int p = e - pq * M;
+            if (pq >= nvalid) continue;
+            const real* c9 = cv_s + pq * 12;
+            const real c21 = c9[6], c12 = c9[7], c22 = c9[8];
+            const real* sq = side + (size_t)pq * 8 * M + 2 * (sd * M + p);
+            const real wg = sq[0], wx = sq[1];
+            const real lo = p >= 1 ? real(1) : real(0), hi = p <= M - 2 ? real(1) : real(0);
+            real g;
+            int pt;
+            if (sd < 2) {
+                // W (a = 0) / E (a = M - 1): ghosts at a' = -1 / M, rows b - 1, b, b + 1
+                const real sg = sd == 0 ? real(-1) : real(1);
+                const real se = sd == 0 ? sL : sR;
+                const real sin_ = sd == 0 ? s1 : sM2;          // s(a_in) for the eta part of a corner ghost
+                const real tb = t0 + real(p) * dy;
+                const real gm = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb);
+                const real gdn = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb - dy) -
+                                 (real(1) - lo) * real(2) * dy * gap_eta(c21, c12, c22, sin_, tB);
+                const real gup = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb + dy) +
+                                 (real(1) - hi) * real(2) * dy * gap_eta(c21, c12, c22, sin_, tT);
+                // W: +wX go(-1, b-1) - wX go(-1, b+1); E: +wX go(M, b+1) - wX go(M, b-1)
+                g = wg * gm + sg * wx * (gup - gdn);
+                pt = (pq * M + p) * M + (sd == 0 ? 0 : M - 1);
+            } else {
+                // S (b = 0) / N (b = M - 1): ghosts at b' = -1 / M, columns a - 1, a, a + 1 inside the patch
+                const real sg = sd == 2 ? real(-1) : real(1);
+                const real te = sd == 2 ? tB : tT;
+                const real sa = s0 + real(p) * dx;
+                const real gm = sg * real(2) * dy * gap_eta(c21, c12, c22, sa, te);
+                const real gl = sg * real(2) * dy * gap_eta(c21, c12, c22, sa - dx, te);
+                const real gr = sg * real(2) * dy * gap_eta(c21, c12, c22, sa + dx, te);
+                // S: +wX go(a-1, -1) - wX go(a+1, -1); N: +wX go(a+1, M) - wX go(a-1, M)
+                g = wg * gm + sg * wx * (hi * gr - lo * gl);
+                pt = (pq * M + (sd == 2 ? 0 : M - 1)) * M + p;
+            }
+            rec1[(size_t)pt * 4 + 2] += g;
+        }
+        __syncwarp();
+    }
+}
+
 template <int M, bool TSRC, typename real>
 __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it, const BatchArgs& A, int lane,
                                            unsigned char* stage)
@@ -253,7 +402,6 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                                : nullptr;
         const int recrow = I.ncols * M * 8;                   // one micro row of the patch row, in values
         real* side = reinterpret_cast<real*>(stage + S::side_off);
-        const int npt = P * M * M;
         if (mode == COEF_SEPARABLE) {
             // Separable map x = X(xi), y = Y(eta) with constant K, v, f: alpha, nu
             // and the xi-weights depend on the column only, gamma, omega and the
@@ -446,125 +594,10 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                 }
             }
         } else {
-            // general point: record of micro point (pa, pb) of patch pq from its
-            // transformed coefficients, written at pt; weights and the forcing of
-            // the quadratic lift as point_weights_k and burst_forcing (without its
-            // ghost terms), the upwind choice by selects
-            auto emit = [&](int pt, int pq, int pa, int pb, real al, real be, real ga, real nu, real om, real ph,
-                            real G) {
-                const real* c9 = cv_s + pq * 12;
-                real C0, c10, c01, c20, c11, c02, c21_, c12_;
-                load_vec4_shared<real>(c9, C0, c10, c01, c20);
-                load_vec4_shared<real>(c9 + 4, c11, c02, c21_, c12_);
-                const real ax = al * idx2, gy = ga * idy2;
-                real wE, wW, wN, wS, ox, oy;
-                real wC = -real(2) * ax - real(2) * gy + ph;
-                const real wX = be * i4dxdy;
-                if (central) {
-                    const real hn = real(0.5) * nu * idx, ho = real(0.5) * om * idy;
-                    wE = ax - hn; wW = ax + hn; wN = gy - ho; wS = gy + ho;
-                    ox = real(0); oy = real(0);
-                } else {
-                    const real nx = nu * idx, oyv = om * idy;
-                    const bool pn = nu > real(0), po = om > real(0);
-                    wW = pn ? ax + nx : ax;
-                    wE = pn ? ax : ax - nx;
-                    wC = pn ? wC - nx : wC + nx;
-                    ox = pn ? -hdx : hdx;
-                    wS = po ? gy + oyv : gy;
-                    wN = po ? gy : gy - oyv;
-                    wC = po ? wC - oyv : wC + oyv;
-                    oy = po ? -hdy : hdy;
-                }
-                const real sa = s0 + real(pa) * dx, tb = t0 + real(pb) * dy;
-                const real u0 = C0 + sa * (c10 + sa * c20 + tb * c11) + tb * (c01 + tb * c02);
-                const real ux = c10 + real(2) * c20 * (sa + ox) + c11 * tb;
-                const real uy = c01 + real(2) * c02 * (tb + oy) + c11 * sa;
-                const real r = real(2) * c20 * al + c11 * be + real(2) * c02 * ga - nu * ux - om * uy + ph * u0 + sT * G;
-                const real dE = dt * wE, dW = dt * wW, dN = dt * wN, dS = dt * wS, dX = dt * wX;
-                const bool aw = pa == 0, ae = pa == M - 1, bs = pb == 0, bn = pb == M - 1;
-                const real e = aw ? dE + dW : (ae ? real(0) : dE);
-                const real ww = ae ? dW + dE : (aw ? real(0) : dW);
-                const real n = bs ? dN + dS : (bn ? real(0) : dN);
-                const real sw = bn ? dS + dN : (bs ? real(0) : dS);
-                const real x = (aw || ae || bs || bn) ? real(0) : dX;
-                store_vec4_shared<real>(rec0 + pt * 4, e, ww, n, sw);
-                store_vec4_shared<real>(rec1 + pt * 4, x, real(1) + dt * wC, dt * r, dt * G);
-                real* sq = side + pq * 8 * M;
-                if (aw) { sq[2 * pb] = dW; sq[2 * pb + 1] = dX; }
-                if (ae) { sq[2 * (M + pb)] = dE; sq[2 * (M + pb) + 1] = dX; }
-                if (bs) { sq[2 * (2 * M + pa)] = dS; sq[2 * (2 * M + pa) + 1] = dX; }
-                if (bn) { sq[2 * (3 * M + pa)] = dN; sq[2 * (3 * M + pa) + 1] = dX; }
-            };
-            {
-                // per-point coefficient records: every lane takes points of the group in turn
-#pragma unroll 1
-                for (int pt = lane; pt < npt; pt += 32) {
-                    const int pq = pt / (M * M);
-                    const int rem = pt - pq * (M * M);
-                    const int pb = rem / M;
-                    const int pa = rem - pb * M;
-                    if (pq < nvalid) {
-                        const real* pr = rect + pb * recrow + (pq * M + pa) * 8;
-                        emit(pt, pq, pa, pb, pr[0], pr[1], pr[2], pr[3], pr[4], pr[5], pr[6]);
-                    } else {
-                        store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
-                        store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
-                    }
-                }
-            }
+            records_setup<M, real>(RecSetup<real>{ cv_s, rec0, rec1, side, rect, idx, idy, idx2, idy2, i4dxdy, hdx, hdy,
+                                                   s0, t0, dx, dy, sT, dt, recrow, nvalid, central }, lane);
         }
         __syncwarp();
-        // ghost terms: a ghost neighbour (a', b') outside the patch adds
-        // weight * (ghost value - lift there) (ghost_offset); the diagonal
-        // ghosts of the cross term are taken by the W/E pass when a' is outside,
-        // else by the S/N pass.
-        const real sL = s0, sR = -s0, tB = t0, tT = -t0;
-        const real s1 = s0 + dx, sM2 = -s0 - dx;              // s(1), s(M - 2)
-#pragma unroll 1
-        for (int sd = 0; sd < (mode == COEF_RECORDS ? 4 : 0); ++sd) {
-#pragma unroll 1
-            for (int e = lane; e < P * M; e += 32) {
-                const int pq = e / M;
-                const int p = e - pq * M;
-                if (pq >= nvalid) continue;
-                const real* c9 = cv_s + pq * 12;
-                const real c21 = c9[6], c12 = c9[7], c22 = c9[8];
-                const real* sq = side + (size_t)pq * 8 * M + 2 * (sd * M + p);
-                const real wg = sq[0], wx = sq[1];
-                const real lo = p >= 1 ? real(1) : real(0), hi = p <= M - 2 ? real(1) : real(0);
-                real g;
-                int pt;
-                if (sd < 2) {
-                    // W (a = 0) / E (a = M - 1): ghosts at a' = -1 / M, rows b - 1, b, b + 1
-                    const real sg = sd == 0 ? real(-1) : real(1);
-                    const real se = sd == 0 ? sL : sR;
-                    const real sin_ = sd == 0 ? s1 : sM2;          // s(a_in) for the eta part of a corner ghost
-                    const real tb = t0 + real(p) * dy;
-                    const real gm = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb);
-                    const real gdn = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb - dy) -
-                                     (real(1) - lo) * real(2) * dy * gap_eta(c21, c12, c22, sin_, tB);
-                    const real gup = sg * real(2) * dx * gap_xi(c21, c12, c22, se, tb + dy) +
-                                     (real(1) - hi) * real(2) * dy * gap_eta(c21, c12, c22, sin_, tT);
-                    // W: +wX go(-1, b-1) - wX go(-1, b+1); E: +wX go(M, b+1) - wX go(M, b-1)
-                    g = wg * gm + sg * wx * (gup - gdn);
-                    pt = (pq * M + p) * M + (sd == 0 ? 0 : M - 1);
-                } else {
-                    // S (b = 0) / N (b = M - 1): ghosts at b' = -1 / M, columns a - 1, a, a + 1 inside the patch
-                    const real sg = sd == 2 ? real(-1) : real(1);
-                    const real te = sd == 2 ? tB : tT;
-                    const real sa = s0 + real(p) * dx;
-                    const real gm = sg * real(2) * dy * gap_eta(c21, c12, c22, sa, te);
-                    const real gl = sg * real(2) * dy * gap_eta(c21, c12, c22, sa - dx, te);
-                    const real gr = sg * real(2) * dy * gap_eta(c21, c12, c22, sa + dx, te);
-                    // S: +wX go(a-1, -1) - wX go(a+1, -1); N: +wX go(a+1, M) - wX go(a-1, M)
-                    g = wg * gm + sg * wx * (hi * gr - lo * gl);
-                    pt = (pq * M + (sd == 2 ? 0 : M - 1)) * M + p;
-                }
-                rec1[(size_t)pt * 4 + 2] += g;
-            }
-            __syncwarp();
-        }
     }
 
     // ---- phase 3: K micro steps, lane (q, a) holding micro column a of patch q
@@ -613,7 +646,9 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     }
 }
 
-__device__ __forceinline__ void boundary_item(const InstDev& I, const BatchItem& it, const BatchArgs& A, int lane)
+// Out of line: inlined, the FP64 solution code of the boundary items joins the
+// patch items' path (measured 1 % slower on the uneven batch).
+__device__ __noinline__ void boundary_item(const InstDev& I, const BatchItem& it, const BatchArgs& A, int lane)
 {
     double* Un = (A.parity ? A.Ubase : A.Sbase) + I.u_off;
     int k = it.jr * 32 + lane;

@@ -375,10 +375,8 @@ __device__ __forceinline__ real burst_forcing(const Poly<real>& c, const Geo& g,
     return r;
 }
 
-// The two parts of burst_forcing: the closed form of L_h(u_lift) + s(T) G
-// without ghost neighbours, and the ghost-neighbour terms (non-zero only at the
-// patch's edge points), so that a kernel can form the first at every point and
-// the second at the edge points only.
+// burst_forcing without its ghost-neighbour terms: the closed form of
+// L_h(u_lift) + s(T) G, for kernels that form the ghost terms their own way.
 template <typename real, typename Geo>
 __device__ __forceinline__ real burst_forcing_base(const Poly<real>& c, const Geo& g, int a, int b,
                                                    real al, real be, real ga, real nu, real om, real ph,
@@ -391,24 +389,6 @@ __device__ __forceinline__ real burst_forcing_base(const Poly<real>& c, const Ge
     return real(2) * c.c20 * al + c.c11 * be + real(2) * c.c02 * ga - nu * ux - om * uy + ph * u0 + sT * G;
 }
 
-template <typename real, typename Geo>
-__device__ __forceinline__ real burst_forcing_ghost(const Poly<real>& c, const Geo& g, int a, int b, real be,
-                                                    const PointW<real>& w)
-{
-    real r = real(0);
-    if (a == 0) r += w.wW * ghost_offset(c, g, -1, b);
-    if (a == g.nx) r += w.wE * ghost_offset(c, g, g.nx + 1, b);
-    if (b == 0) r += w.wS * ghost_offset(c, g, a, -1);
-    if (b == g.ny) r += w.wN * ghost_offset(c, g, a, g.ny + 1);
-    if (be != real(0)) {
-        auto out = [&](int ap, int bp) { return ap < 0 || ap > g.nx || bp < 0 || bp > g.ny; };
-        if (out(a + 1, b + 1)) r += w.wX * ghost_offset(c, g, a + 1, b + 1);
-        if (out(a - 1, b - 1)) r += w.wX * ghost_offset(c, g, a - 1, b - 1);
-        if (out(a + 1, b - 1)) r -= w.wX * ghost_offset(c, g, a + 1, b - 1);
-        if (out(a - 1, b + 1)) r -= w.wX * ghost_offset(c, g, a - 1, b + 1);
-    }
-    return r;
-}
 
 // time factor s(t) of the source
 __device__ __forceinline__ double time_factor(int kind, double c, double t)

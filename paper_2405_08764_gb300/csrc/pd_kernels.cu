@@ -242,6 +242,32 @@ __device__ __forceinline__ long long rec_index(const InstDev& I, int jr, int ic,
     return ((long long)(jr * I.my + b) * I.ncols + ic) * I.mx + a;
 }
 
+// Ghost-neighbour terms of the burst forcing at micro point (a, b): weight *
+// (ghost value - lift there), non-zero at edge points only.  The W/E/S/N ghosts
+// are formed for every point without branches (zero weights inside the patch):
+// the W/E ghost offset is -+2 dx gap_xi at the left/right edge s, the S/N one
+// -+2 dy gap_eta at the bottom/top edge t; the diagonal ghosts of the cross
+// term (beta != 0, edge points only) as ghost_offset.
+template <typename real, typename Geo>
+__device__ __forceinline__ real lift_ghost_terms(const Poly<real>& c, const Geo& g, int a, int b, real be,
+                                                 const PointW<real>& w)
+{
+    const real sa = g.s(a), tb = g.t(b);
+    const real se = a == 0 ? real(-0.5) * g.hx : real(0.5) * g.hx;
+    const real te = b == 0 ? real(-0.5) * g.hy : real(0.5) * g.hy;
+    const real wx = a == 0 ? -w.wW : (a == g.nx ? w.wE : real(0));
+    const real wy = b == 0 ? -w.wS : (b == g.ny ? w.wN : real(0));
+    real r = wx * (real(2) * g.dx * edge_gap_xi(c, se, tb)) + wy * (real(2) * g.dy * edge_gap_eta(c, sa, te));
+    if (be != real(0) && (a == 0 || a == g.nx || b == 0 || b == g.ny)) {
+        auto out = [&](int ap, int bp) { return ap < 0 || ap > g.nx || bp < 0 || bp > g.ny; };
+        if (out(a + 1, b + 1)) r += w.wX * ghost_offset(c, g, a + 1, b + 1);
+        if (out(a - 1, b - 1)) r += w.wX * ghost_offset(c, g, a - 1, b - 1);
+        if (out(a + 1, b - 1)) r -= w.wX * ghost_offset(c, g, a + 1, b - 1);
+        if (out(a - 1, b + 1)) r -= w.wX * ghost_offset(c, g, a - 1, b + 1);
+    }
+    return r;
+}
+
 // lift of several patches per block (ppb <= 32, so that every phase keeps the
 // block's threads busy): interpolant coefficients
 // (FP64, nine threads per patch), then per micro point the lifted value u0
@@ -250,7 +276,7 @@ __device__ __forceinline__ long long rec_index(const InstDev& I, int jr, int ic,
 // A = C0 + c10 s + c20 s^2, B = c01 + c11 s, Q = c02 t^2 (one FP64 fma and one
 // add per point).
 template <typename real>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, (sizeof(real) == 4 ? 4 : 2))
 lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restrict__ tab, double* u0,
             real* r_out, real* w_out, double* edge, double* bias_out, int edge_stride, int ppb)
 {
@@ -266,7 +292,6 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
     __shared__ long long recb_s[PPB];        // record index of point (0, 0) of every patch
     __shared__ long long ob_s[PPB];          // micro-state index of point (0, 0)
     __shared__ int ab_s[1024];               // (b << 16) | a of in-patch point tl
-    __shared__ int eab_s[128];               // (b << 16) | a of the patch's edge points
     __shared__ int se_s[4 * 34];             // (side << 8) | e of edge entry tl
     const int p0 = blockIdx.x * ppb;
     const int mm = I.mx * I.my;
@@ -291,16 +316,6 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
     for (int t = threadIdx.x; t < 4 * edge_stride; t += blockDim.x) {
         const int side = t / edge_stride;
         se_s[t] = (side << 8) | (t - side * edge_stride);
-    }
-    // edge points: bottom row, top row, then the left and right columns without corners
-    const int n_edge = 2 * I.mx + 2 * (I.my - 2);
-    for (int t = threadIdx.x; t < n_edge; t += blockDim.x) {
-        int a, b;
-        if (t < I.mx) { a = t; b = 0; }
-        else if (t < 2 * I.mx) { a = t - I.mx; b = I.my - 1; }
-        else if (t < 2 * I.mx + I.my - 2) { a = 0; b = t - 2 * I.mx + 1; }
-        else { a = I.mx - 1; b = t - 2 * I.mx - (I.my - 2) + 1; }
-        eab_s[t] = (b << 16) | a;
     }
     for (int t = threadIdx.x; t < ppb; t += blockDim.x) {
         int i = 0, j = 0, ic = 0, jr = 0;
@@ -397,46 +412,12 @@ lift_kernel(const InstDev I, const double* __restrict__ U, const double* __restr
             const long long o = ob_s[q] + tl;
             u0[o] = fma(gt[b + 1], tabB[q][a], tabA[q][a] + tabQ[q][b]);
             PointW<real> pw = point_weights_k<real>(I, kc, v[0], v[1], v[2], v[3], v[4], v[5]);
-            // the ghost-neighbour terms of the edge points follow in their own loop,
-            // so that no warp runs the edge cases of burst_forcing for interior points
-            r_out[o] = burst_forcing_base<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw);
+            r_out[o] = burst_forcing_base<real>(cr, gr, a, b, v[0], v[1], v[2], v[3], v[4], v[5], v[6], sT, pw) +
+                       lift_ghost_terms<real>(cr, gr, a, b, v[1], pw);
             w_out[o] = real(0);
         }
         tl += blockDim.x;
         while (tl >= mm) { tl -= mm; ++q; }
-    }
-    __syncthreads();     // the forcing of every point is written before its edge terms are added
-    {
-        int qe = 0, te = threadIdx.x;
-        while (te >= n_edge) { te -= n_edge; ++qe; }
-        for (; qe < ppb; ) {
-            const int p = p0 + qe;
-            if (p < I.n_patch) {
-                const real* cq = csr[qe];
-                real c0, c1, c2, c3, c4, c5, c6, c7, c8, c9, c10, c11;
-                load_vec4_shared(cq, c0, c1, c2, c3);
-                load_vec4_shared(cq + 4, c4, c5, c6, c7);
-                load_vec4_shared(cq + 8, c8, c9, c10, c11);
-                (void)c9; (void)c10; (void)c11;
-                const Poly<real> cr = { c0, c1, c2, c3, c4, c5, c6, c7, c8 };
-                const int ab = eab_s[te];
-                const int b = ab >> 16, a = ab & 0xffff;
-                real v[8];
-                if (I.coef_mode != COEF_RECORDS) {
-                    const int4 pq = pij_s[qe];
-                    table_coeffs_k<real>(I, kc, pq.z, a, pq.w, b, v);
-                } else {
-                    const real* rr = rec + (recb_s[qe] + b * rowstride + a) * 8;
-                    load_vec4<real>(rr, v[0], v[1], v[2], v[3]);
-                    load_vec4<real>(rr + 4, v[4], v[5], v[6], v[7]);
-                }
-                const PointW<real> pw = point_weights_k<real>(I, kc, v[0], v[1], v[2], v[3], v[4], v[5]);
-                const long long o = ob_s[qe] + b * I.mx + a;
-                r_out[o] += burst_forcing_ghost<real>(cr, gr, a, b, v[1], pw);
-            }
-            te += blockDim.x;
-            while (te >= n_edge) { te -= n_edge; ++qe; }
-        }
     }
     // edge data of eq. (edge) = d/dxi, d/deta of the interpolant P at the edges
     // (dense over (patch, side, entry))
