@@ -155,11 +155,14 @@ refresh_kernel(const InstDev I, const double* __restrict__ D, const real* __rest
         }
         const real be = cc[1];
         const PointW<real> w = point_weights_k<real>(I, kc, cc[0], be, cc[2], cc[3], cc[4], cc[5]);
-        real v = real(0);
-        if (a == 0) v += w.wW * ghost_delta(c, g, -1, b);
-        if (a == nx) v += w.wE * ghost_delta(c, g, nx + 1, b);
-        if (b == 0) v += w.wS * ghost_delta(c, g, a, -1);
-        if (b == ny) v += w.wN * ghost_delta(c, g, a, ny + 1);
+        // W/E and S/N ghosts without branches: the W/E ghost changes by -+2 dx d/dxi
+        // at the left/right edge s, the S/N ghost by -+2 dy d/deta at the bottom/top
+        // edge t (zero weight on the sides the point is not on)
+        const real se = a == 0 ? real(-0.5) * g.hx : real(0.5) * g.hx;
+        const real te = b == 0 ? real(-0.5) * g.hy : real(0.5) * g.hy;
+        const real wx = a == 0 ? -w.wW : (a == nx ? w.wE : real(0));
+        const real wy = b == 0 ? -w.wS : (b == ny ? w.wN : real(0));
+        real v = wx * (real(2) * g.dx * dxi_poly(c, se, g.t(b))) + wy * (real(2) * g.dy * deta_poly(c, g.s(a), te));
         if (be != real(0)) {
             auto out = [&](int ap, int bp) { return ap < 0 || ap > nx || bp < 0 || bp > ny; };
             if (out(a + 1, b + 1)) v += w.wX * ghost_delta(c, g, a + 1, b + 1);
