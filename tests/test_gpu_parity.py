@@ -154,6 +154,52 @@ def test_burst_and_restrict_match_oracle(env, orc, name, prec):
     assert np.abs(dU - dwant).max() <= tol * max(np.abs(dwant).max(), 1e-300)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_separate_passes_on_a_grid_of_two_instances(env, orc, prec):
+    """pd_lift, pd_micro_burst, pd_restrict and pd_project on a two-instance grid
+    whose second instance's micro points start 81 points in, off a 16-byte
+    boundary (the restriction stages such a block with plain loads, the first
+    instance's 81 points through its 16-byte copies and a one-point tail): each
+    instance matches the oracle to the one-instance tolerances."""
+    pa, pb = CASES["tiny"], CASES["p412"]
+    oa, ob = orc.Oracle(pa), orc.Oracle(pb)
+    g = env([pa, pb], prec=prec)
+    ia, ib = g.info(0), g.info(1)
+    assert ib["point_offset"] == oa.n_patch * oa.mx * oa.my and ib["point_offset"] % 4 != 0
+    Ua, Ub = _rand_state(oa, pa), _rand_state(ob, pb)
+    U = np.zeros(g.n_macro_total)
+    U[ia["u_offset"]:ia["u_offset"] + oa.n_macro] = Ua
+    U[ib["u_offset"]:ib["u_offset"] + ob.n_macro] = Ub
+    Ud = torch.tensor(U, device="cuda")
+    st = g.new_state()
+    g.lift(Ud, 0.21, st)
+    K = min(pa["k_micro"], pb["k_micro"])
+    g.micro_burst(st, 0.21, K)
+    dU = g.restrict(st).cpu().numpy()
+    tol = 1e-9 if prec == "fp64" else 2e-5
+    dwant = []
+    for k, (o, Uk, info) in enumerate(((oa, Ua, ia), (ob, Ub, ib))):
+        v = g.state_views(st, k)
+        u0, _ = o.lift(Uk)
+        np.testing.assert_allclose(v["u0"].cpu().numpy().reshape(u0.shape), u0, rtol=0,
+                                   atol=1e-13 * np.abs(u0).max())
+        want = o.burst(Uk, 0.21, K, info["dt_micro"], "split")
+        w = v["w"].cpu().numpy().astype(np.float64)
+        assert np.abs(w - want).max() <= tol * np.abs(want).max(), (k, prec)
+        dk = o.restrict(Uk, want, "split")
+        po = info["patch_offset"]
+        got = dU[po:po + o.n_patch]
+        assert np.abs(got - dk).max() <= tol * max(np.abs(dk).max(), 1e-300), (k, prec)
+        dwant.append((o, Uk, info, dk))
+    dUd = torch.tensor(dU, device="cuda")
+    g.project(Ud, dUd, 0.3, 0.01)
+    Uo = Ud.cpu().numpy()
+    for o, Uk, info, _ in dwant:
+        po, uo = info["patch_offset"], info["u_offset"]
+        want = o.project(Uk, dU[po:po + o.n_patch], 0.3, 0.01, info["tau"])
+        np.testing.assert_allclose(Uo[uo:uo + o.n_macro], want, rtol=1e-14, atol=1e-15)
+
+
 @pytest.mark.parametrize("name", ["c1", "p411", "c3s", "polar_aniso"])
 def test_project_matches_oracle(env, orc, name):
     p = CASES[name]
