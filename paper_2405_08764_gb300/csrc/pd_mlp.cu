@@ -110,13 +110,13 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) { f32x2 d; asm(
 __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) { f32x2 d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
 __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) { f32x2 d; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
 
-// gelu_fast of (x0 + b0, x1 + b1) as a pair: x (1 + 0.044715 x^2) C, tanh by
+// gelu_fast of (x0 + b0, x1 + b1) as a pair: u = x (C + 0.044715 C x^2), tanh by
 // tanh.approx per element, x (1/2 + t/2)
 __device__ __forceinline__ void gelu_fast2(float& x0, float& x1, float b0, float b1)
 {
+    constexpr float kC = 0.7978845608028654f, kC3 = 0.044715f * 0.7978845608028654f;
     const f32x2 x = add2(pk2(x0, x1), pk2(b0, b1));
-    const f32x2 p = mul2(x, fma2(mul2(x, x), pk2(0.044715f, 0.044715f), pk2(1.0f, 1.0f)));
-    const f32x2 u = mul2(p, pk2(0.7978845608028654f, 0.7978845608028654f));
+    const f32x2 u = mul2(x, fma2(mul2(x, x), pk2(kC3, kC3), pk2(kC, kC)));
     float u0, u1;
     upk2(u, u0, u1);
     const f32x2 h = fma2(pk2(tanh_fast(u0), tanh_fast(u1)), pk2(0.5f, 0.5f), pk2(0.5f, 0.5f));
@@ -680,21 +680,44 @@ __device__ __forceinline__ void epi_hidden32(const uint32_t (&u)[32], int col0, 
     }
 }
 
-// Output-layer epilogue: part + sum over 32 columns of w4 * GELU(acc + b3), in
-// column order.
+// GELU of a pair with the accurate tanh of tanh_acc (exp2 and reciprocal per
+// element, the rest on packed FP32 pairs): x (1/2 + t/2), t = 1 - 2 / (exp(2u) + 1),
+// u = C x (1 + 0.044715 x^2)
+__device__ __forceinline__ f32x2 gelu_acc2(f32x2 x)
+{
+    constexpr float kU2 = 0.7978845608028654f * 2.8853900817779268f;   // C * 2 / ln 2
+    constexpr float kU23 = 0.044715f * kU2;
+    const f32x2 z = mul2(x, fma2(mul2(x, x), pk2(kU23, kU23), pk2(kU2, kU2)));
+    float z0, z1, e0, e1;
+    upk2(z, z0, z1);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e0) : "f"(z0));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(z1));
+    float d0, d1, r0, r1;
+    upk2(add2(pk2(e0, e1), pk2(1.0f, 1.0f)), d0, d1);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(d0));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(d1));
+    const f32x2 t = fma2(pk2(r0, r1), pk2(-2.0f, -2.0f), pk2(1.0f, 1.0f));
+    return mul2(x, fma2(t, pk2(0.5f, 0.5f), pk2(0.5f, 0.5f)));
+}
+
+// Output-layer epilogue: part + sum over 32 columns of w4 * GELU(acc + b3), the
+// even and odd columns accumulated as one packed pair
 __device__ __forceinline__ float epi_dot32(const uint32_t (&u)[32], int col0, const float* b3, const float* w4, float part)
 {
     const float4* bq = reinterpret_cast<const float4*>(b3 + col0);
     const float4* wq = reinterpret_cast<const float4*>(w4 + col0);
+    f32x2 acc = pk2(part, 0.0f);
 #pragma unroll
     for (int k4 = 0; k4 < 8; ++k4) {
         const float4 bb = __ldg(bq + k4), ww = __ldg(wq + k4);
-        part = fmaf(gelu_f(__uint_as_float(u[4 * k4 + 0]) + bb.x), ww.x, part);
-        part = fmaf(gelu_f(__uint_as_float(u[4 * k4 + 1]) + bb.y), ww.y, part);
-        part = fmaf(gelu_f(__uint_as_float(u[4 * k4 + 2]) + bb.z), ww.z, part);
-        part = fmaf(gelu_f(__uint_as_float(u[4 * k4 + 3]) + bb.w), ww.w, part);
+        const f32x2 x01 = add2(pk2(__uint_as_float(u[4 * k4 + 0]), __uint_as_float(u[4 * k4 + 1])), pk2(bb.x, bb.y));
+        const f32x2 x23 = add2(pk2(__uint_as_float(u[4 * k4 + 2]), __uint_as_float(u[4 * k4 + 3])), pk2(bb.z, bb.w));
+        acc = fma2(gelu_acc2(x01), pk2(ww.x, ww.y), acc);
+        acc = fma2(gelu_acc2(x23), pk2(ww.z, ww.w), acc);
     }
-    return part;
+    float a0, a1;
+    upk2(acc, a0, a1);
+    return a0 + a1;
 }
 
 // Two tiles in flight per block (slots 0 and 1, each with its own activation
