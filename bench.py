@@ -53,7 +53,7 @@ def flop_per_update(has_cross: bool) -> float:
 # source (sha256 of the sources); null once the kernel changes.
 # For the batch: the four per-size launches of one macro step of the 4096-instance
 # batch (profiles/batch_kernel_c4.md).
-NCU_TRAFFIC = {"sources_sha256": "8136228db95bcf3ecc758497156add34e1f39ed043dafabfa984d3f333b486c7",
+NCU_TRAFFIC = {"sources_sha256": "57edddbd4f9d72fc0a42b0f723b32a35d8b9ef36d8fb45003b7a44eb1856c238",
                "bytes_per_launch": 506.2e6}
 
 

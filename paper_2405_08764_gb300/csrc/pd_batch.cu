@@ -646,8 +646,8 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     }
 }
 
-// Out of line: inlined, the FP64 solution code of the boundary items joins the
-// patch items' path (measured 1 % slower on the uneven batch).
+// Out of line: inlined, the FP64 solution code of the boundary items cost the
+// patch items' path 1 % on the uneven batch (measured).
 __device__ __noinline__ void boundary_item(const InstDev& I, const BatchItem& it, const BatchArgs& A, int lane)
 {
     double* Un = (A.parity ? A.Ubase : A.Sbase) + I.u_off;

@@ -494,9 +494,10 @@ burst_kernel(const InstDev I, const double* __restrict__ tab, int k_steps, real*
 }
 
 // trapezoid restriction of the departure: ppb (<= 64) patches per block, their
-// contiguous w staged through shared memory with coalesced loads, four threads
-// per patch summing against a table of the trapezoid weights (accumulation in
-// the grid's precision, like the fused kernels' column sums), dU in FP64
+// contiguous w staged into shared memory with 16-byte cp.async copies (plain
+// loads where the block's start is not 16-byte aligned), four threads per patch
+// summing against a table of the trapezoid weights (accumulation in the grid's
+// precision, like the fused kernels' column sums), dU in FP64
 constexpr int kRestrictPatches = 64;
 constexpr size_t kRestrictStage = 96 * 1024;
 
@@ -554,14 +555,9 @@ restrict_kernel(const InstDev I, const real* __restrict__ w, const double* __res
     }
 }
 
-// eq. (Extrapolation) on interior nodes + Dirichlet data at t + dt_macro
-// (scale = dt_macro / tau, formed on the host: no FP64 division per node)
-// Grid rows y (strided by gridDim.y): y < nrows is patch row jr = y, blockIdx.x a
-// chunk of kProjectPer * blockDim.x of its columns; the rows after those hold
-// chunks of the boundary nodes.  Each thread issues the loads of all its nodes
-// before the first update, so it keeps kProjectPer loads of U and dU in flight.
 // Dirichlet data at one boundary node, out of line: inlined, the FP64 solution
-// code is if-converted into the interior path of every warp
+// code tripled the instructions every warp of the projection issued, interior
+// warps included (measured)
 __device__ __noinline__ void project_boundary_node(const InstDev& I, double* __restrict__ U, int q, double t_next)
 {
     const int2 ij = I.bnd_ij[q];
@@ -569,6 +565,12 @@ __device__ __noinline__ void project_boundary_node(const InstDev& I, double* __r
     U[(long long)ij.y * I.nxp + ij.x] = exact_solution(I.sol, xy.x, xy.y, t_next);
 }
 
+// eq. (Extrapolation) on interior nodes + Dirichlet data at t + dt_macro
+// (scale = dt_macro / tau, formed on the host: no FP64 division per node).
+// Grid rows y (strided by gridDim.y): y < nrows is patch row jr = y, blockIdx.x a
+// chunk of kProjectPer * blockDim.x of its columns; the rows after those hold
+// chunks of the boundary nodes.  Each thread issues the loads of all its nodes
+// before the first update, so it keeps kProjectPer loads of U and dU in flight.
 constexpr int kProjectPer = 4;
 constexpr int kProjectBlock = 128;
 
