@@ -666,16 +666,20 @@ __device__ __noinline__ void boundary_item(const InstDev& I, const BatchItem& it
 // Resident blocks per SM requested from the compiler for each micro size: the
 // burst keeps about 9 M values per lane (departure, forcing, six weights, source
 // factor), so the small micro sizes run at a higher occupancy than the largest.
-template <int M, typename real>
+template <int M, bool TSRC, typename real>
 struct BatchBounds {
-    static constexpr int min_blocks = sizeof(real) == 4 ? (M <= 5 ? 8 : M <= 7 ? 6 : M <= 9 ? 5 : 4)
+    // m = 11 (FP32, no time-dependent source) runs ten 64-thread blocks per SM
+    // at 96 registers, which needs the shared-memory carveout at its maximum;
+    // with the source term its burst would spill there, so it keeps eight
+    static constexpr bool max_shared = sizeof(real) == 4 && M >= 11 && !TSRC;
+    static constexpr int min_blocks = sizeof(real) == 4 ? (M <= 5 ? 8 : M <= 7 ? 6 : M <= 9 ? 5 : max_shared ? 5 : 4)
                                                         : (M <= 5 ? 4 : M <= 7 ? 3 : 2);
 };
 
 // One micro size per kernel: the items of this launch are the patch groups of
 // the instances with m = M and those instances' boundary chunks.
 template <int M, bool TSRC, typename real>
-__global__ void __launch_bounds__(128, BatchBounds<M, real>::min_blocks) batch_kernel(const BatchArgs A)
+__global__ void __launch_bounds__(128, BatchBounds<M, TSRC, real>::min_blocks) batch_kernel(const BatchArgs A)
 {
     extern __shared__ __align__(16) unsigned char batch_smem[];
     unsigned char* stage = batch_smem + (size_t)(threadIdx.x >> 5) * WarpStage<M, real>::bytes;
@@ -719,6 +723,11 @@ cudaError_t launch_m(const BatchArgs& a, int block, int grid, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    if (BatchBounds<M, TSRC, real>::max_shared) {
+        e = cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
     batch_kernel<M, TSRC, real><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -729,6 +738,10 @@ int occupancy_m(int block)
     const size_t smem = smem_bytes<M, TSRC, real>(block);
     if (cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
+        return 0;
+    if (BatchBounds<M, TSRC, real>::max_shared &&
+        cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<M, TSRC, real>, block, smem) != cudaSuccess)
