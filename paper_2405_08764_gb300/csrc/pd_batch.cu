@@ -49,11 +49,14 @@ struct WarpStage {
     static constexpr size_t cv_off = fp64_off + (size_t)P * 4 * sizeof(double);
     static constexpr size_t rec0_off = cv_off + (size_t)P * 12 * sizeof(real);
     static constexpr size_t rec1_off = rec0_off + (size_t)NPT * 4 * sizeof(real);
-    // per patch, side (W, E, S, N) and position along it: the dt-scaled stencil
-    // weight toward the ghost and the cross weight, before the mirror folding
-    static constexpr size_t side_off = rec1_off + (size_t)NPT * 4 * sizeof(real);
-    // separable maps: per patch and micro row the row factors of the record (12 values)
-    static constexpr size_t row_off = side_off + (size_t)P * 4 * M * 2 * sizeof(real);
+    // table instances (separable, polar): per patch and micro row the row factors
+    // of the record (12 values; polar: 8 per lane);
+    static constexpr size_t row_off = rec1_off + (size_t)NPT * 4 * sizeof(real);
+    // per-point-record instances instead, in the same place: per patch, side
+    // (W, E, S, N) and position along it the dt-scaled stencil weight toward the
+    // ghost and the cross weight, before the mirror folding
+    static constexpr size_t side_off = row_off;
+    static_assert(P * 4 * M * 2 <= P * M * 12 && 32 * 8 <= P * M * 12, "row region holds either use");
     // a record of zeros (8 values) for the lanes that hold no micro column
     static constexpr size_t zero_off = row_off + (size_t)P * M * 12 * sizeof(real);
     static constexpr size_t bytes = zero_off + 8 * sizeof(real);
@@ -669,11 +672,14 @@ __device__ __noinline__ void boundary_item(const InstDev& I, const BatchItem& it
 template <int M, bool TSRC, typename real>
 struct BatchBounds {
     // m = 11 (FP32, no time-dependent source) runs ten 64-thread blocks per SM
-    // at 96 registers, which needs the shared-memory carveout at its maximum;
-    // with the source term its burst would spill there, so it keeps eight
+    // at 96 registers, which needs the shared-memory carveout at its maximum, and
+    // m = 7 one block more than at 80 registers at 72 (its stage then limits it);
+    // with the source term their bursts would spill there, so they keep the
+    // larger budgets
     static constexpr bool max_shared = sizeof(real) == 4 && M >= 11 && !TSRC;
-    static constexpr int min_blocks = sizeof(real) == 4 ? (M <= 5 ? 8 : M <= 7 ? 6 : M <= 9 ? 5 : max_shared ? 5 : 4)
-                                                        : (M <= 5 ? 4 : M <= 7 ? 3 : 2);
+    static constexpr int min_blocks =
+        sizeof(real) == 4 ? (M <= 5 ? 8 : M <= 7 ? (TSRC ? 6 : 7) : M <= 9 ? 5 : max_shared ? 5 : 4)
+                          : (M <= 5 ? 4 : M <= 7 ? 3 : 2);
 };
 
 // One micro size per kernel: the items of this launch are the patch groups of
