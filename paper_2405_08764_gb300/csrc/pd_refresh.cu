@@ -83,8 +83,11 @@ __device__ __forceinline__ real ghost_delta(const real (&c)[9], const PatchGeo<r
 // working precision; instance constants and slot weights are converted once
 // per block (a double -> float conversion issues on the FP64 pipe, a small
 // fraction of the FP32 rate on this part).
+// FP32: eight blocks (64 warps) per SM at 32 registers.  The kernel is a chain
+// of dependent latencies per warp, so more warps in flight pay more than the
+// few values the tighter register budget moves to local memory (measured).
 template <typename real>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(real) == 4 ? 8 : 1))
 refresh_kernel(const InstDev I, const double* __restrict__ D, const real* __restrict__ rec, real* __restrict__ r)
 {
     __shared__ real cw_s[9][3];
