@@ -106,9 +106,12 @@ struct pd_grid {
     InstDev* insts_dev = nullptr;
     BatchItem* items_dev = nullptr;
     int n_items = 0;
-    // micro-size classes of the batch: items [cls_beg[c], cls_beg[c] + cls_n[c])
-    // are the patch groups and boundary chunks of the instances with m = cls_m[c]
+    // classes of the batch: items [cls_beg[c], cls_beg[c] + cls_n[c]) are the
+    // patch groups of the separable-map instances with m = cls_m[c] (cls_sep[c],
+    // FP32 grids), or the patch groups of the other instances and the boundary
+    // chunks of all instances with m = cls_m[c]
     std::vector<int> cls_m, cls_beg, cls_n;
+    std::vector<char> cls_sep;
     bool batch_dirty = true;
     double* dtm_dev = nullptr;
     double2* scale_dev = nullptr;    // per instance (dtm inv_tau inv_nn, dtm inv_tau)
@@ -542,30 +545,41 @@ pd_status prepare_batch(pd_grid* g)
         s.I.ppw = g->bt_half ? std::max(1, (P + 1) / 2) : P;
         host[k] = s.I;
     }
-    // one class per micro size (largest first); in each class the patch groups,
-    // then the boundary chunks of the class's instances
+    // per micro size (largest first): on FP32 grids one class of the separable-map
+    // instances' patch groups, then one of the other instances' patch groups and
+    // every instance's boundary chunks (either may be empty and is then skipped)
     std::vector<int> sizes;
     for (size_t k = 0; k < n; ++k)
         if (std::find(sizes.begin(), sizes.end(), g->inst[k].I.mx) == sizes.end()) sizes.push_back(g->inst[k].I.mx);
     std::sort(sizes.rbegin(), sizes.rend());
-    g->cls_m.clear(); g->cls_beg.clear(); g->cls_n.clear();
+    g->cls_m.clear(); g->cls_beg.clear(); g->cls_n.clear(); g->cls_sep.clear();
+    const bool fp32 = g->inst[0].d.prec == PD_FP32;
+    auto sep_of = [&](const InstDev& I) { return fp32 && I.coef_mode == COEF_SEPARABLE; };
     for (int m : sizes) {
-        const int beg = (int)items.size();
-        for (size_t k = 0; k < n; ++k) {
-            const InstDev& I = g->inst[k].I;
-            if (I.mx != m) continue;
-            int wpr = (I.ncols + I.ppw - 1) / I.ppw;
-            for (int jr = 0; jr < I.nrows; ++jr)
-                for (int wc = 0; wc < wpr; ++wc) items.push_back(BatchItem{ (int)k, 0, jr, wc });
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool sep = pass == 0;
+            if (sep && !fp32) continue;
+            const int beg = (int)items.size();
+            for (size_t k = 0; k < n; ++k) {
+                const InstDev& I = g->inst[k].I;
+                if (I.mx != m || sep_of(I) != sep) continue;
+                int wpr = (I.ncols + I.ppw - 1) / I.ppw;
+                for (int jr = 0; jr < I.nrows; ++jr)
+                    for (int wc = 0; wc < wpr; ++wc) items.push_back(BatchItem{ (int)k, 0, jr, wc });
+            }
+            if (!sep) {
+                for (size_t k = 0; k < n; ++k) {
+                    if (g->inst[k].I.mx != m) continue;
+                    int chunks = (g->inst[k].I.n_bnd + 31) / 32;
+                    for (int c = 0; c < chunks; ++c) items.push_back(BatchItem{ (int)k, 1, c, 0 });
+                }
+            }
+            if ((int)items.size() == beg) continue;
+            g->cls_m.push_back(m);
+            g->cls_sep.push_back(sep ? 1 : 0);
+            g->cls_beg.push_back(beg);
+            g->cls_n.push_back((int)items.size() - beg);
         }
-        for (size_t k = 0; k < n; ++k) {
-            if (g->inst[k].I.mx != m) continue;
-            int chunks = (g->inst[k].I.n_bnd + 31) / 32;
-            for (int c = 0; c < chunks; ++c) items.push_back(BatchItem{ (int)k, 1, c, 0 });
-        }
-        g->cls_m.push_back(m);
-        g->cls_beg.push_back(beg);
-        g->cls_n.push_back((int)items.size() - beg);
     }
     if (!g->insts_dev) PD_CUDA(g, cudaMalloc(&g->insts_dev, sizeof(InstDev) * n));
     PD_CUDA(g, cudaMemcpy(g->insts_dev, host.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice));
@@ -607,9 +621,9 @@ pd_status batch_buffers(pd_grid* g, int n_macro, const std::vector<double>& dtm)
         PD_CUDA(g, cudaMemcpy(g->scale_dev, sc.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
         g->dtm_host = dtm;
     }
-    // one work-queue counter per macro step and micro-size class (at most the
-    // five batched micro sizes, so the classes may be rebuilt afterwards)
-    const size_t n_counters = (size_t)n_macro * 5;
+    // one work-queue counter per macro step and class (at most two classes for
+    // each of the five batched micro sizes, so the classes may be rebuilt afterwards)
+    const size_t n_counters = (size_t)n_macro * 10;
     if (n_counters > g->counters_n) {
         if (g->counters) { cudaStreamSynchronize(g->stream); cudaFree(g->counters); }
         PD_CUDA(g, cudaMalloc(&g->counters, sizeof(int) * n_counters));
@@ -647,11 +661,11 @@ pd_status batch_time_tables(pd_grid* g, double t0, int n_macro, const std::vecto
     return PD_OK;
 }
 
-int batch_grid(const pd_grid* g, int block, int M)
+int batch_grid(const pd_grid* g, int block, int M, bool sep)
 {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
-    int per = batch_blocks_per_sm(g->inst[0].d.prec, batch_tsrc(g), M, block);
+    int per = batch_blocks_per_sm(g->inst[0].d.prec, batch_tsrc(g), M, sep, block);
     return std::max(1, per) * nsm;
 }
 
@@ -663,7 +677,7 @@ pd_status enqueue_batch(pd_grid* g, double* U, int n_macro, cudaStream_t st, int
     PD_CUDA(g, cudaMemsetAsync(g->counters, 0, sizeof(int) * (size_t)n_macro * ncls, st));
     int block = g->bt_block;
     std::vector<int> grid(ncls);
-    for (int c = 0; c < ncls; ++c) grid[c] = batch_grid(g, block, g->cls_m[c]);
+    for (int c = 0; c < ncls; ++c) grid[c] = batch_grid(g, block, g->cls_m[c], g->cls_sep[c] != 0);
     for (int t = 0; t < n_macro; ++t) {
         for (int c = 0; c < ncls; ++c) {
             if (g->cls_n[c] == 0) continue;
@@ -676,7 +690,8 @@ pd_status enqueue_batch(pd_grid* g, double* U, int n_macro, cudaStream_t st, int
             a.tab = tables ? g->tab : nullptr;
             a.tab_off = tables ? g->tab_off_dev : nullptr;
             a.step = t;
-            cudaError_t e = launch_batch(g->inst[0].d.prec, batch_tsrc(g), g->cls_m[c], a, block, grid[c], st);
+            cudaError_t e = launch_batch(g->inst[0].d.prec, batch_tsrc(g), g->cls_m[c], g->cls_sep[c] != 0, a, block,
+                                         grid[c], st);
             if (e != cudaSuccess) return cuda_fail(g, e, "batched step");
             n_launch += 1;
         }

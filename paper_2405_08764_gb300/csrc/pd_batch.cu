@@ -30,6 +30,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 namespace pd {
 
 namespace {
@@ -63,6 +65,30 @@ struct WarpStage {
     static_assert(cv_off % 16 == 0 && rec0_off % 16 == 0 && rec1_off % 16 == 0 && side_off % 16 == 0 &&
                   row_off % 16 == 0 && zero_off % 16 == 0, "16-byte aligned planes");
 };
+
+// The stage of a warp that runs only separable-map items (FP32): the
+// east/west weights of such a point depend on its column only and stay in the
+// lane's registers, the north/south weights on its row only and stay in the row
+// factors, so the stage keeps one plane per point, (cX, cC, dt r, 0), besides
+// the row factors, the coefficients and the zero record.
+template <int M, typename real>
+struct WarpStageSep {
+    static constexpr int P = 32 / M;
+    static constexpr int NPT = P * M * M;
+    static constexpr size_t fp64_off = 0;
+    static constexpr size_t cv_off = fp64_off + (size_t)P * 4 * sizeof(double);
+    static constexpr size_t rec1_off = cv_off + (size_t)P * 12 * sizeof(real);
+    static constexpr size_t rec0_off = rec1_off;        // no per-point weight plane
+    static constexpr size_t row_off = rec1_off + (size_t)NPT * 4 * sizeof(real);
+    static constexpr size_t side_off = row_off;
+    static constexpr size_t zero_off = row_off + (size_t)P * M * 12 * sizeof(real);
+    static constexpr size_t bytes = zero_off + 16 * sizeof(real);
+    static_assert(cv_off % 16 == 0 && rec1_off % 16 == 0 && row_off % 16 == 0 && zero_off % 16 == 0,
+                  "16-byte aligned planes");
+};
+
+template <int M, typename real, bool SEP>
+using StageOf = typename std::conditional<SEP, WarpStageSep<M, real>, WarpStage<M, real>>::type;
 
 template <typename real>
 __device__ __forceinline__ void store_vec4_shared(real* p, real x, real y, real z, real w)
@@ -344,11 +370,46 @@ __device__ __noinline__ void records_setup(const RecSetup<real> k, int lane)
     }
 }
 
-template <int M, bool TSRC, typename real>
+// K micro steps of a separable-map patch group: burst_steps with the cross
+// term and without the time-dependent source (table instances carry none), the
+// east/west weights one value per lane.  The same operations in the same order.
+template <int M, typename real>
+__device__ __forceinline__ void burst_steps_sep(real (&w)[M], const real cE, const real cW, const real (&cN)[M],
+                                                const real (&cS)[M], const real (&cC)[M], const real (&cX)[M],
+                                                const real (&Rr)[M], int K)
+{
+    for (int k = 0; k < K; ++k) {
+        real e_n = __shfl_down_sync(kFull, w[0], 1);
+        real v_n = __shfl_up_sync(kFull, w[0], 1);
+        real d_n = e_n - v_n, d_c = d_n, d_p = d_n;
+        real w_prev = real(0);
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const real e_c = e_n, v_c = v_n;
+            d_p = d_c;
+            d_c = d_n;
+            if (b + 1 < M) {
+                e_n = __shfl_down_sync(kFull, w[b + 1], 1);
+                v_n = __shfl_up_sync(kFull, w[b + 1], 1);
+                d_n = e_n - v_n;
+            }
+            real acc = fma(cC[b], w[b], Rr[b]);
+            acc = fma(cE, e_c, acc);
+            acc = fma(cW, v_c, acc);
+            if (b + 1 < M) acc = fma(cN[b], w[b + 1], acc);
+            if (b > 0) acc = fma(cS[b], w_prev, acc);
+            if (b > 0 && b + 1 < M) acc = fma(cX[b], d_n - d_p, acc);
+            w_prev = w[b];
+            w[b] = acc;
+        }
+    }
+}
+
+template <int M, bool TSRC, typename real, bool SEP>
 __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it, const BatchArgs& A, int lane,
                                            unsigned char* stage)
 {
-    using S = WarpStage<M, real>;
+    using S = StageOf<M, real, SEP>;
     const int P = I.ppw;                      // patches per warp chosen for this instance (<= 32 / M)
     const int jr = it.jr;
     const int ic0 = it.wc * P;
@@ -380,6 +441,7 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     // the points on that side added to their forcing.
     const double* trow = (A.tab && (TSRC || I.sol != PD_SOL_NONE))
                              ? A.tab + A.tab_off[it.inst] + (long long)A.step * (I.K + kTabExtra) : nullptr;
+    real sep_ef = real(0), sep_wf = real(0);  // separable-only warps: the lane's east/west weights
     {
         // instance constants in registers for the whole item (read once from
         // the instance record, never inside the point loops)
@@ -405,7 +467,7 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                                : nullptr;
         const int recrow = I.ncols * M * 8;                   // one micro row of the patch row, in values
         real* side = reinterpret_cast<real*>(stage + S::side_off);
-        if (mode == COEF_SEPARABLE) {
+        if (SEP || mode == COEF_SEPARABLE) {
             // Separable map x = X(xi), y = Y(eta) with constant K, v, f: alpha, nu
             // and the xi-weights depend on the column only, gamma, omega and the
             // eta-weights on the row only, beta = 2 K12 X'^-1 Y'^-1 is a product,
@@ -498,19 +560,24 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                     const int pt = (q * M + b) * M + a;
                     // unfolded dt wX at (a, b) = xu ib
                     const real g = ghost_terms<M, real>(a, b, wu, eu, wsn, wsn, xu * ib, c21, c12, c22, s0, t0, dx, dy);
-                    store_vec4_shared<real>(rec0 + pt * 4, ef, wf, nf, sf);
+                    if constexpr (!SEP) store_vec4_shared<real>(rec0 + pt * 4, ef, wf, nf, sf);
                     store_vec4_shared<real>(rec1 + pt * 4, x, ccol + crow, dt * r + g, real(0));
+                }
+                if constexpr (SEP) {
+                    sep_ef = ef;
+                    sep_wf = wf;
                 }
             } else if (q < P) {
                 // patches past the end of the row: zero records
 #pragma unroll 1
                 for (int b = 0; b < M; ++b) {
                     const int pt = (q * M + b) * M + a;
-                    store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
+                    if constexpr (!SEP) store_vec4_shared<real>(rec0 + pt * 4, real(0), real(0), real(0), real(0));
                     store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
                 }
             }
-        } else if (mode == COEF_POLAR) {
+        } else if constexpr (!SEP) {
+          if (mode == COEF_POLAR) {
             // Polar map x = R cos xi, y = R sin xi with constant K, v, f: each
             // coefficient of table_coeffs is a sum of products of an angular factor
             // (the lane's micro column) and a radial factor (the micro row, shared by
@@ -596,9 +663,10 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
                     store_vec4_shared<real>(rec1 + pt * 4, real(0), real(0), real(0), real(0));
                 }
             }
-        } else {
+          } else {
             records_setup<M, real>(RecSetup<real>{ cv_s, rec0, rec1, side, rect, idx, idy, idx2, idy2, i4dxdy, hdx, hdy,
                                                    s0, t0, dx, dy, sT, dt, recrow, nvalid, central }, lane);
+          }
         }
         __syncwarp();
     }
@@ -606,25 +674,48 @@ __device__ __forceinline__ void patch_item(const InstDev& I, const BatchItem& it
     // ---- phase 3: K micro steps, lane (q, a) holding micro column a of patch q
     // a patch past the end of its row has zero records; a lane past the last
     // patch of the group reads the zero record for every row
-    real w[M], Rr[M], cE[M], cW[M], cN[M], cS[M], cC[M], cX[M], Gs[M];
+    real w[M];
     const real* z = reinterpret_cast<const real*>(stage + S::zero_off);
-    const real* r0p = q < P ? rec0 + ((size_t)(qc * M) * M + a) * 4 : z;
-    const real* r1p = q < P ? rec1 + ((size_t)(qc * M) * M + a) * 4 : z + 4;
-    const int rs = q < P ? M * 4 : 0;
+    if constexpr (SEP) {
+        // separable-only warps: per point (cX, cC, dt r) from the stage, the row's
+        // north/south weights from the row factors, east/west from the lane
+        real Rr[M], cN[M], cS[M], cC[M], cX[M];
+        const real* r1p = q < P ? rec1 + ((size_t)(qc * M) * M + a) * 4 : z;
+        const int rs = q < P ? M * 4 : 0;
+        const real* rqp = q < P ? reinterpret_cast<const real*>(stage + S::row_off) + qc * M * 12 : z + 8;
+        const int rqs = q < P ? 12 : 0;
 #pragma unroll
-    for (int b = 0; b < M; ++b) {
-        real e, ww, n, s, x, cc, R, Gd;
-        load_vec4_shared<real>(r0p + b * rs, e, ww, n, s);
-        load_vec4_shared<real>(r1p + b * rs, x, cc, R, Gd);
-        cE[b] = e; cW[b] = ww; cN[b] = n; cS[b] = s; cX[b] = x; cC[b] = cc;
-        Rr[b] = R;
-        Gs[b] = Gd;
-        w[b] = real(0);
-    }
+        for (int b = 0; b < M; ++b) {
+            real x, cc, R, Gd;
+            load_vec4_shared<real>(r1p + b * rs, x, cc, R, Gd);
+            (void)Gd;
+            cN[b] = rqp[b * rqs];
+            cS[b] = rqp[b * rqs + 1];
+            cX[b] = x; cC[b] = cc;
+            Rr[b] = R;
+            w[b] = real(0);
+        }
+        burst_steps_sep<M, real>(w, sep_ef, sep_wf, cN, cS, cC, cX, Rr, I.K);
+    } else {
+        real Rr[M], cE[M], cW[M], cN[M], cS[M], cC[M], cX[M], Gs[M];
+        const real* r0p = q < P ? rec0 + ((size_t)(qc * M) * M + a) * 4 : z;
+        const real* r1p = q < P ? rec1 + ((size_t)(qc * M) * M + a) * 4 : z + 4;
+        const int rs = q < P ? M * 4 : 0;
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            real e, ww, n, s, x, cc, R, Gd;
+            load_vec4_shared<real>(r0p + b * rs, e, ww, n, s);
+            load_vec4_shared<real>(r1p + b * rs, x, cc, R, Gd);
+            cE[b] = e; cW[b] = ww; cN[b] = n; cS[b] = s; cX[b] = x; cC[b] = cc;
+            Rr[b] = R;
+            Gs[b] = Gd;
+            w[b] = real(0);
+        }
 
-    // time-dependent source: ds_k read straight from the instance's time table (L1)
-    if (TSRC && trow) burst_steps<M, true, true, real>(w, cE, cW, cN, cS, cC, cX, Gs, Rr, trow, I.K);
-    else burst_steps<M, true, false, real>(w, cE, cW, cN, cS, cC, cX, Gs, Rr, trow, I.K);
+        // time-dependent source: ds_k read straight from the instance's time table (L1)
+        if (TSRC && trow) burst_steps<M, true, true, real>(w, cE, cW, cN, cS, cC, cX, Gs, Rr, trow, I.K);
+        else burst_steps<M, true, false, real>(w, cE, cW, cN, cS, cC, cX, Gs, Rr, trow, I.K);
+    }
 
     // ---- phase 4: restriction and projective update
     real col = real(0.5) * (w[0] + w[M - 1]);
@@ -682,15 +773,30 @@ struct BatchBounds {
                           : (M <= 5 ? 4 : M <= 7 ? 3 : 2);
 };
 
+// Separable-only warps (FP32): their burst holds six values per micro row
+// instead of eight, so they run more blocks per SM than BatchBounds allows.
+template <int M>
+struct SepBounds {
+    static constexpr int min_blocks = M <= 5 ? 10 : M <= 7 ? 8 : M <= 9 ? 6 : 6;
+};
+
+template <int M, bool TSRC, typename real, bool SEP>
+struct KernelBounds {
+    static constexpr int min_blocks = SEP ? SepBounds<M>::min_blocks : BatchBounds<M, TSRC, real>::min_blocks;
+    static constexpr bool max_shared = !SEP && BatchBounds<M, TSRC, real>::max_shared;
+};
+
 // One micro size per kernel: the items of this launch are the patch groups of
-// the instances with m = M and those instances' boundary chunks.
-template <int M, bool TSRC, typename real>
-__global__ void __launch_bounds__(128, BatchBounds<M, TSRC, real>::min_blocks) batch_kernel(const BatchArgs A)
+// the instances with m = M and those instances' boundary chunks; with SEP, the
+// patch groups of the separable-map instances with m = M only (FP32).
+template <int M, bool TSRC, typename real, bool SEP>
+__global__ void __launch_bounds__(128, (KernelBounds<M, TSRC, real, SEP>::min_blocks)) batch_kernel(const BatchArgs A)
 {
+    using S = StageOf<M, real, SEP>;
     extern __shared__ __align__(16) unsigned char batch_smem[];
-    unsigned char* stage = batch_smem + (size_t)(threadIdx.x >> 5) * WarpStage<M, real>::bytes;
+    unsigned char* stage = batch_smem + (size_t)(threadIdx.x >> 5) * S::bytes;
     const int lane = threadIdx.x & 31;
-    if (lane < 8) reinterpret_cast<real*>(stage + WarpStage<M, real>::zero_off)[lane] = real(0);
+    if (lane < (SEP ? 16 : 8)) reinterpret_cast<real*>(stage + S::zero_off)[lane] = real(0);
     __syncwarp();
     // the next item's index, record and the head of its instance record are
     // requested while the current item runs
@@ -710,89 +816,121 @@ __global__ void __launch_bounds__(128, BatchBounds<M, TSRC, real>::min_blocks) b
         }
         const InstDev& I = A.insts[it.inst];
         if (it.kind == 1) boundary_item(I, it, A, lane);
-        else patch_item<M, TSRC, real>(I, it, A, lane, stage);
+        else patch_item<M, TSRC, real, SEP>(I, it, A, lane, stage);
         idx = nidx;
         it = nit;
     }
 }
 
-template <int M, bool TSRC, typename real>
+template <int M, bool TSRC, typename real, bool SEP>
 size_t smem_bytes(int block)
 {
-    return (size_t)(block / 32) * WarpStage<M, real>::bytes;
+    return (size_t)(block / 32) * StageOf<M, real, SEP>::bytes;
 }
 
-template <int M, bool TSRC, typename real>
-cudaError_t launch_m(const BatchArgs& a, int block, int grid, cudaStream_t st)
+template <int M, bool TSRC, typename real, bool SEP>
+cudaError_t set_attributes(size_t smem)
 {
-    const size_t smem = smem_bytes<M, TSRC, real>(block);
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<M, TSRC, real, SEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    if (BatchBounds<M, TSRC, real>::max_shared) {
-        e = cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    if (KernelBounds<M, TSRC, real, SEP>::max_shared)
+        e = cudaFuncSetAttribute(batch_kernel<M, TSRC, real, SEP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-    }
-    batch_kernel<M, TSRC, real><<<grid, block, smem, st>>>(a);
+    return e;
+}
+
+template <int M, bool TSRC, typename real, bool SEP>
+cudaError_t launch_m(const BatchArgs& a, int block, int grid, cudaStream_t st)
+{
+    const size_t smem = smem_bytes<M, TSRC, real, SEP>(block);
+    cudaError_t e = set_attributes<M, TSRC, real, SEP>(smem);
+    if (e != cudaSuccess) return e;
+    batch_kernel<M, TSRC, real, SEP><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int M, bool TSRC, typename real>
+template <int M, bool TSRC, typename real, bool SEP>
 int occupancy_m(int block)
 {
-    const size_t smem = smem_bytes<M, TSRC, real>(block);
-    if (cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
-    if (BatchBounds<M, TSRC, real>::max_shared &&
-        cudaFuncSetAttribute(batch_kernel<M, TSRC, real>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-        return 0;
+    const size_t smem = smem_bytes<M, TSRC, real, SEP>(block);
+    if (set_attributes<M, TSRC, real, SEP>(smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<M, TSRC, real>, block, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<M, TSRC, real, SEP>, block, smem) != cudaSuccess)
         return 0;
     return nb;
 }
 
+// separable-only kernels exist for FP32 and serve grids with and without a
+// time-dependent source (their items carry none)
 template <bool TSRC, typename real>
-cudaError_t launch_tr(int M, const BatchArgs& a, int block, int grid, cudaStream_t st)
+cudaError_t launch_tr(int M, bool sep, const BatchArgs& a, int block, int grid, cudaStream_t st)
 {
+    if (sep) {
+        if constexpr (sizeof(real) == 4) {
+            switch (M) {
+            case 3: return launch_m<3, false, real, true>(a, block, grid, st);
+            case 5: return launch_m<5, false, real, true>(a, block, grid, st);
+            case 7: return launch_m<7, false, real, true>(a, block, grid, st);
+            case 9: return launch_m<9, false, real, true>(a, block, grid, st);
+            case 11: return launch_m<11, false, real, true>(a, block, grid, st);
+            default: return cudaErrorInvalidValue;
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (M) {
-    case 3: return launch_m<3, TSRC, real>(a, block, grid, st);
-    case 5: return launch_m<5, TSRC, real>(a, block, grid, st);
-    case 7: return launch_m<7, TSRC, real>(a, block, grid, st);
-    case 9: return launch_m<9, TSRC, real>(a, block, grid, st);
-    case 11: return launch_m<11, TSRC, real>(a, block, grid, st);
+    case 3: return launch_m<3, TSRC, real, false>(a, block, grid, st);
+    case 5: return launch_m<5, TSRC, real, false>(a, block, grid, st);
+    case 7: return launch_m<7, TSRC, real, false>(a, block, grid, st);
+    case 9: return launch_m<9, TSRC, real, false>(a, block, grid, st);
+    case 11: return launch_m<11, TSRC, real, false>(a, block, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <bool TSRC, typename real>
-int occupancy_tr(int M, int block)
+int occupancy_tr(int M, bool sep, int block)
 {
+    if (sep) {
+        if constexpr (sizeof(real) == 4) {
+            switch (M) {
+            case 3: return occupancy_m<3, false, real, true>(block);
+            case 5: return occupancy_m<5, false, real, true>(block);
+            case 7: return occupancy_m<7, false, real, true>(block);
+            case 9: return occupancy_m<9, false, real, true>(block);
+            case 11: return occupancy_m<11, false, real, true>(block);
+            default: return 0;
+            }
+        }
+        return 0;
+    }
     switch (M) {
-    case 3: return occupancy_m<3, TSRC, real>(block);
-    case 5: return occupancy_m<5, TSRC, real>(block);
-    case 7: return occupancy_m<7, TSRC, real>(block);
-    case 9: return occupancy_m<9, TSRC, real>(block);
-    case 11: return occupancy_m<11, TSRC, real>(block);
+    case 3: return occupancy_m<3, TSRC, real, false>(block);
+    case 5: return occupancy_m<5, TSRC, real, false>(block);
+    case 7: return occupancy_m<7, TSRC, real, false>(block);
+    case 9: return occupancy_m<9, TSRC, real, false>(block);
+    case 11: return occupancy_m<11, TSRC, real, false>(block);
     default: return 0;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_batch(int prec, bool tsrc, int M, const BatchArgs& a, int block, int grid, cudaStream_t st)
+cudaError_t launch_batch(int prec, bool tsrc, int M, bool sep, const BatchArgs& a, int block, int grid,
+                         cudaStream_t st)
 {
-    if (prec == PD_FP32) return tsrc ? launch_tr<true, float>(M, a, block, grid, st) : launch_tr<false, float>(M, a, block, grid, st);
-    return tsrc ? launch_tr<true, double>(M, a, block, grid, st) : launch_tr<false, double>(M, a, block, grid, st);
+    if (prec == PD_FP32)
+        return tsrc ? launch_tr<true, float>(M, sep, a, block, grid, st) : launch_tr<false, float>(M, sep, a, block, grid, st);
+    if (sep) return cudaErrorInvalidValue;
+    return tsrc ? launch_tr<true, double>(M, false, a, block, grid, st) : launch_tr<false, double>(M, false, a, block, grid, st);
 }
 
-int batch_blocks_per_sm(int prec, bool tsrc, int M, int block)
+int batch_blocks_per_sm(int prec, bool tsrc, int M, bool sep, int block)
 {
-    if (prec == PD_FP32) return tsrc ? occupancy_tr<true, float>(M, block) : occupancy_tr<false, float>(M, block);
-    return tsrc ? occupancy_tr<true, double>(M, block) : occupancy_tr<false, double>(M, block);
+    if (prec == PD_FP32) return tsrc ? occupancy_tr<true, float>(M, sep, block) : occupancy_tr<false, float>(M, sep, block);
+    if (sep) return 0;
+    return tsrc ? occupancy_tr<true, double>(M, false, block) : occupancy_tr<false, double>(M, false, block);
 }
 
 }  // namespace pd

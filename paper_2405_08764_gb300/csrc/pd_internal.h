@@ -552,8 +552,11 @@ struct BatchArgs {
     int step;                  // macro step index within the pd_step call
 };
 // one launch covers the items of the instances with micro size M (M x M patches)
-cudaError_t launch_batch(int prec, bool tsrc, int M, const BatchArgs& a, int block, int grid, cudaStream_t st);
-int batch_blocks_per_sm(int prec, bool tsrc, int M, int block);
+// sep: the separable-map patch groups of one micro size (FP32 only), run by
+// kernels whose burst keeps the column-only east/west weights per lane
+cudaError_t launch_batch(int prec, bool tsrc, int M, bool sep, const BatchArgs& a, int block, int grid,
+                         cudaStream_t st);
+int batch_blocks_per_sm(int prec, bool tsrc, int M, bool sep, int block);
 cudaError_t launch_batch_time_tables(const InstDev* insts, int n_inst, const double* dtm, double t0, int n_macro,
                                      const long long* tab_off, double* tab, long long total, cudaStream_t st);
 int persist_item_warps(const InstDev& I);
