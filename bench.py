@@ -51,10 +51,10 @@ def flop_per_update(has_cross: bool) -> float:
 
 # DRAM traffic of the dominant kernel from an ncu capture of this kernel
 # source (sha256 of the sources); null once the kernel changes.
-# For the batch: the four per-size launches of one macro step of the 4096-instance
-# batch (profiles/batch_kernel_c4.md).
-NCU_TRAFFIC = {"sources_sha256": "a2e60ea1bc24183a5192ecfed5bef7818dca1dde45b93bebbd2a57fed9a8a0e9",
-               "bytes_per_launch": 512.3e6}
+# For the batch: the eight launches of one macro step of the 4096-instance batch
+# (four micro sizes, separable-map and other patch groups; profiles/batch_kernel_c4.md).
+NCU_TRAFFIC = {"sources_sha256": "af0c707261038e2a9fdda8058bb1cd9f47c61603f1698010f72fa4d7625fe8a8",
+               "bytes_per_launch": 455.7e6}
 
 
 def kernel_sources_sha(files=("pd_batch.cu", "pd_device.cuh", "pd_internal.h")) -> str:
